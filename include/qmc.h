@@ -1,0 +1,205 @@
+/*
+ * qmc.h - C ABI of the GB300 variational Monte Carlo local-energy engine.
+ *
+ * The library evaluates, for a batch of electron configurations ("walkers"),
+ * the local energy E_L = H Psi / Psi of a Slater-Jastrow(-backflow)
+ * wavefunction, samples |Psi|^2 with a Metropolis walker step, and returns
+ * the low-variance energy gradient and the interatomic forces.  The method
+ * is the one of QMCTorch (arXiv:2506.09743):
+ *
+ *   H      = -1/2 sum_i lap_i + sum_{i>j} 1/r_ij - sum_{i,a} Z_a/r_ia
+ *            + sum_{a>b} Z_a Z_b / R_ab                          (Eq. Hmol)
+ *   Psi    = exp(J(r)) sum_n d_n D_n^up(r~^up) D_n^dn(r~^dn)    (Eq. psimol)
+ *   r~_i   = r_i + sum_{j!=i} (w / r_ij)(r_i - r_j)   (Sec. 2.1, Sec. 3)
+ *   J      = sum_{i<j} w0 r_ij / (1 + b r_ij)       (Eqs. jastrow, pade_kernel)
+ *   kinetic term by the trace formulas of App. F and App. G and the
+ *   excited-determinant table method (Eq. table, App. F / App. H).
+ *
+ * Conventions (all calls):
+ *  - Walker coordinates are float64, coordinate-major ("SoA"): element
+ *    [k][w] at walkers[k * ldw + w], k = 3*i + d for electron i (up electrons
+ *    first, 0 .. n_up-1) and axis d (x, y, z); ldw >= n_walkers.  Units bohr.
+ *  - Device pointers are owned by the caller and are not retained after the
+ *    call returns.  Host pointers are read (or written) before return.
+ *  - Calls taking a `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *    default stream) are stream-ordered and asynchronous unless they return
+ *    a value on the host, in which case they synchronise that stream.
+ *  - Every call returns a qmc_status and never aborts the process; on error
+ *    qmc_last_error() gives a message (thread-local, valid until the next
+ *    call on the same thread).  A walker whose energy is not finite (an
+ *    electron exactly on a nucleus or on another electron, or exactly on a
+ *    node) gets NaN and does not fail the call.
+ *  - A qmc_wf is not safe for concurrent calls on different streams when the
+ *    library-owned workspace is used (workspace == NULL); pass a separate
+ *    caller-owned workspace per concurrent call instead.
+ */
+#ifndef QMC_GB300_H
+#define QMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qmc_wf qmc_wf; /* opaque; owns its device-resident tables */
+
+typedef enum {
+  QMC_OK = 0,
+  QMC_ERR_ARG = 1,         /* invalid argument (null pointer, bad size, bad index) */
+  QMC_ERR_OOM = 2,         /* device allocation failed or workspace too small */
+  QMC_ERR_CUDA = 3,        /* a CUDA runtime error; message has the CUDA text */
+  QMC_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  QMC_ERR_UNSUPPORTED = 5  /* shape outside the compiled limits (see below) */
+} qmc_status;
+
+/* Precision forms of the local energy.
+ *  QMC_FP64        everything in FP64 (AO, AO->MO contraction, determinants).
+ *  QMC_FP32        FP32 AOs and SIMT FP32 AO->MO contraction; determinant LU,
+ *                  log|det|, inverse update and energy assembly in FP64.
+ *  QMC_MIXED_TF32  FP32 AOs; AO->MO contraction on tcgen05 tensor cores with
+ *                  TF32 inputs split into high and low parts (three products,
+ *                  FP32 accumulation in tensor memory); FP64 determinants.
+ *  QMC_MIXED_BF16  as MIXED_TF32 with BF16 high/low parts (kind::f16).
+ * Jastrow and Coulomb terms are FP64 in QMC_FP64 and use FP32 pair
+ * arithmetic with FP64 sums in the other forms. */
+typedef enum { QMC_FP64 = 0, QMC_FP32 = 1, QMC_MIXED_TF32 = 2, QMC_MIXED_BF16 = 3 } qmc_precision;
+
+/* Compiled limits (QMC_ERR_UNSUPPORTED beyond them). */
+#define QMC_MAX_ATOMS 16
+#define QMC_MAX_SPIN_ELECTRONS 8 /* per spin channel */
+#define QMC_MAX_MO 32            /* MOs (tensor-core forms: 16) */
+#define QMC_MAX_AO 256           /* AOs (tensor-core forms: 64) */
+#define QMC_MAX_PRIM 8           /* primitives per contracted Gaussian */
+
+/* Nuclei and electron counts (Eq. Hmol).  Host arrays. */
+typedef struct {
+  int32_t n_atom;
+  const double* xyz; /* [n_atom][3] nuclear positions, bohr */
+  const double* z;   /* [n_atom] nuclear charges */
+  int32_t n_up;      /* electrons of spin up (electrons 0 .. n_up-1) */
+  int32_t n_down;    /* electrons of spin down */
+} qmc_atoms;
+
+/* Atomic orbitals (Sec. 2.1).  AO b is centred on atom ao_atom[b] with
+ * d = r - R: kind 0 (Slater) phi = N dx^kx dy^ky dz^kz |d|^kn exp(-zeta |d|)
+ * with one primitive (zeta = prim_exp, prim_coef scales it); kind 1
+ * (contracted Cartesian Gaussian) phi = sum_p c_p N_p dx^kx dy^ky dz^kz
+ * exp(-alpha_p |d|^2).  Normalisation: STO radial (2 zeta)^(n+1/2)/sqrt((2n)!),
+ * n = kn + l + 1, times sqrt((2l+1)!!/(4 pi (2kx-1)!!(2ky-1)!!(2kz-1)!!));
+ * GTO primitive (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2kx-1)!!(2ky-1)!!(2kz-1)!!).
+ * Host arrays. */
+typedef struct {
+  int32_t n_ao;
+  const int32_t* ao_atom;       /* [n_ao] */
+  const int32_t* ao_kind;       /* [n_ao] 0 = STO, 1 = GTO */
+  const int32_t* ao_pow;        /* [n_ao][4] kx, ky, kz, kn */
+  const int32_t* ao_prim_start; /* [n_ao + 1] offsets into prim_exp / prim_coef */
+  const double* prim_exp;       /* zeta (STO) or alpha (GTO) */
+  const double* prim_coef;      /* contraction coefficients */
+} qmc_basis;
+
+/* Molecular orbitals phi_m = sum_b C[b][m] AO_b (Sec. 2.1; the paper's
+ * c x mu product).  Host array [n_ao][n_mo], row-major. */
+typedef struct {
+  int32_t n_mo;
+  const double* coeff;
+} qmc_mos;
+
+/* Determinant expansion sum_n d_n D_n^up D_n^dn (Eq. psimol).  Per
+ * determinant and spin an excitation record (rank, h1, h2, p1, p2): the
+ * ground-state columns h1 < h2 (orbitals 0 .. n_s-1) are replaced in place
+ * by virtual orbitals p1 < p2 (Eq. AX, App. H); rank 0 = ground state, rank
+ * at most 2, unused entries -1.  Host arrays. */
+typedef struct {
+  int32_t n_det;
+  const double* weight; /* [n_det] CI weights d_n */
+  const int32_t* exc;   /* [n_det][2][5] */
+} qmc_dets;
+
+/* Pade electron-electron Jastrow u(r) = w0 r / (1 + b r), w0 = w0_par for
+ * parallel and w0_anti for antiparallel spins (Eq. pade_kernel, App. D),
+ * and the inverse backflow kernel K(r) = backflow_w / r (Sec. 3; 0 = off). */
+typedef struct {
+  double w0_par;
+  double w0_anti;
+  double b;
+  double backflow_w;
+} qmc_jastrow;
+
+typedef struct {
+  int32_t precision; /* qmc_precision */
+  int32_t device;    /* CUDA device ordinal the tables live on */
+} qmc_options;
+
+/* Build a wavefunction: validates the inputs, computes normalisations and the
+ * device-resident tables on `opt->device`.  *out is set on QMC_OK.  Defines
+ * Psi of Eq. psimol with the pieces above. */
+qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const qmc_mos* mos,
+                         const qmc_dets* dets, const qmc_jastrow* jastrow, const qmc_options* opt,
+                         qmc_wf** out);
+
+/* Free a wavefunction and its device tables (NULL is a no-op). */
+void qmc_destroy_wf(qmc_wf* wf);
+
+/* Move the nuclei (same basis, MOs and determinants), e.g. along a bond
+ * (Sec. 3.3).  xyz: host [n_atom][3].  Stream-ordered on the legacy stream
+ * (synchronous). */
+qmc_status qmc_set_geometry(qmc_wf* wf, const double* xyz);
+
+/* Bytes of device scratch that one call with n_walkers needs when a caller
+ * workspace is passed (0 on error). */
+size_t qmc_workspace_size(const qmc_wf* wf, int64_t n_walkers);
+
+/* Local energies (Eq. Hmol, kinetic term by App. F / App. G and Eq. table):
+ * e_loc[w] = E_L(r_w) and, if log_psi != NULL, log_psi[w] = log|Psi(r_w)|.
+ * walkers: device [3N][ldw]; e_loc, log_psi: device [n_walkers].
+ * workspace: device scratch of at least qmc_workspace_size(wf, n_walkers)
+ * bytes, or NULL to use a library-owned buffer (grown on demand).
+ * n_walkers = 0 is a no-op. */
+qmc_status qmc_local_energy(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw,
+                            double* e_loc, double* log_psi, void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/* As qmc_local_energy with HOST buffers: copies the walkers to library-owned
+ * device memory, evaluates, and copies e_loc (and log_psi if not NULL) back;
+ * returns after the results are on the host.  walkers: host [3N][n_walkers]
+ * (ldw = n_walkers); host buffers should be pinned for full speed. */
+qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_walkers,
+                                 double* e_loc, double* log_psi, void* stream);
+
+/* Metropolis-Hastings walker steps (App. B): every step moves all electrons
+ * of a walker by step * z, z ~ N(0, 1) per coordinate, and accepts with
+ * probability min(1, |Psi'/Psi|^2).  Random numbers: Philox4x32-10 with key
+ * (seed mod 2^32, seed div 2^32) and counter (block, first_walker + w,
+ * global step mod 2^32, global step div 2^32), global step = step_offset + t;
+ * block j gives Gaussians 4j..4j+3 by Box-Muller on word pairs, block
+ * ceil(3N/4) word 0 the acceptance uniform u, with u(x) = (x + 0.5) 2^-32;
+ * accept iff log u < 2 (log|Psi'| - log|Psi|).  The result is therefore a
+ * pure function of (wf, walkers, seed, first_walker, step_offset, n_steps,
+ * step), independent of batching.
+ * walkers: device [3N][ldw], updated in place.  log_psi: device [n_walkers],
+ * if not NULL receives log|Psi| of the final positions.  n_accept: device
+ * int64 [n_walkers], if not NULL incremented by each walker's accepted moves.
+ * workspace as for qmc_local_energy (qmc_workspace_size covers it). */
+qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_steps,
+                      double step, uint64_t seed, uint64_t first_walker, uint64_t step_offset,
+                      double* log_psi, int64_t* n_accept, void* workspace, size_t workspace_bytes,
+                      void* stream);
+
+/* Number of variational parameters and the offsets of the gradient blocks:
+ * offsets[0] exponents (one per primitive, prim_exp order), [1] MO
+ * coefficients (row-major n_ao x n_mo), [2] CI weights, [3] Jastrow b,
+ * [4] backflow w, [5] = n_param.  offsets may be NULL. */
+qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[6]);
+
+/* Message of the last failed call on this thread ("" if none yet).  The
+ * pointer stays valid until the next library call on the same thread. */
+const char* qmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMC_GB300_H */

@@ -1,0 +1,159 @@
+"""GB300-native variational Monte Carlo local-energy engine (QMCTorch method).
+
+Python side of the C ABI declared in ``include/qmc.h``: argument marshalling
+only.  Every step of the computation runs in the CUDA library
+``libqmc_gb300.so``; PyTorch provides device memory and streams.
+
+    from paper_2506_09743_gb300 import Wavefunction
+    wf = Wavefunction(molecule, precision="mixed_tf32")
+    e_loc, log_psi = wf.local_energy(walkers_soa)      # torch CUDA float64 [3N, W]
+    wf.sample(walkers_soa, n_steps=50, step=0.2, seed=1)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import PRECISIONS, QmcError  # noqa: F401
+
+__all__ = ["Wavefunction", "QmcError", "PRECISIONS", "library"]
+
+
+def library():
+    """The loaded ctypes library (raises if it has not been built)."""
+    return _lib.load()
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Wavefunction:
+    """A device-resident Slater-Jastrow(-backflow) wavefunction.
+
+    ``mol`` is a ``qmc_inputs.Molecule`` (plain arrays).  ``precision`` is one
+    of ``fp64``, ``fp32``, ``mixed_tf32``, ``mixed_bf16``.
+    """
+
+    def __init__(self, mol, precision: str = "fp64", device: int = 0):
+        lib = library()
+        self.mol = mol
+        self.precision = precision
+        self.device = device
+        self.n_elec = mol.n_up + mol.n_down
+        # keep the marshalled arrays alive for the duration of the call
+        self._arrays = a = dict(
+            xyz=np.ascontiguousarray(mol.atom_xyz, dtype=np.float64).reshape(-1),
+            z=np.ascontiguousarray(mol.atom_z, dtype=np.float64),
+            ao_atom=np.ascontiguousarray(mol.ao_atom, dtype=np.int32),
+            ao_kind=np.ascontiguousarray(mol.ao_kind, dtype=np.int32),
+            ao_pow=np.ascontiguousarray(mol.ao_pow, dtype=np.int32).reshape(-1),
+            ao_prim_start=np.ascontiguousarray(mol.ao_prim_start, dtype=np.int32),
+            prim_exp=np.ascontiguousarray(mol.prim_exp, dtype=np.float64),
+            prim_coef=np.ascontiguousarray(mol.prim_coef, dtype=np.float64),
+            mo=np.ascontiguousarray(mol.mo_coeff, dtype=np.float64).reshape(-1),
+            det_w=np.ascontiguousarray(mol.det_weight, dtype=np.float64),
+            det_exc=np.ascontiguousarray(mol.det_exc, dtype=np.int32).reshape(-1),
+        )
+        atoms = _lib.Atoms(mol.n_atom, _ptr(a["xyz"], ctypes.c_double), _ptr(a["z"], ctypes.c_double),
+                           mol.n_up, mol.n_down)
+        basis = _lib.Basis(mol.n_ao, _ptr(a["ao_atom"], ctypes.c_int32), _ptr(a["ao_kind"], ctypes.c_int32),
+                           _ptr(a["ao_pow"], ctypes.c_int32), _ptr(a["ao_prim_start"], ctypes.c_int32),
+                           _ptr(a["prim_exp"], ctypes.c_double), _ptr(a["prim_coef"], ctypes.c_double))
+        mos = _lib.Mos(mol.n_mo, _ptr(a["mo"], ctypes.c_double))
+        dets = _lib.Dets(mol.n_det, _ptr(a["det_w"], ctypes.c_double), _ptr(a["det_exc"], ctypes.c_int32))
+        jas = _lib.Jastrow(mol.jastrow_w0_par, mol.jastrow_w0_anti, mol.jastrow_b, mol.backflow_w)
+        opt = _lib.Options(PRECISIONS[precision], device)
+        handle = ctypes.c_void_p()
+        _lib.check(lib.qmc_create_wf(ctypes.byref(atoms), ctypes.byref(basis), ctypes.byref(mos),
+                                     ctypes.byref(dets), ctypes.byref(jas), ctypes.byref(opt),
+                                     ctypes.byref(handle)))
+        self._h = handle
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.qmc_destroy_wf(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def set_geometry(self, xyz):
+        a = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+        _lib.check(self._lib.qmc_set_geometry(self._h, _ptr(a, ctypes.c_double)))
+
+    def workspace_size(self, n_walkers: int) -> int:
+        return int(self._lib.qmc_workspace_size(self._h, int(n_walkers)))
+
+    def param_layout(self):
+        n = ctypes.c_int64()
+        off = (ctypes.c_int64 * 6)()
+        _lib.check(self._lib.qmc_param_layout(self._h, ctypes.byref(n), off))
+        return int(n.value), [int(v) for v in off]
+
+    # ------------------------------------------------------------------
+    def local_energy(self, walkers, n_walkers: int | None = None, e_loc=None, log_psi=None, workspace=None,
+                     stream=None, want_log_psi: bool = True):
+        """E_L (and log|Psi|) for walkers given as a CUDA float64 tensor [3N, ldw]."""
+        import torch
+
+        assert walkers.is_cuda and walkers.dtype == torch.float64 and walkers.dim() == 2
+        assert walkers.stride(1) == 1 and walkers.shape[0] == 3 * self.n_elec
+        W = walkers.shape[1] if n_walkers is None else int(n_walkers)
+        ldw = walkers.stride(0)
+        if e_loc is None:
+            e_loc = torch.empty(W, dtype=torch.float64, device=walkers.device)
+        if log_psi is None and want_log_psi:
+            log_psi = torch.empty(W, dtype=torch.float64, device=walkers.device)
+        ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+        _lib.check(self._lib.qmc_local_energy(self._h, _dptr(walkers), W, ldw, _dptr(e_loc), _dptr(log_psi),
+                                              _dptr(workspace), ws_bytes, _stream_handle(stream)))
+        return e_loc, log_psi
+
+    def local_energy_host(self, walkers: np.ndarray, e_loc: np.ndarray | None = None,
+                          log_psi: np.ndarray | None = None, stream=None):
+        """E_L from HOST buffers: walkers float64 [3N, W] C-contiguous (pinned
+        memory is fastest); results are on the host when this returns."""
+        W = walkers.shape[1]
+        assert walkers.dtype == np.float64 and walkers.flags.c_contiguous and walkers.shape[0] == 3 * self.n_elec
+        if e_loc is None:
+            e_loc = np.empty(W, dtype=np.float64)
+        _lib.check(self._lib.qmc_local_energy_host(
+            self._h, walkers.ctypes.data_as(ctypes.c_void_p), W, e_loc.ctypes.data_as(ctypes.c_void_p),
+            None if log_psi is None else log_psi.ctypes.data_as(ctypes.c_void_p),
+            ctypes.c_void_p(0) if stream is None else _stream_handle(stream)))
+        return e_loc, log_psi
+
+    def sample(self, walkers, n_steps: int, step: float, seed: int, first_walker: int = 0, step_offset: int = 0,
+               n_walkers: int | None = None, log_psi=None, n_accept=None, workspace=None, stream=None):
+        """Metropolis steps, updating the CUDA float64 walkers [3N, ldw] in place."""
+        import torch
+
+        assert walkers.is_cuda and walkers.dtype == torch.float64 and walkers.stride(1) == 1
+        W = walkers.shape[1] if n_walkers is None else int(n_walkers)
+        ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+        _lib.check(self._lib.qmc_sample(self._h, _dptr(walkers), W, walkers.stride(0), int(n_steps), float(step),
+                                        int(seed), int(first_walker), int(step_offset), _dptr(log_psi),
+                                        _dptr(n_accept), _dptr(workspace), ws_bytes, _stream_handle(stream)))
+        return walkers

@@ -1,0 +1,101 @@
+"""ctypes declarations of the C ABI in ``include/qmc.h``.
+
+Loading fails loudly (``RuntimeError``) if the shared library is missing:
+there is no CPU fallback anywhere in the package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqmc_gb300.so")
+
+QMC_OK, QMC_ERR_ARG, QMC_ERR_OOM, QMC_ERR_CUDA, QMC_ERR_TIMEOUT, QMC_ERR_UNSUPPORTED = range(6)
+STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA", 4: "QMC_ERR_TIMEOUT",
+                5: "QMC_ERR_UNSUPPORTED"}
+QMC_FP64, QMC_FP32, QMC_MIXED_TF32, QMC_MIXED_BF16 = range(4)
+PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "mixed_tf32": QMC_MIXED_TF32, "mixed_bf16": QMC_MIXED_BF16}
+
+# every exported symbol declared in include/qmc.h
+EXPORTED = (
+    "qmc_create_wf", "qmc_destroy_wf", "qmc_set_geometry", "qmc_workspace_size", "qmc_local_energy",
+    "qmc_local_energy_host", "qmc_sample", "qmc_param_layout", "qmc_last_error",
+)
+
+PD = POINTER(c_double)
+PI32 = POINTER(c_int32)
+
+
+class Atoms(ctypes.Structure):
+    _fields_ = [("n_atom", c_int32), ("xyz", PD), ("z", PD), ("n_up", c_int32), ("n_down", c_int32)]
+
+
+class Basis(ctypes.Structure):
+    _fields_ = [("n_ao", c_int32), ("ao_atom", PI32), ("ao_kind", PI32), ("ao_pow", PI32),
+                ("ao_prim_start", PI32), ("prim_exp", PD), ("prim_coef", PD)]
+
+
+class Mos(ctypes.Structure):
+    _fields_ = [("n_mo", c_int32), ("coeff", PD)]
+
+
+class Dets(ctypes.Structure):
+    _fields_ = [("n_det", c_int32), ("weight", PD), ("exc", PI32)]
+
+
+class Jastrow(ctypes.Structure):
+    _fields_ = [("w0_par", c_double), ("w0_anti", c_double), ("b", c_double), ("backflow_w", c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("device", c_int32)]
+
+
+class QmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library once; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    lib.qmc_create_wf.argtypes = [POINTER(Atoms), POINTER(Basis), POINTER(Mos), POINTER(Dets), POINTER(Jastrow),
+                                  POINTER(Options), POINTER(c_void_p)]
+    lib.qmc_create_wf.restype = c_int32
+    lib.qmc_destroy_wf.argtypes = [c_void_p]
+    lib.qmc_destroy_wf.restype = None
+    lib.qmc_set_geometry.argtypes = [c_void_p, PD]
+    lib.qmc_set_geometry.restype = c_int32
+    lib.qmc_workspace_size.argtypes = [c_void_p, c_int64]
+    lib.qmc_workspace_size.restype = c_size_t
+    lib.qmc_local_energy.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_size_t,
+                                     c_void_p]
+    lib.qmc_local_energy.restype = c_int32
+    lib.qmc_local_energy_host.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
+    lib.qmc_local_energy_host.restype = c_int32
+    lib.qmc_sample.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_double, c_uint64, c_uint64,
+                               c_uint64, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    lib.qmc_sample.restype = c_int32
+    lib.qmc_param_layout.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int64)]
+    lib.qmc_param_layout.restype = c_int32
+    lib.qmc_last_error.argtypes = []
+    lib.qmc_last_error.restype = c_char_p
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != QMC_OK:
+        msg = _lib.qmc_last_error().decode() if _lib is not None else ""
+        raise QmcError(status, msg)

@@ -1,0 +1,571 @@
+// C ABI of the engine: wavefunction construction, workspace management and
+// the launch sequences of qmc_local_energy / qmc_sample.
+//
+// Launch sequence of one local-energy evaluation (Sec. 2.2, App. F):
+//   k_jastrow   J, grad J, kinJ, V                  (thread per walker)
+//   k_ao_mo_*   Phi and (lap + 2 grad J . grad) Phi  (SIMT, or tcgen05 for the
+//               mixed forms)
+//   k_det       A0^-1, tables, excited determinants, E_L, log|Psi|
+// One Metropolis step (App. B): k_propose, the value-only form of the same
+// three stages on the proposal, k_accept.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qmc_internal.cuh"
+
+using namespace qmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+qmc_status fail(qmc_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+qmc_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return QMC_ERR_CUDA;
+}
+
+double dfact(int n) {
+  double r = 1.0;
+  while (n > 1) { r *= n; n -= 2; }
+  return r;
+}
+
+double fact(int n) {
+  double r = 1.0;
+  for (int k = 2; k <= n; ++k) r *= k;
+  return r;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct qmc_wf {
+  int device = 0;
+  int precision = QMC_FP64;
+  WfDev dev{};
+  // host copies kept for set_geometry / layout queries
+  int n_prim = 0;
+  std::vector<double> atom_xyz, atom_z;
+  // device allocations
+  void* blob = nullptr;
+  // library-owned workspace and host-call staging buffers
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* stage = nullptr;
+  size_t stage_bytes = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t ta_size(int prec) { return prec == QMC_FP64 ? 8 : 4; }
+
+size_t workspace_bytes(const qmc_wf* wf, int64_t W) {
+  const int64_t ldm = round_up(W > 0 ? W : 1, 32);
+  const int N = wf->dev.n_elec;
+  const size_t ta = ta_size(wf->precision);
+  size_t b = 0;
+  b += align256(3 * N * ldm * ta);                     // gradJ
+  b += align256(3 * ldm * sizeof(double));             // jscal
+  b += align256((size_t)N * 2 * wf->dev.n_mo * ldm * ta);  // MO channels
+  b += align256(3 * N * ldm * sizeof(double));         // proposals
+  b += 2 * align256(ldm * sizeof(double));             // lp, lp_new
+  b += align256(sizeof(int));                          // device error flag
+  return b;
+}
+
+Workspace carve(const qmc_wf* wf, void* base, int64_t W, int** err_flag) {
+  Workspace ws{};
+  ws.ldm = round_up(W > 0 ? W : 1, 32);
+  const int N = wf->dev.n_elec;
+  const size_t ta = ta_size(wf->precision);
+  char* p = static_cast<char*>(base);
+  ws.gradJ = p; p += align256(3 * N * ws.ldm * ta);
+  ws.jscal = reinterpret_cast<double*>(p); p += align256(3 * ws.ldm * sizeof(double));
+  ws.mo = p; p += align256((size_t)N * 2 * wf->dev.n_mo * ws.ldm * ta);
+  ws.prop = reinterpret_cast<double*>(p); p += align256(3 * N * ws.ldm * sizeof(double));
+  ws.lp = reinterpret_cast<double*>(p); p += align256(ws.ldm * sizeof(double));
+  ws.lp_new = reinterpret_cast<double*>(p); p += align256(ws.ldm * sizeof(double));
+  *err_flag = reinterpret_cast<int*>(p);
+  return ws;
+}
+
+qmc_status get_workspace(qmc_wf* wf, int64_t W, void* user, size_t user_bytes, void** out) {
+  const size_t need = workspace_bytes(wf, W);
+  if (user) {
+    if (user_bytes < need)
+      return fail(QMC_ERR_OOM, "workspace too small: need " + std::to_string(need) + " bytes");
+    *out = user;
+    return QMC_OK;
+  }
+  if (wf->ws_bytes < need) {
+    if (wf->ws) cudaFree(wf->ws);
+    wf->ws = nullptr;
+    wf->ws_bytes = 0;
+    cudaError_t e = cudaMalloc(&wf->ws, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QMC_ERR_OOM, std::string("workspace allocation: ") + cudaGetErrorString(e));
+    }
+    wf->ws_bytes = need;
+  }
+  *out = wf->ws;
+  return QMC_OK;
+}
+
+double vnn_of(const WfDev& d) {
+  double v = 0.0;
+  for (int a = 0; a < d.n_atom; ++a)
+    for (int b = a + 1; b < d.n_atom; ++b) {
+      const double dx = d.atom_xyz[a][0] - d.atom_xyz[b][0], dy = d.atom_xyz[a][1] - d.atom_xyz[b][1],
+                   dz = d.atom_xyz[a][2] - d.atom_xyz[b][2];
+      v += d.atom_z[a] * d.atom_z[b] / std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  return v;
+}
+
+// Split an FP32 value into TF32 high part (round to nearest, 10 explicit
+// mantissa bits) and the FP32 remainder.
+uint32_t tf32_hi_bits(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return u;
+  u += 0x1000u;  // round half away from zero at bit 13
+  return u & 0xffffe000u;
+}
+
+float bits_f(uint32_t u) {
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Offset (in 32-bit words) of element (row, k) of a K-major operand stored as
+// 8-row x 16-byte core matrices, core matrices along K contiguous (128 B
+// apart) and 8-row groups k_pad*4 bytes apart.
+size_t core_offset_words(int row, int k, int k_pad) {
+  return (size_t)(row / 8) * (k_pad / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4 + (k % 4);
+}
+
+qmc_status launch_status(cudaError_t e, const char* where) {
+  return e == cudaSuccess ? QMC_OK : cuda_fail(e, where);
+}
+
+}  // namespace
+
+extern "C" {
+
+qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const qmc_mos* mos, const qmc_dets* dets,
+                         const qmc_jastrow* jastrow, const qmc_options* opt, qmc_wf** out) {
+  if (!atoms || !basis || !mos || !dets || !jastrow || !opt || !out) return fail(QMC_ERR_ARG, "null argument");
+  *out = nullptr;
+  const int na = atoms->n_atom, nup = atoms->n_up, ndn = atoms->n_down;
+  if (na < 1 || na > QMC_MAX_ATOMS || !atoms->xyz || !atoms->z) return fail(QMC_ERR_ARG, "bad atoms");
+  if (nup < 0 || ndn < 0 || nup + ndn < 1) return fail(QMC_ERR_ARG, "bad electron counts");
+  if (nup > QMC_MAX_SPIN_ELECTRONS || ndn > QMC_MAX_SPIN_ELECTRONS)
+    return fail(QMC_ERR_UNSUPPORTED, "more than 8 electrons per spin");
+  const int nao = basis->n_ao, nmo = mos->n_mo;
+  if (nao < 1 || nao > QMC_MAX_AO || !basis->ao_atom || !basis->ao_kind || !basis->ao_pow ||
+      !basis->ao_prim_start || !basis->prim_exp || !basis->prim_coef)
+    return fail(QMC_ERR_ARG, "bad basis");
+  if (nmo < 1 || nmo > QMC_MAX_MO || !mos->coeff) return fail(QMC_ERR_ARG, "bad MO table");
+  if (nmo < nup || nmo < ndn) return fail(QMC_ERR_ARG, "fewer MOs than electrons of one spin");
+  const int prec = opt->precision;
+  if (prec < QMC_FP64 || prec > QMC_MIXED_BF16) return fail(QMC_ERR_ARG, "bad precision");
+  const bool tc = prec == QMC_MIXED_TF32 || prec == QMC_MIXED_BF16;
+  if (tc && (nmo > 16 || nao > 64)) return fail(QMC_ERR_UNSUPPORTED, "tensor-core forms need n_mo <= 16, n_ao <= 64");
+  if (prec == QMC_MIXED_BF16) return fail(QMC_ERR_UNSUPPORTED, "BF16 form not built");
+  if (!dets->weight || !dets->exc || dets->n_det < 1 || dets->n_det > kMaxDets)
+    return fail(QMC_ERR_ARG, "bad determinant list");
+  if (jastrow->backflow_w != 0.0) return fail(QMC_ERR_UNSUPPORTED, "backflow form not built");
+
+  qmc_wf* wf = new qmc_wf();
+  wf->device = opt->device;
+  wf->precision = prec;
+  WfDev& d = wf->dev;
+  d.n_atom = na;
+  d.n_up = nup;
+  d.n_down = ndn;
+  d.n_elec = nup + ndn;
+  d.n_ao = nao;
+  d.n_mo = nmo;
+  d.w0_par = jastrow->w0_par;
+  d.w0_anti = jastrow->w0_anti;
+  d.jb = jastrow->b;
+  d.bf_w = jastrow->backflow_w;
+  for (int a = 0; a < na; ++a) {
+    for (int k = 0; k < 3; ++k) d.atom_xyz[a][k] = atoms->xyz[3 * a + k];
+    d.atom_z[a] = atoms->z[a];
+  }
+  d.vnn = vnn_of(d);
+  wf->atom_xyz.assign(atoms->xyz, atoms->xyz + 3 * na);
+  wf->atom_z.assign(atoms->z, atoms->z + na);
+
+  // ---- basis: shells, normalisation, angular factors
+  std::vector<ShellDev> shells;
+  std::vector<int> ao_pow(nao);
+  std::vector<double> ang(nao);
+  wf->n_prim = basis->ao_prim_start[nao];
+  for (int b = 0; b < nao; ++b) {
+    const int atom = basis->ao_atom[b], kind = basis->ao_kind[b];
+    const int kx = basis->ao_pow[4 * b], ky = basis->ao_pow[4 * b + 1], kz = basis->ao_pow[4 * b + 2],
+              kn = basis->ao_pow[4 * b + 3];
+    const int s0 = basis->ao_prim_start[b], s1 = basis->ao_prim_start[b + 1];
+    if (atom < 0 || atom >= na || (kind != 0 && kind != 1) || kx < 0 || ky < 0 || kz < 0 || kn < 0 || kx > 4 ||
+        ky > 4 || kz > 4 || kx + ky + kz > 4 || kn > 8 || s1 <= s0 || (kind == 0 && s1 - s0 != 1) ||
+        s1 - s0 > QMC_MAX_PRIM) {
+      delete wf;
+      return fail(QMC_ERR_ARG, "bad AO " + std::to_string(b));
+    }
+    const int l = kx + ky + kz;
+    ao_pow[b] = kx | (ky << 4) | (kz << 8);
+    const double df = dfact(2 * kx - 1) * dfact(2 * ky - 1) * dfact(2 * kz - 1);
+    ShellDev sh{};
+    sh.atom = atom;
+    sh.kind = kind;
+    sh.kn = kind == 0 ? kn : 0;
+    sh.l = l;
+    sh.n_prim = s1 - s0;
+    sh.ao_first = b;
+    sh.n_ao = 1;
+    if (kind == 0) {
+      const double zeta = basis->prim_exp[s0];
+      const int n = kn + l + 1;
+      ang[b] = std::sqrt(dfact(2 * l + 1) / (4.0 * M_PI * df));
+      sh.expo[0] = zeta;
+      sh.coef[0] = basis->prim_coef[s0] * std::pow(2.0 * zeta, n + 0.5) / std::sqrt(fact(2 * n));
+    } else {
+      ang[b] = 1.0 / std::sqrt(df);
+      for (int p = s0; p < s1; ++p) {
+        const double al = basis->prim_exp[p];
+        sh.expo[p - s0] = al;
+        sh.coef[p - s0] = basis->prim_coef[p] * std::pow(2.0 * al / M_PI, 0.75) * std::pow(4.0 * al, 0.5 * l);
+      }
+    }
+    bool merged = false;
+    if (!shells.empty()) {
+      ShellDev& q = shells.back();
+      if (q.atom == sh.atom && q.kind == sh.kind && q.kn == sh.kn && q.l == sh.l && q.n_prim == sh.n_prim &&
+          q.ao_first + q.n_ao == b) {
+        bool same = true;
+        for (int p = 0; p < sh.n_prim; ++p) same = same && q.expo[p] == sh.expo[p] && q.coef[p] == sh.coef[p];
+        if (same) { q.n_ao += 1; merged = true; }
+      }
+    }
+    if (!merged) shells.push_back(sh);
+  }
+  if ((int)shells.size() > kMaxShells) {
+    delete wf;
+    return fail(QMC_ERR_UNSUPPORTED, "too many shells");
+  }
+  d.n_shell = (int)shells.size();
+  {  // balance the AO count between the two thread halves of the tensor-core AO stage
+    int acc = 0;
+    d.shell_split = d.n_shell;
+    for (int s = 0; s < d.n_shell; ++s) {
+      if (2 * acc >= nao) { d.shell_split = s; break; }
+      acc += shells[s].n_ao;
+    }
+  }
+  std::vector<double> mo64((size_t)nao * nmo);
+  std::vector<float> mo32((size_t)nao * nmo);
+  for (int b = 0; b < nao; ++b)
+    for (int m = 0; m < nmo; ++m) {
+      mo64[(size_t)b * nmo + m] = mos->coeff[(size_t)b * nmo + m] * ang[b];
+      mo32[(size_t)b * nmo + m] = (float)mo64[(size_t)b * nmo + m];
+    }
+
+  // ---- determinants: unique excitation records per spin
+  std::vector<int> exc(2 * kMaxExc * 5, -1);
+  std::vector<int> det_idx(2 * dets->n_det);
+  for (int s = 0; s < 2; ++s) {
+    const int ns = s == 0 ? nup : ndn;
+    std::map<std::vector<int>, int> seen;
+    std::vector<int> g = {0, -1, -1, -1, -1};
+    seen[g] = 0;
+    for (int k = 0; k < 5; ++k) exc[(s * kMaxExc + 0) * 5 + k] = g[k];
+    int h_lo = ns, p_hi = ns;
+    for (int n = 0; n < dets->n_det; ++n) {
+      std::vector<int> e(dets->exc + (n * 2 + s) * 5, dets->exc + (n * 2 + s) * 5 + 5);
+      const int rank = e[0];
+      bool ok = rank >= 0 && rank <= 2;
+      if (ok && rank == 0) e = g;
+      if (ok && rank >= 1) ok = e[1] >= 0 && e[1] < ns && e[3] >= ns && e[3] < nmo;
+      if (ok && rank == 2) ok = e[2] > e[1] && e[2] < ns && e[4] > e[3] && e[4] < nmo;
+      if (ok && rank == 1) { e[2] = -1; e[4] = -1; }
+      if (!ok) {
+        delete wf;
+        return fail(QMC_ERR_ARG, "bad excitation record of determinant " + std::to_string(n));
+      }
+      auto it = seen.find(e);
+      int idx;
+      if (it == seen.end()) {
+        idx = (int)seen.size();
+        if (idx >= kMaxExc) {
+          delete wf;
+          return fail(QMC_ERR_UNSUPPORTED, "too many distinct excitations");
+        }
+        seen[e] = idx;
+        for (int k = 0; k < 5; ++k) exc[(s * kMaxExc + idx) * 5 + k] = e[k];
+      } else {
+        idx = it->second;
+      }
+      det_idx[2 * n + s] = idx;
+      if (rank >= 1) { h_lo = std::min(h_lo, e[1]); p_hi = std::max(p_hi, e[3] + 1); }
+      if (rank == 2) { p_hi = std::max(p_hi, e[4] + 1); }
+    }
+    d.n_exc[s] = (int)seen.size();
+    d.h_lo[s] = h_lo;
+    d.p_hi[s] = p_hi;
+    d.nh[s] = ns - h_lo;
+    d.nv[s] = p_hi - ns;
+  }
+  d.n_det = dets->n_det;
+  d.tab_elems = 2 * (d.nh[0] * d.nv[0] + d.nh[1] * d.nv[1]);
+  if (d.tab_elems * 64 * 8 > 200 * 1024) {
+    delete wf;
+    return fail(QMC_ERR_UNSUPPORTED, "excitation tables exceed shared memory");
+  }
+
+  // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
+  d.k_pad = tc ? (int)round_up(nao, 8) : 0;
+  std::vector<uint32_t> tc_hi, tc_lo;
+  if (tc) {
+    tc_hi.assign((size_t)16 * d.k_pad, 0u);
+    tc_lo.assign((size_t)16 * d.k_pad, 0u);
+    for (int m = 0; m < 16; ++m)
+      for (int b = 0; b < d.k_pad; ++b) {
+        const float v = (m < nmo && b < nao) ? mo32[(size_t)b * nmo + m] : 0.0f;
+        const uint32_t hi = tf32_hi_bits(v);
+        const float lo = v - bits_f(hi);
+        uint32_t lo_bits;
+        std::memcpy(&lo_bits, &lo, 4);
+        const size_t off = core_offset_words(m, b, d.k_pad);
+        tc_hi[off] = hi;
+        tc_lo[off] = tf32_hi_bits(bits_f(lo_bits));
+      }
+  }
+
+  // ---- upload everything in one blob
+  DeviceGuard guard(wf->device);
+  std::vector<std::pair<const void*, size_t>> parts = {
+      {shells.data(), sizeof(ShellDev) * shells.size()}, {ao_pow.data(), sizeof(int) * nao},
+      {mo64.data(), sizeof(double) * mo64.size()},       {mo32.data(), sizeof(float) * mo32.size()},
+      {exc.data(), sizeof(int) * exc.size()},           {det_idx.data(), sizeof(int) * det_idx.size()},
+      {dets->weight, sizeof(double) * dets->n_det},      {tc_hi.data(), sizeof(uint32_t) * tc_hi.size()},
+      {tc_lo.data(), sizeof(uint32_t) * tc_lo.size()}};
+  size_t total = 0;
+  for (auto& p : parts) total += align256(p.second);
+  cudaError_t e = cudaMalloc(&wf->blob, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete wf;
+    return fail(QMC_ERR_OOM, std::string("table allocation: ") + cudaGetErrorString(e));
+  }
+  std::vector<char*> ptr;
+  char* base = static_cast<char*>(wf->blob);
+  for (auto& p : parts) {
+    ptr.push_back(base);
+    if (p.second) {
+      e = cudaMemcpy(base, p.first, p.second, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        cudaFree(wf->blob);
+        delete wf;
+        return cuda_fail(e, "table upload");
+      }
+    }
+    base += align256(p.second);
+  }
+  d.shells = reinterpret_cast<const ShellDev*>(ptr[0]);
+  d.ao_pow = reinterpret_cast<const int*>(ptr[1]);
+  d.mo64 = reinterpret_cast<const double*>(ptr[2]);
+  d.mo32 = reinterpret_cast<const float*>(ptr[3]);
+  d.exc = reinterpret_cast<const int*>(ptr[4]);
+  d.det_idx = reinterpret_cast<const int*>(ptr[5]);
+  d.det_w = reinterpret_cast<const double*>(ptr[6]);
+  d.mo_tc_hi = reinterpret_cast<const uint32_t*>(ptr[7]);
+  d.mo_tc_lo = reinterpret_cast<const uint32_t*>(ptr[8]);
+  *out = wf;
+  return QMC_OK;
+}
+
+void qmc_destroy_wf(qmc_wf* wf) {
+  if (!wf) return;
+  {
+    DeviceGuard guard(wf->device);
+    if (wf->blob) cudaFree(wf->blob);
+    if (wf->ws) cudaFree(wf->ws);
+    if (wf->stage) cudaFree(wf->stage);
+  }
+  delete wf;
+}
+
+qmc_status qmc_set_geometry(qmc_wf* wf, const double* xyz) {
+  if (!wf || !xyz) return fail(QMC_ERR_ARG, "null argument");
+  for (int a = 0; a < wf->dev.n_atom; ++a)
+    for (int k = 0; k < 3; ++k) wf->dev.atom_xyz[a][k] = xyz[3 * a + k];
+  wf->dev.vnn = vnn_of(wf->dev);
+  wf->atom_xyz.assign(xyz, xyz + 3 * wf->dev.n_atom);
+  return QMC_OK;
+}
+
+size_t qmc_workspace_size(const qmc_wf* wf, int64_t n_walkers) {
+  if (!wf || n_walkers < 0) return 0;
+  return workspace_bytes(wf, n_walkers);
+}
+
+qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[6]) {
+  if (!wf || !n_param) return fail(QMC_ERR_ARG, "null argument");
+  int64_t o[6];
+  o[0] = 0;
+  o[1] = o[0] + wf->n_prim;
+  o[2] = o[1] + (int64_t)wf->dev.n_ao * wf->dev.n_mo;
+  o[3] = o[2] + wf->dev.n_det;
+  o[4] = o[3] + 1;
+  o[5] = o[4] + 1;
+  *n_param = o[5];
+  if (offsets)
+    for (int k = 0; k < 6; ++k) offsets[k] = o[k];
+  return QMC_OK;
+}
+
+static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                            int* err_flag, bool kinetic, double* e_loc, double* log_psi, cudaStream_t st) {
+  const WfDev& d = wf->dev;
+  qmc_status s = launch_status(launch_jastrow(d, wf->precision, walkers, W, ldw, ws, kinetic, st), "jastrow");
+  if (s) return s;
+  const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
+  const int nch = kinetic ? 2 : 1;
+  if (tc) {
+    s = launch_status(cudaMemsetAsync(err_flag, 0, sizeof(int), st), "error flag reset");
+    if (s) return s;
+  }
+  s = launch_status(tc ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, ws, nch, err_flag, st)
+                       : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, ws, nch, st),
+                    "ao_mo");
+  if (s) return s;
+  return launch_status(launch_det(d, wf->precision, W, ws, kinetic, e_loc, log_psi, st), "det");
+}
+
+qmc_status qmc_local_energy(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_loc,
+                            double* log_psi, void* workspace, size_t workspace_bytes_, void* stream) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  if (n_walkers < 0 || ldw < n_walkers) return fail(QMC_ERR_ARG, "bad walker count or leading dimension");
+  if (n_walkers == 0) return QMC_OK;
+  if (!walkers || !e_loc) return fail(QMC_ERR_ARG, "null walkers or e_loc");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  void* base;
+  qmc_status s = get_workspace(wf, n_walkers, workspace, workspace_bytes_, &base);
+  if (s) return s;
+  int* err_flag;
+  Workspace ws = carve(wf, base, n_walkers, &err_flag);
+  return eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, log_psi,
+                   static_cast<cudaStream_t>(stream));
+}
+
+qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_walkers, double* e_loc,
+                                 double* log_psi, void* stream) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  if (n_walkers < 0) return fail(QMC_ERR_ARG, "bad walker count");
+  if (n_walkers == 0) return QMC_OK;
+  if (!walkers || !e_loc) return fail(QMC_ERR_ARG, "null walkers or e_loc");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t W = n_walkers;
+  const size_t in_bytes = sizeof(double) * 3 * wf->dev.n_elec * W;
+  const size_t need = align256(in_bytes) + 2 * align256(sizeof(double) * W);
+  double *d_in, *d_e, *d_lp;
+  {
+    std::lock_guard<std::mutex> lock(wf->mu);
+    DeviceGuard guard(wf->device);
+    if (wf->stage_bytes < need) {
+      if (wf->stage) cudaFree(wf->stage);
+      wf->stage = nullptr;
+      wf->stage_bytes = 0;
+      cudaError_t e = cudaMalloc(&wf->stage, need);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QMC_ERR_OOM, std::string("staging allocation: ") + cudaGetErrorString(e));
+      }
+      wf->stage_bytes = need;
+    }
+    char* p = reinterpret_cast<char*>(wf->stage);
+    d_in = reinterpret_cast<double*>(p);
+    d_e = reinterpret_cast<double*>(p + align256(in_bytes));
+    d_lp = reinterpret_cast<double*>(p + align256(in_bytes) + align256(sizeof(double) * W));
+    cudaError_t e = cudaMemcpyAsync(d_in, walkers, in_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "walker upload");
+  }
+  qmc_status s = qmc_local_energy(wf, d_in, W, W, d_e, log_psi ? d_lp : nullptr, nullptr, 0, stream);
+  if (s) return s;
+  DeviceGuard guard(wf->device);
+  cudaError_t e = cudaMemcpyAsync(e_loc, d_e, sizeof(double) * W, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && log_psi) e = cudaMemcpyAsync(log_psi, d_lp, sizeof(double) * W, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? QMC_OK : cuda_fail(e, "result download");
+}
+
+qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_steps, double step,
+                      uint64_t seed, uint64_t first_walker, uint64_t step_offset, double* log_psi,
+                      int64_t* n_accept, void* workspace, size_t workspace_bytes_, void* stream) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  if (n_walkers < 0 || ldw < n_walkers || n_steps < 0) return fail(QMC_ERR_ARG, "bad sizes");
+  if (n_walkers == 0) return QMC_OK;
+  if (!walkers) return fail(QMC_ERR_ARG, "null walkers");
+  if (!(step > 0.0) || !std::isfinite(step)) return fail(QMC_ERR_ARG, "step must be positive and finite");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  void* base;
+  qmc_status s = get_workspace(wf, n_walkers, workspace, workspace_bytes_, &base);
+  if (s) return s;
+  int* err_flag;
+  Workspace ws = carve(wf, base, n_walkers, &err_flag);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, false, nullptr, ws.lp, st);
+  if (s) return s;
+  Workspace wp = ws;  // value path on the proposals: walkers = prop, ldw = ldm
+  for (int t = 0; t < n_steps; ++t) {
+    const uint64_t g = step_offset + (uint64_t)t;
+    s = launch_status(launch_propose(wf->dev, walkers, n_walkers, ldw, ws, step, seed, first_walker, g, st),
+                      "propose");
+    if (s) return s;
+    s = eval_path(wf, ws.prop, n_walkers, ws.ldm, wp, err_flag, false, nullptr, ws.lp_new, st);
+    if (s) return s;
+    s = launch_status(launch_accept(wf->dev, walkers, n_walkers, ldw, ws, seed, first_walker, g, n_accept, st),
+                      "accept");
+    if (s) return s;
+  }
+  if (log_psi) {
+    cudaError_t e = cudaMemcpyAsync(log_psi, ws.lp, sizeof(double) * n_walkers, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "log_psi copy");
+  }
+  return QMC_OK;
+}
+
+const char* qmc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

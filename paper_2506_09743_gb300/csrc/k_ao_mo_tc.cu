@@ -1,0 +1,266 @@
+// AO evaluation fused with the AO->MO contraction on the 5th-generation
+// tensor cores (tcgen05, sm_103a).  Mixed forms only.
+//
+// CTA = 256 threads, 128 walkers x one electron.  Each walker row is computed
+// by two threads (they split the shells); the FP32 AO channels are written
+// into shared memory as the MMA A operand, split into TF32 high and low parts
+//     a = a_hi + a_lo,  a_hi = rna_tf32(a),  a_lo = rna_tf32(a - a_hi),
+// and one thread issues, per channel c (value / kinetic operator) and K step,
+//     D_c += A_c,hi B_hi + A_c,hi B_lo + A_c,lo B_hi        (kind::tf32)
+// with M = 128 rows (walkers), N = 16 (MOs, padded), K = 8 per instruction,
+// accumulating in FP32 in tensor memory (two 16-column accumulators).  The
+// dropped a_lo b_lo term and the TF32 rounding of the low parts leave an
+// error of order 2^-21 relative to |a||b|, i.e. FP32-level accuracy.
+// B = MO^T (scaled by the AO angular factors) is prepared on the host in the
+// same core-matrix layout and copied into shared memory per CTA.
+//
+// Shared-memory operand layout (K-major, no swizzle): 8-row x 16-byte core
+// matrices; element (row, k) at byte
+//     (row / 8) * SBO + (k / 4) * 128 + (row % 8) * 16 + (k % 4) * 4,
+// LBO = 128 B (next core matrix along K) and SBO = (k_pad / 4) * 128 B (next
+// 8-row group).
+//
+// The MMA completion is signalled by tcgen05.commit on an mbarrier; the wait
+// is bounded (about one second), after which the kernel raises an error flag
+// instead of hanging.
+#include "ao_eval.cuh"
+
+namespace qmc {
+
+namespace {
+
+constexpr int kRows = 128;
+constexpr int kThreads = 256;
+constexpr int kNPad = 16;
+constexpr uint32_t kTmemCols = 32;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// SM100 shared-memory matrix descriptor, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = 16, M = 128.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kNPad >> 3) << 17) |
+                                ((uint32_t)(kRows >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdescTf32), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+  const long long t0 = clock64();
+  for (int it = 0; it < (1 << 24); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) break;  // ~1 s at 2 GHz
+  }
+  return false;
+}
+
+}  // namespace
+
+template <int NCH>
+__global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double* __restrict__ walkers, int64_t W,
+                                                         int64_t ldw, const float* __restrict__ gradJ,
+                                                         float* __restrict__ mo_out, int64_t ldm,
+                                                         int* __restrict__ err_flag) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int kp = wf.k_pad;
+  const size_t tile_words = (size_t)kRows * kp;
+  uint32_t* A = reinterpret_cast<uint32_t*>(smem_raw);                // [NCH][2][128][kp]
+  uint32_t* B = A + (size_t)NCH * 2 * tile_words;                     // [2][16][kp]
+  ShellDev* sh_s = reinterpret_cast<ShellDev*>(B + 2 * kNPad * kp);  // [n_shell]
+  int* pow_s = reinterpret_cast<int*>(sh_s + wf.n_shell);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(pow_s + ((wf.n_ao + 3) & ~3));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  for (int k = tid; k < 2 * kNPad * kp; k += kThreads)
+    B[k] = k < kNPad * kp ? wf.mo_tc_hi[k] : wf.mo_tc_lo[k - kNPad * kp];
+  for (int k = tid; k < wf.n_shell * (int)(sizeof(ShellDev) / 4); k += kThreads)
+    reinterpret_cast<int*>(sh_s)[k] = reinterpret_cast<const int*>(wf.shells)[k];
+  for (int k = tid; k < wf.n_ao; k += kThreads) pow_s[k] = wf.ao_pow[k];
+  __syncthreads();
+
+  // ---- AO channels -> A operand (TF32 hi / lo) in shared memory
+  const int row = tid & (kRows - 1), half = tid >> 7;
+  const int64_t w = (int64_t)blockIdx.x * kRows + row;
+  const int i = blockIdx.y;
+  const bool live = w < W;
+  auto put = [&](int ch, int k, float v) {
+    const size_t off = (size_t)(row / 8) * (kp / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4 + (k % 4);
+    const uint32_t hi = tf32_rna(v);
+    const float lo = v - __uint_as_float(hi);
+    A[(size_t)(ch * 2 + 0) * tile_words + off] = hi;
+    A[(size_t)(ch * 2 + 1) * tile_words + off] = tf32_rna(lo);
+  };
+  {
+    double rx = 0.0, ry = 0.0, rz = 0.0;
+    float gjx = 0.f, gjy = 0.f, gjz = 0.f;
+    if (live) {
+      rx = walkers[(int64_t)(3 * i) * ldw + w];
+      ry = walkers[(int64_t)(3 * i + 1) * ldw + w];
+      rz = walkers[(int64_t)(3 * i + 2) * ldw + w];
+      if (NCH == 2) {
+        gjx = gradJ[(int64_t)(3 * i) * ldm + w];
+        gjy = gradJ[(int64_t)(3 * i + 1) * ldm + w];
+        gjz = gradJ[(int64_t)(3 * i + 2) * ldm + w];
+      }
+    }
+    const int s_begin = half == 0 ? 0 : wf.shell_split;
+    const int s_end = half == 0 ? wf.shell_split : wf.n_shell;
+    int cur_atom = -1;
+    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, rho = 0.f, irho = 0.f;
+    float px[5], py[5], pz[5];
+    for (int s = s_begin; s < s_end; ++s) {
+      const ShellDev& sh = sh_s[s];
+      if (sh.atom != cur_atom) {
+        cur_atom = sh.atom;
+        dx = float(rx - wf.atom_xyz[cur_atom][0]);
+        dy = float(ry - wf.atom_xyz[cur_atom][1]);
+        dz = float(rz - wf.atom_xyz[cur_atom][2]);
+        r2 = dx * dx + dy * dy + dz * dz;
+        irho = rsqrtf(r2);
+        rho = r2 * irho;
+        pow_table(dx, px); pow_table(dy, py); pow_table(dz, pz);
+      }
+      float f, g1, f2;
+      shell_radial(sh, r2, rho, irho, f, g1, f2, NCH == 2);
+      const float radial_lap = f2 + float(2 * (sh.l + 1)) * g1;
+      for (int k = 0; k < sh.n_ao; ++k) {
+        const int b = sh.ao_first + k;
+        float P, Px, Py, Pz, lapP;
+        angular(pow_s[b], px, py, pz, P, Px, Py, Pz, lapP, NCH == 2);
+        const float v = live ? P * f : 0.f;
+        put(0, b, v);
+        if (NCH == 2) {
+          const float gx = f * Px + P * g1 * dx, gy = f * Py + P * g1 * dy, gz = f * Pz + P * g1 * dz;
+          const float kin = f * lapP + P * radial_lap + 2.f * (gjx * gx + gjy * gy + gjz * gz);
+          put(1, b, live ? kin : 0.f);
+        }
+      }
+    }
+    if (half == 1)
+      for (int k = wf.n_ao; k < kp; ++k)
+        for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
+  }
+  // generic-proxy shared stores -> visible to the tensor core (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (tid == 0) {
+    const uint32_t lbo = 128, sbo = (uint32_t)(kp / 4) * 128;
+    const uint32_t b_hi = smem_u32(B), b_lo = smem_u32(B + kNPad * kp);
+    for (int ch = 0; ch < NCH; ++ch) {
+      const uint32_t a_hi = smem_u32(A + (size_t)(ch * 2) * tile_words);
+      const uint32_t a_lo = smem_u32(A + (size_t)(ch * 2 + 1) * tile_words);
+      const uint32_t d = tmem + (uint32_t)(ch * kNPad);
+      for (int ks = 0; ks < kp / 8; ++ks) {
+        const uint32_t koff = (uint32_t)ks * 256;  // two core matrices along K
+        mma_tf32(d, smem_desc(a_hi + koff, lbo, sbo), smem_desc(b_hi + koff, lbo, sbo), ks > 0 ? 1u : 0u);
+        mma_tf32(d, smem_desc(a_hi + koff, lbo, sbo), smem_desc(b_lo + koff, lbo, sbo), 1u);
+        mma_tf32(d, smem_desc(a_lo + koff, lbo, sbo), smem_desc(b_hi + koff, lbo, sbo), 1u);
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+  }
+  const bool done = mbar_wait_bounded(smem_u32(mbar), 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!done) {
+    // the accumulators are not trustworthy: poison this tile's outputs
+    if (tid == 0) atomicExch(err_flag, 1);
+    const int ch = tid >> 7;
+    if (ch < NCH && live)
+      for (int m = 0; m < wf.n_mo; ++m) mo_out[((int64_t)(i * NCH + ch) * wf.n_mo + m) * ldm + w] = __int_as_float(0x7fc00000);
+  } else {
+    // ---- epilogue: TMEM -> registers -> MO channels in HBM
+    const int quad = warp & 3, ch = warp >> 2;
+    if (ch < NCH) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ch * kNPad);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int64_t wr = (int64_t)blockIdx.x * kRows + quad * 32 + (tid & 31);
+      if (wr < W) {
+        const int nmo = wf.n_mo;
+#pragma unroll
+        for (int m = 0; m < kNPad; ++m)
+          if (m < nmo) mo_out[((int64_t)(i * NCH + ch) * nmo + m) * ldm + wr] = __uint_as_float(v[m]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+size_t tc_smem_bytes(const WfDev& wf, int nch) {
+  const size_t kp = (size_t)wf.k_pad;
+  size_t b = (size_t)nch * 2 * kRows * kp * 4 + 2 * kNPad * kp * 4;
+  b += sizeof(ShellDev) * wf.n_shell + 4 * (size_t)((wf.n_ao + 3) & ~3) + 16;
+  return b;
+}
+
+cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
+                            const Workspace& ws, int nch, int* err_flag, cudaStream_t st) {
+  if (W == 0) return cudaSuccess;
+  if (prec != QMC_MIXED_TF32) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((W + kRows - 1) / kRows), (unsigned)wf.n_elec);
+  const size_t smem = tc_smem_bytes(wf, nch);
+  const float* gj = static_cast<const float*>(ws.gradJ);
+  float* mo = static_cast<float*>(ws.mo);
+  if (nch == 2) {
+    cudaFuncSetAttribute(k_ao_mo_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ao_mo_tc<2><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, mo, ws.ldm, err_flag);
+  } else {
+    cudaFuncSetAttribute(k_ao_mo_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ao_mo_tc<1><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, mo, ws.ldm, err_flag);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace qmc

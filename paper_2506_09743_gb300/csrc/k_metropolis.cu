@@ -1,0 +1,89 @@
+// Metropolis-Hastings walker step (App. B): Gaussian proposal moving all
+// electrons at once, acceptance min(1, |Psi'/Psi|^2) in log form.
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
+// key (seed lo, seed hi) and counter (block j, walker, step lo, step hi).
+// Block j gives Gaussians 4j..4j+3 by Box-Muller on the word pairs
+// (x0, x1), (x2, x3) with u(x) = (x + 0.5) 2^-32; block ceil(3N/4) word 0 is
+// the acceptance uniform.  Both kernels regenerate their numbers from the
+// counter, so nothing random is stored between them.
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+struct u4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ u4 philox4x32_10(u4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = u4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
+
+__global__ void __launch_bounds__(128) k_propose(int n3, const double* __restrict__ walkers, int64_t W, int64_t ldw,
+                                                 double* __restrict__ prop, int64_t ldm, double step, uint64_t seed,
+                                                 uint64_t first_walker, uint64_t gstep) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const uint32_t wi = (uint32_t)(first_walker + (uint64_t)w);
+  const double two_pi = 6.283185307179586;
+  for (int j = 0; 4 * j < n3; ++j) {
+    const u4 x = philox4x32_10(u4{(uint32_t)j, wi, (uint32_t)gstep, (uint32_t)(gstep >> 32)}, k0, k1);
+    double z[4];
+    const double r1 = sqrt(-2.0 * log(u01(x.x))), r2 = sqrt(-2.0 * log(u01(x.z)));
+    double s1, c1, s2, c2;
+    sincos(two_pi * u01(x.y), &s1, &c1);
+    sincos(two_pi * u01(x.w), &s2, &c2);
+    z[0] = r1 * c1; z[1] = r1 * s1; z[2] = r2 * c2; z[3] = r2 * s2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * j + q;
+      if (k < n3) prop[(int64_t)k * ldm + w] = walkers[(int64_t)k * ldw + w] + step * z[q];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_accept(int n3, double* __restrict__ walkers, int64_t W, int64_t ldw,
+                                                const double* __restrict__ prop, int64_t ldm,
+                                                double* __restrict__ lp, const double* __restrict__ lp_new,
+                                                uint64_t seed, uint64_t first_walker, uint64_t gstep,
+                                                int64_t* __restrict__ n_accept) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const uint32_t wi = (uint32_t)(first_walker + (uint64_t)w);
+  const int nblk = (n3 + 3) / 4;
+  const u4 x = philox4x32_10(u4{(uint32_t)nblk, wi, (uint32_t)gstep, (uint32_t)(gstep >> 32)}, (uint32_t)seed,
+                             (uint32_t)(seed >> 32));
+  const double lnew = lp_new[w], lold = lp[w];
+  if (log(u01(x.x)) < 2.0 * (lnew - lold)) {
+    for (int k = 0; k < n3; ++k) walkers[(int64_t)k * ldw + w] = prop[(int64_t)k * ldm + w];
+    lp[w] = lnew;
+    if (n_accept) n_accept[w] += 1;
+  }
+}
+
+cudaError_t launch_propose(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                           double step, uint64_t seed, uint64_t first_walker, uint64_t gstep, cudaStream_t st) {
+  if (W == 0) return cudaSuccess;
+  k_propose<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(3 * wf.n_elec, walkers, W, ldw, ws.prop, ws.ldm, step,
+                                                          seed, first_walker, gstep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accept(const WfDev& wf, double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                          uint64_t seed, uint64_t first_walker, uint64_t gstep, int64_t* n_accept,
+                          cudaStream_t st) {
+  if (W == 0) return cudaSuccess;
+  k_accept<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(3 * wf.n_elec, walkers, W, ldw, ws.prop, ws.ldm, ws.lp,
+                                                         ws.lp_new, seed, first_walker, gstep, n_accept);
+  return cudaGetLastError();
+}
+
+}  // namespace qmc

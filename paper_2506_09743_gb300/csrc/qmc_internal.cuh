@@ -1,0 +1,89 @@
+// Internal declarations of the GB300 VMC engine (not part of the C ABI).
+//
+// Data layout in HBM (W walkers, ldm = W rounded up to 32):
+//   walkers        double [3N][ldw]            caller-owned, coordinate-major
+//   grad J         TA     [3N][ldm]            Jastrow gradient per electron
+//   jastrow scal.  double [3][ldm]             J, sum_i(lap_i J + |grad_i J|^2), V
+//   MO channels    TA     [N][NCH][n_mo][ldm]  channel 0 = Phi_{i,m},
+//                                              channel 1 = (lap + 2 grad J . grad) Phi_{i,m}
+// with TA = double (FP64 form) or float (other forms).  Every kernel maps
+// consecutive threads to consecutive walkers, so all of these accesses are
+// coalesced.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qmc.h"
+
+namespace qmc {
+
+constexpr int kMaxShells = 128;
+constexpr int kMaxExc = 512;   // unique excitations per spin channel
+constexpr int kMaxDets = 4096;
+
+// One radial function shared by the AOs of a shell (same atom, kind, kn, l
+// and primitives).  Radial normalisation and contraction coefficients are
+// folded into coef; the per-AO angular factor is folded into the MO table.
+struct ShellDev {
+  int atom, kind, kn, l;
+  int n_prim, ao_first, n_ao, pad;
+  double expo[QMC_MAX_PRIM];
+  double coef[QMC_MAX_PRIM];
+};
+
+// Everything a kernel needs, passed by value (pointers are device memory).
+struct WfDev {
+  int n_atom, n_up, n_down, n_elec;
+  int n_ao, n_mo, n_shell, n_det;
+  int n_exc[2];   // unique excitation records per spin (index 0 = ground)
+  int h_lo[2];    // smallest hole index per spin (n_s if none)
+  int p_hi[2];    // one past the largest particle index per spin (n_s if none)
+  int nh[2], nv[2];  // table extents: holes n_s - h_lo, virtuals p_hi - n_s
+  int tab_elems;  // doubles of excitation tables per walker
+  double w0_par, w0_anti, jb, bf_w, vnn;
+  double atom_xyz[QMC_MAX_ATOMS][3];
+  double atom_z[QMC_MAX_ATOMS];
+  const ShellDev* shells;  // [n_shell]
+  const int* ao_pow;       // [n_ao] kx | ky << 4 | kz << 8
+  const double* mo64;      // [n_ao][n_mo] MO coefficients x AO angular factors
+  const float* mo32;       // same, FP32
+  const int* exc;          // [2][kMaxExc][5] rank, h1, h2, p1, p2
+  const int* det_idx;      // [n_det][2] excitation index per spin
+  const double* det_w;     // [n_det]
+  // tensor-core B operand: MO^T split into high and low parts, K-major
+  // core-matrix layout [n_mo_pad=16][k_pad], 32-bit words
+  const uint32_t* mo_tc_hi;
+  const uint32_t* mo_tc_lo;
+  int k_pad;        // AO dimension padded to a multiple of the MMA K step
+  int shell_split;  // tensor-core AO stage: threads of half 0 take shells [0, split)
+};
+
+struct Workspace {
+  int64_t ldm;
+  void* gradJ;     // TA [3N][ldm]
+  double* jscal;   // [3][ldm]
+  void* mo;        // TA [N][NCH][n_mo][ldm]
+  double* prop;    // [3N][ldm] proposed positions (sampling)
+  double* lp;      // [ldm] current log|Psi| (sampling)
+  double* lp_new;  // [ldm] proposed log|Psi| (sampling)
+};
+
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// kernel launchers (return cudaError_t of the launch)
+cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
+                           const Workspace& ws, bool derivs, cudaStream_t st);
+cudaError_t launch_ao_mo_simt(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
+                              const Workspace& ws, int nch, cudaStream_t st);
+cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
+                            const Workspace& ws, int nch, int* err_flag, cudaStream_t st);
+cudaError_t launch_det(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,
+                       double* e_loc, double* log_psi, cudaStream_t st);
+cudaError_t launch_propose(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                           double step, uint64_t seed, uint64_t first_walker, uint64_t gstep, cudaStream_t st);
+cudaError_t launch_accept(const WfDev& wf, double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                          uint64_t seed, uint64_t first_walker, uint64_t gstep, int64_t* n_accept,
+                          cudaStream_t st);
+
+}  // namespace qmc

@@ -1,0 +1,161 @@
+"""GPU parity of qmc_local_energy against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import qmc_inputs as qi
+from oracle import qmc_oracle as O
+
+from gpu_common import fp64_check, mixed_check, oracle_reference
+
+pytestmark = pytest.mark.gpu
+
+MOLS = {
+    "h2": lambda: qi.make_h2(),
+    "lih": lambda: qi.make_lih(),
+    "co": lambda: qi.make_co(),
+}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2506_09743_gb300 as p
+
+    return p
+
+
+def _run(pkg, mol, r, precision, ldw_pad=0):
+    wf = pkg.Wavefunction(mol, precision=precision)
+    x = torch.zeros(3 * mol.n_elec, r.shape[0] + ldw_pad, dtype=torch.float64, device="cuda")
+    x[:, : r.shape[0]] = torch.tensor(qi.to_soa(r), device="cuda")
+    e, lp = wf.local_energy(x, n_walkers=r.shape[0])
+    torch.cuda.synchronize()
+    out = e.cpu().numpy(), lp.cpu().numpy()
+    wf.close()
+    return out
+
+
+# 1000 walkers: several 64/128-walker tiles and a ragged tail
+@pytest.mark.parametrize("name", ["h2", "lih", "co"])
+def test_fp64_parity(pkg, name):
+    mol = MOLS[name]()
+    r = qi.walkers(mol, 1000, seed=21)
+    E_ref, lp_ref, sens = oracle_reference(mol, r)
+    E, lp = _run(pkg, mol, r, "fp64", ldw_pad=7)
+    worst = fp64_check(E, E_ref, sens)
+    assert np.abs(lp - lp_ref)[sens <= 1e4].max() <= 1e-10 * np.maximum(1, np.abs(lp_ref)).max()
+    print(f"{name} fp64 worst rel err {worst:.2e}")
+
+
+@pytest.mark.parametrize("name", ["h2", "lih", "co"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed_tf32"])
+def test_reduced_precision_parity(pkg, name, precision):
+    mol = MOLS[name]()
+    r = qi.walkers(mol, 1000, seed=22)
+    E_ref, lp_ref, sens = oracle_reference(mol, r)
+    E, lp = _run(pkg, mol, r, precision)
+    stats = mixed_check(E, E_ref, sens)
+    print(f"{name} {precision} |dE| median {stats['median']:.2e} p99 {stats['p99']:.2e} max {stats['max']:.2e}")
+
+
+def test_closed_forms_on_gpu(pkg):
+    mol = qi.make_hydrogenic(1.0, 1.0)
+    r = qi.walkers(mol, 333, seed=4)
+    E, _ = _run(pkg, mol, r, "fp64")
+    assert np.abs(E + 0.5).max() < 1e-13
+    he = qi.make_helium(1.6875)
+    r = qi.walkers(he, 257, seed=5)
+    z = 1.6875
+    r1, r2 = np.linalg.norm(r[:, 0], axis=-1), np.linalg.norm(r[:, 1], axis=-1)
+    r12 = np.linalg.norm(r[:, 0] - r[:, 1], axis=-1)
+    ref = -z * z + (z - 2) * (1 / r1 + 1 / r2) + 1 / r12
+    for prec, tol in (("fp64", 1e-12), ("mixed_tf32", 1e-4)):
+        E, _ = _run(pkg, he, r, prec)
+        assert np.abs(E - ref).max() < tol * np.maximum(1, np.abs(ref)).max(), prec
+
+
+@pytest.mark.parametrize("W", [1, 31, 129])
+def test_small_and_ragged_batches(pkg, W):
+    mol = qi.make_co(n_det=20)
+    r = qi.walkers(mol, W, seed=6)
+    E_ref, _, sens = oracle_reference(mol, r)
+    for prec in ("fp64", "mixed_tf32"):
+        E, _ = _run(pkg, mol, r, prec, ldw_pad=3)
+        err = np.abs(E - E_ref)[sens <= 1e3]
+        assert err.max() <= (1e-8 if prec == "fp64" else 2e-4)
+
+
+def test_zero_walkers_is_a_noop(pkg):
+    mol = qi.make_h2()
+    wf = pkg.Wavefunction(mol)
+    x = torch.zeros(6, 4, dtype=torch.float64, device="cuda")
+    e = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+    wf.local_energy(x, n_walkers=0, e_loc=e, log_psi=e)
+    assert e.item() == 7.0
+
+
+def test_caller_workspace_and_too_small_workspace(pkg):
+    from paper_2506_09743_gb300 import QmcError
+
+    mol = qi.make_lih()
+    r = qi.walkers(mol, 300, seed=8)
+    wf = pkg.Wavefunction(mol)
+    x = torch.tensor(qi.to_soa(r), device="cuda")
+    need = wf.workspace_size(300)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    e1, _ = wf.local_energy(x, workspace=ws)
+    e2, _ = wf.local_energy(x)
+    torch.cuda.synchronize()
+    assert torch.equal(e1, e2)
+    with pytest.raises(QmcError) as ei:
+        wf.local_energy(x, workspace=ws[: need // 2])
+    assert "workspace" in str(ei.value)
+
+
+def test_host_entry_point_matches_device(pkg):
+    mol = qi.make_co(n_det=30)
+    r = qi.walkers(mol, 500, seed=9)
+    wf = pkg.Wavefunction(mol, precision="mixed_tf32")
+    soa = np.ascontiguousarray(qi.to_soa(r))
+    e_h, lp_h = wf.local_energy_host(soa, log_psi=np.empty(500))
+    e_d, lp_d = wf.local_energy(torch.tensor(soa, device="cuda"))
+    torch.cuda.synchronize()
+    assert np.array_equal(e_h, e_d.cpu().numpy()) and np.array_equal(lp_h, lp_d.cpu().numpy())
+
+
+def test_full_size_co_sampled_parity(pkg):
+    """CO at its full 262,144-walker size in the launch configuration the
+    benchmark times; 256 sampled walkers checked against the oracle."""
+    mol = qi.make_co()
+    W = qi.WORKLOAD_WALKERS["co"]
+    r = qi.walkers(mol, W, seed=qi.SEED_WALKERS)
+    idx = np.random.default_rng(0).choice(W, size=256, replace=False)
+    E_ref, _, sens = oracle_reference(mol, r[idx])
+    x = torch.tensor(qi.to_soa(r), device="cuda")
+    for prec in ("fp64", "mixed_tf32"):
+        wf = pkg.Wavefunction(mol, precision=prec)
+        e, _ = wf.local_energy(x)
+        torch.cuda.synchronize()
+        E = e.cpu().numpy()
+        assert np.isfinite(E).mean() > 0.999
+        if prec == "fp64":
+            fp64_check(E[idx], E_ref, sens, max_excluded=0.02)
+        else:
+            mixed_check(E[idx], E_ref, sens, max_excluded=0.02)
+        wf.close()
+
+
+def test_set_geometry_matches_fresh_wavefunction(pkg):
+    mol = qi.make_lih()
+    r = qi.walkers(mol, 200, seed=10)
+    stretched = mol.with_bond_scale(1.7)
+    wf = pkg.Wavefunction(mol)
+    wf.set_geometry(stretched.atom_xyz)
+    x = torch.tensor(qi.to_soa(r), device="cuda")
+    e1, _ = wf.local_energy(x)
+    e2, _ = _run(pkg, stretched, r, "fp64")
+    torch.cuda.synchronize()
+    assert np.allclose(e1.cpu().numpy(), e2, rtol=0, atol=0)

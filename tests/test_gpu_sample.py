@@ -1,0 +1,94 @@
+"""GPU Metropolis sampler (qmc_sample) against the oracle chain and physics."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import qmc_inputs as qi
+from oracle import qmc_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2506_09743_gb300 as p
+
+    return p
+
+
+def test_h2_chain_matches_oracle(pkg):
+    """The H2 workload: 1024 walkers, 200 steps of 0.2 bohr.  Same Philox
+    counters on both sides: identical accept decisions, positions equal to
+    rounding of the Box-Muller transcendental functions."""
+    mol = qi.make_h2()
+    r0 = qi.walkers(mol, 1024, seed=qi.SEED_WALKERS)
+    r_ref, lp_ref, acc_ref = O.metropolis(O.Wavefunction(mol), torch.tensor(r0), 200, 0.2, seed=0x5EED)
+    wf = pkg.Wavefunction(mol)
+    x = torch.tensor(qi.to_soa(r0), device="cuda")
+    lp = torch.empty(1024, dtype=torch.float64, device="cuda")
+    acc = torch.zeros(1024, dtype=torch.int64, device="cuda")
+    wf.sample(x, n_steps=200, step=0.2, seed=0x5EED, log_psi=lp, n_accept=acc)
+    torch.cuda.synchronize()
+    r_gpu = qi.from_soa(x.cpu().numpy(), 1024, 2)
+    same = acc.cpu().numpy() == acc_ref.numpy()
+    assert same.mean() >= 0.999, same.mean()
+    d = np.abs(r_gpu - r_ref.numpy()).max(axis=(1, 2))
+    assert np.all(d[same] < 1e-10), d[same].max()
+    assert np.abs(lp.cpu().numpy() - lp_ref.numpy())[same].max() < 1e-10
+
+
+def test_chain_resume_and_batching_on_gpu(pkg):
+    mol = qi.make_lih()
+    r0 = torch.tensor(qi.to_soa(qi.walkers(mol, 300, seed=3)), device="cuda")
+    wf = pkg.Wavefunction(mol)
+    a = r0.clone()
+    wf.sample(a, n_steps=10, step=0.3, seed=42)
+    b = r0.clone()
+    wf.sample(b, n_steps=4, step=0.3, seed=42)
+    wf.sample(b, n_steps=6, step=0.3, seed=42, step_offset=4)
+    c = r0.clone()
+    wf.sample(c[:, :100], n_steps=10, step=0.3, seed=42, n_walkers=100)
+    tail = r0[:, 100:].contiguous()
+    wf.sample(tail, n_steps=10, step=0.3, seed=42, first_walker=100)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert torch.equal(a[:, :100], c[:, :100]) and torch.equal(a[:, 100:], tail)
+
+
+def test_helium_mean_energy_within_3_sigma_gpu(pkg):
+    """He with the optimal 1s(27/16) product: <E> = -(27/16)^2 exactly."""
+    he = qi.make_helium(1.6875)
+    W = 16384
+    wf = pkg.Wavefunction(he)
+    x = torch.tensor(qi.to_soa(qi.walkers(he, W, seed=13)), device="cuda")
+    wf.sample(x, n_steps=300, step=0.5, seed=77)
+    acc = torch.zeros(W, dtype=torch.float64, device="cuda")
+    n_blk = 8
+    for k in range(n_blk):
+        wf.sample(x, n_steps=20, step=0.5, seed=77, step_offset=300 + 20 * k)
+        e, _ = wf.local_energy(x)
+        acc += e
+    torch.cuda.synchronize()
+    per_walker = (acc / n_blk).cpu().numpy()
+    mean = per_walker.mean()
+    err = per_walker.std() / math.sqrt(W)
+    assert abs(mean - (-2.84765625)) < 3 * err, (mean, err)
+
+
+def test_mixed_precision_sampler_runs_and_accepts(pkg):
+    mol = qi.make_co(n_det=100)
+    W = 4096
+    wf = pkg.Wavefunction(mol, precision="mixed_tf32")
+    x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=2)), device="cuda")
+    acc = torch.zeros(W, dtype=torch.int64, device="cuda")
+    lp = torch.empty(W, dtype=torch.float64, device="cuda")
+    wf.sample(x, n_steps=20, step=0.05, seed=9, n_accept=acc, log_psi=lp)
+    torch.cuda.synchronize()
+    rate = acc.double().mean().item() / 20
+    assert 0.3 < rate < 1.0, rate
+    assert torch.isfinite(lp).float().mean().item() > 0.999
