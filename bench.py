@@ -1,0 +1,316 @@
+"""Benchmark: walker local-energy evaluations per second, CO (14 electrons).
+
+Workload: CO, 7 up + 7 down electrons, 58 contracted Cartesian GTOs (5s4p2d
+per atom, 3 primitives), 14 MOs, 100 determinants of the (10e, 12o) active
+space, Pade Jastrow; 262,144 seeded synthetic walkers per GPU.  One step =
+one qmc_local_energy call over the whole batch (Jastrow + Coulomb, AO
+evaluation, AO->MO contraction, reference inverse, excited-determinant
+tables, E_L assembly).  The headline `value` is the mixed form (FP32 AOs,
+tcgen05 TF32x3 AO->MO contraction, FP64 determinants); the plain FP64 form is
+timed on the same walkers and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched with torchrun (one rank per GPU); walkers are independent,
+so every rank evaluates its own batch with no collective on the data path
+(weak scaling) and the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import qmc_inputs as qi  # noqa: E402
+
+METRIC = "walker local-energy evals/s (CO, 14 e-) vs FP64 plain; p99 request latency"
+UNIT = "walker-evals/s"
+WORKLOAD = "CO 14e- 58 GTO 14 MO 100 det, 262144 walkers"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)
+
+
+def det_stage_flops(mol) -> float:
+    """Algorithmic FP64 flops per walker of the determinant stage (FMA = 2):
+    per spin with n electrons, nh holes, nv virtuals: reference inverse 2n^3,
+    Tr(A0^-1 B0) 2n^2, per virtual column 2(2n^2 + nh n); per spin excitation
+    rank 1: 2, rank 2: 12; per determinant 8 (ratio and kinetic numerator)."""
+    tot = 0.0
+    dets = np.asarray(mol.det_exc)
+    for s, n in enumerate((mol.n_up, mol.n_down)):
+        if n == 0:
+            continue
+        ex = dets[:, s, :]
+        ranks = ex[:, 0]
+        holes = [h for row in ex for h in row[1:1 + row[0]]]
+        parts = [p for row in ex for p in row[3:3 + row[0]]]
+        nh = n - min(holes) if holes else 0
+        nv = max(parts) + 1 - n if parts else 0
+        tot += 2 * n ** 3 + 2 * n * n + nv * 2 * (2 * n * n + nh * n)
+        uniq = {tuple(row) for row in ex}
+        tot += sum(2 if r[0] == 1 else 12 if r[0] == 2 else 0 for r in uniq)
+    return tot + 8 * len(dets)
+
+
+def ao_mo_stage_flops(mol) -> float:
+    """Algorithmic flops per walker of the AO->MO contraction (two channels)."""
+    return 2.0 * 2 * mol.n_elec * mol.n_ao * mol.n_mo
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n_walkers: int = 16384):
+    """The oracle (plain FP64 CPU) on a bounded sample of the same workload."""
+    import torch
+
+    from oracle import qmc_oracle as O
+
+    mol = qi.make_co()
+    r = torch.tensor(qi.walkers(mol, n_walkers, seed=qi.SEED_WALKERS))
+    wf = O.Wavefunction(mol)
+    O.local_energy(wf, r[:64])  # warm the allocator
+    t0 = time.perf_counter()
+    O.local_energy(wf, r)
+    dt = time.perf_counter() - t0
+    return {"value": n_walkers / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n_walkers} of the 262144 CO walkers (same seed), one evaluation, {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    """--impl reference: the oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import torch
+
+    from oracle import qmc_oracle as O
+
+    mol = qi.make_co()
+    per_step = 2048
+    wf = O.Wavefunction(mol)
+    total = args.warmup + args.steps
+    r = torch.tensor(qi.walkers(mol, per_step * max(1, total), seed=qi.SEED_WALKERS))
+    times = []
+    for k in range(total):
+        t0 = time.perf_counter()
+        O.local_energy(wf, r[k * per_step:(k + 1) * per_step])
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = per_step / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "walkers_per_step": per_step, "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": f"{per_step} CO walkers per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--walkers", type=int, default=qi.WORKLOAD_WALKERS["co"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2506_09743_gb300 import Wavefunction
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    mol = qi.make_co()
+    W = args.walkers
+    r = qi.walkers(mol, W, seed=qi.SEED_WALKERS + rank)
+    soa = np.ascontiguousarray(qi.to_soa(r))
+    x = torch.tensor(soa, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def timed_device(wf, steps, warmup):
+        e = torch.empty(W, dtype=torch.float64, device="cuda")
+        lp = torch.empty(W, dtype=torch.float64, device="cuda")
+        wf.set_timing(True)
+        for _ in range(warmup):
+            wf.local_energy(x, e_loc=e, log_psi=lp)
+        barrier()
+        step_ms, stage = [], []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with ClockSampler(local) as clk:
+            for k in range(steps):
+                flush.zero_()  # evict L2 between steps (outside the timed events)
+                ev[k][0].record(stream)
+                wf.local_energy(x, e_loc=e, log_psi=lp)
+                ev[k][1].record(stream)
+                stage.append(wf.last_stage_ms())  # waits for this step; outside the events
+            barrier()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        wf.set_timing(False)
+        finite = float(torch.isfinite(e).double().mean().item())
+        return float(np.sum(step_ms)), np.mean(np.asarray(stage), axis=0), finite, clk.summary()
+
+    wf_mixed = Wavefunction(mol, precision="mixed_tf32", device=local)
+    wf_fp64 = Wavefunction(mol, precision="fp64", device=local)
+
+    tot_mixed, stage_mixed, fin_mixed, clocks = timed_device(wf_mixed, args.steps, args.warmup)
+    tot_fp64, stage_fp64, fin_fp64, clocks64 = timed_device(wf_fp64, max(3, args.steps // 4), 3)
+    k64 = max(3, args.steps // 4)
+    tot_mixed = max_over_ranks(tot_mixed)
+    tot_fp64 = max_over_ranks(tot_fp64)
+    ms_step = tot_mixed / args.steps
+    value = world * W * args.steps / (tot_mixed / 1e3)
+    value_fp64 = world * W * k64 / (tot_fp64 / 1e3)
+
+    # end to end through the host-buffer C call (pinned host memory)
+    pin_in = torch.from_numpy(soa).pin_memory()
+    pin_e = torch.empty(W, dtype=torch.float64).pin_memory()
+    pin_lp = torch.empty(W, dtype=torch.float64).pin_memory()
+    in_np, e_np, lp_np = pin_in.numpy(), pin_e.numpy(), pin_lp.numpy()
+    for _ in range(args.warmup):
+        wf_mixed.local_energy_host(in_np, e_np, lp_np, stream=stream)
+    barrier()
+    e2e_steps = max(3, args.steps // 2)
+    t_e2e = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        wf_mixed.local_energy_host(in_np, e_np, lp_np, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        t_e2e.append(a.elapsed_time(b))
+    barrier()
+    e2e_ms = max_over_ranks(float(np.sum(t_e2e)))
+    e2e_value = world * W * e2e_steps / (e2e_ms / 1e3)
+
+    flops_det = det_stage_flops(mol) * W
+    det_ms = float(stage_mixed[2])
+    achieved = flops_det / (det_ms / 1e3) / 1e12
+    flops_ao64 = ao_mo_stage_flops(mol) * W
+    roofline = {"kernel": "k_det (determinants, tables, E_L; mixed form)", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": None,
+                "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "flops_per_launch": flops_det, "kernel_ms": det_ms}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 AO / tf32x3 MMA / f64 det", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "walkers_per_gpu": W, "precision": "mixed_tf32",
+                   "l2": "flushed (256 MB write) between timed steps, outside the timed events",
+                   "parallelism": f"walker shards x{world}, no data-path collective"},
+        "fp64_plain": {"value": value_fp64, "ms_per_step": tot_fp64 / k64,
+                       "stage_ms": [float(v) for v in stage_fp64], "finite_frac": fin_fp64,
+                       "ao_mo_fp64_tflops": flops_ao64 / (float(stage_fp64[1]) / 1e3) / 1e12},
+        "mixed_vs_fp64": value / value_fp64,
+        "stage_ms": {"jastrow_coulomb": float(stage_mixed[0]), "ao_mo_tcgen05": float(stage_mixed[1]),
+                     "det_eloc": float(stage_mixed[2])},
+        "finite_frac": fin_mixed,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(soa.nbytes),
+                "d2h_bytes_per_step": int(2 * 8 * W), "api": "qmc_local_energy_host (pinned host buffers)"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+        "p99_request_latency_ms": None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

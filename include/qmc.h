@@ -194,6 +194,18 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
  * [4] backflow w, [5] = n_param.  offsets may be NULL. */
 qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[6]);
 
+/* Per-stage device timing (tracing aid; the paper has no counterpart).  When
+ * enabled, every qmc_local_energy / qmc_sample evaluation records CUDA events
+ * on its stream around its three stages: [0] Jastrow and Coulomb terms,
+ * [1] AO evaluation and AO->MO contraction, [2] determinants, tables and
+ * local-energy assembly.  Off by default (no events recorded). */
+qmc_status qmc_set_timing(qmc_wf* wf, int32_t enable);
+
+/* Milliseconds of each stage of the last timed evaluation on this wf
+ * (ms[0..n-1], n <= 3).  Waits for that evaluation's last event.
+ * QMC_ERR_ARG if timing was never enabled or nothing was timed yet. */
+qmc_status qmc_last_stage_ms(qmc_wf* wf, float* ms, int32_t n);
+
 /* Message of the last failed call on this thread ("" if none yet).  The
  * pointer stays valid until the next library call on the same thread. */
 const char* qmc_last_error(void);

@@ -112,6 +112,16 @@ class Wavefunction:
         _lib.check(self._lib.qmc_param_layout(self._h, ctypes.byref(n), off))
         return int(n.value), [int(v) for v in off]
 
+    def set_timing(self, enable: bool = True):
+        """Record per-stage CUDA events on the call's stream (tracing aid)."""
+        _lib.check(self._lib.qmc_set_timing(self._h, 1 if enable else 0))
+
+    def last_stage_ms(self):
+        """[Jastrow+Coulomb, AO+MO, det+assembly] ms of the last timed call."""
+        ms = (ctypes.c_float * 3)()
+        _lib.check(self._lib.qmc_last_stage_ms(self._h, ms, 3))
+        return [float(v) for v in ms]
+
     # ------------------------------------------------------------------
     def local_energy(self, walkers, n_walkers: int | None = None, e_loc=None, log_psi=None, workspace=None,
                      stream=None, want_log_psi: bool = True):

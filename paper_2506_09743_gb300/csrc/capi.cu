@@ -75,6 +75,10 @@ struct qmc_wf {
   size_t ws_bytes = 0;
   double* stage = nullptr;
   size_t stage_bytes = 0;
+  // optional per-stage timing events
+  bool timing = false;
+  bool timed_once = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::mutex mu;
 };
 
@@ -91,7 +95,8 @@ size_t workspace_bytes(const qmc_wf* wf, int64_t W) {
   size_t b = 0;
   b += align256(3 * N * ldm * ta);                     // gradJ
   b += align256(3 * ldm * sizeof(double));             // jscal
-  b += align256((size_t)N * 2 * wf->dev.n_mo * ldm * ta);  // MO channels
+  const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
+  b += align256((size_t)N * 2 * mo_row_pad(wf->dev.n_mo, tc) * ldm * ta);  // MO channels
   b += align256(3 * N * ldm * sizeof(double));         // proposals
   b += 2 * align256(ldm * sizeof(double));             // lp, lp_new
   b += align256(sizeof(int));                          // device error flag
@@ -106,7 +111,9 @@ Workspace carve(const qmc_wf* wf, void* base, int64_t W, int** err_flag) {
   char* p = static_cast<char*>(base);
   ws.gradJ = p; p += align256(3 * N * ws.ldm * ta);
   ws.jscal = reinterpret_cast<double*>(p); p += align256(3 * ws.ldm * sizeof(double));
-  ws.mo = p; p += align256((size_t)N * 2 * wf->dev.n_mo * ws.ldm * ta);
+  const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
+  ws.nmp = mo_row_pad(wf->dev.n_mo, tc);
+  ws.mo = p; p += align256((size_t)N * 2 * ws.nmp * ws.ldm * ta);
   ws.prop = reinterpret_cast<double*>(p); p += align256(3 * N * ws.ldm * sizeof(double));
   ws.lp = reinterpret_cast<double*>(p); p += align256(ws.ldm * sizeof(double));
   ws.lp_new = reinterpret_cast<double*>(p); p += align256(ws.ldm * sizeof(double));
@@ -258,12 +265,16 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
       ang[b] = std::sqrt(dfact(2 * l + 1) / (4.0 * M_PI * df));
       sh.expo[0] = zeta;
       sh.coef[0] = basis->prim_coef[s0] * std::pow(2.0 * zeta, n + 0.5) / std::sqrt(fact(2 * n));
+      sh.expo_f[0] = (float)sh.expo[0];
+      sh.coef_f[0] = (float)sh.coef[0];
     } else {
       ang[b] = 1.0 / std::sqrt(df);
       for (int p = s0; p < s1; ++p) {
         const double al = basis->prim_exp[p];
         sh.expo[p - s0] = al;
         sh.coef[p - s0] = basis->prim_coef[p] * std::pow(2.0 * al / M_PI, 0.75) * std::pow(4.0 * al, 0.5 * l);
+        sh.expo_f[p - s0] = (float)sh.expo[p - s0];
+        sh.coef_f[p - s0] = (float)sh.coef[p - s0];
       }
     }
     bool merged = false;
@@ -283,11 +294,12 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
     return fail(QMC_ERR_UNSUPPORTED, "too many shells");
   }
   d.n_shell = (int)shells.size();
-  {  // balance the AO count between the two thread halves of the tensor-core AO stage
-    int acc = 0;
-    d.shell_split = d.n_shell;
-    for (int s = 0; s < d.n_shell; ++s) {
-      if (2 * acc >= nao) { d.shell_split = s; break; }
+  {  // balance the AO count between the four thread parts of the tensor-core AO stage
+    int acc = 0, part = 1;
+    d.shell_part[0] = 0;
+    for (int q = 1; q <= 4; ++q) d.shell_part[q] = d.n_shell;
+    for (int s = 0; s < d.n_shell && part < 4; ++s) {
+      while (part < 4 && 4 * acc >= part * nao) d.shell_part[part++] = s;
       acc += shells[s].n_ao;
     }
   }
@@ -346,9 +358,12 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
   }
   d.n_det = dets->n_det;
   d.tab_elems = 2 * (d.nh[0] * d.nv[0] + d.nh[1] * d.nv[1]);
-  if (d.tab_elems * 64 * 8 > 200 * 1024) {
-    delete wf;
-    return fail(QMC_ERR_UNSUPPORTED, "excitation tables exceed shared memory");
+  {
+    const int ns = std::max(nup, ndn);
+    if (det_smem_bytes(d, ns, det_team_size(d), true) > 227 * 1024) {
+      delete wf;
+      return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
+    }
   }
 
   // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
@@ -420,6 +435,8 @@ void qmc_destroy_wf(qmc_wf* wf) {
     if (wf->blob) cudaFree(wf->blob);
     if (wf->ws) cudaFree(wf->ws);
     if (wf->stage) cudaFree(wf->stage);
+    for (auto& e : wf->ev)
+      if (e) cudaEventDestroy(e);
   }
   delete wf;
 }
@@ -453,11 +470,17 @@ qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[
   return QMC_OK;
 }
 
+static void mark(qmc_wf* wf, int k, cudaStream_t st) {
+  if (wf->timing) cudaEventRecord(wf->ev[k], st);
+}
+
 static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                             int* err_flag, bool kinetic, double* e_loc, double* log_psi, cudaStream_t st) {
   const WfDev& d = wf->dev;
+  mark(wf, 0, st);
   qmc_status s = launch_status(launch_jastrow(d, wf->precision, walkers, W, ldw, ws, kinetic, st), "jastrow");
   if (s) return s;
+  mark(wf, 1, st);
   const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
   const int nch = kinetic ? 2 : 1;
   if (tc) {
@@ -468,7 +491,12 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
                        : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, ws, nch, st),
                     "ao_mo");
   if (s) return s;
-  return launch_status(launch_det(d, wf->precision, W, ws, kinetic, e_loc, log_psi, st), "det");
+  mark(wf, 2, st);
+  s = launch_status(launch_det(d, wf->precision, W, ws, kinetic, e_loc, log_psi, st), "det");
+  if (s) return s;
+  mark(wf, 3, st);
+  if (wf->timing) wf->timed_once = true;
+  return QMC_OK;
 }
 
 qmc_status qmc_local_energy(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_loc,
@@ -564,6 +592,29 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
     if (e != cudaSuccess) return cuda_fail(e, "log_psi copy");
   }
   return QMC_OK;
+}
+
+qmc_status qmc_set_timing(qmc_wf* wf, int32_t enable) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  if (enable && !wf->ev[0])
+    for (auto& e : wf->ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return cuda_fail(r, "event create");
+    }
+  wf->timing = enable != 0;
+  return QMC_OK;
+}
+
+qmc_status qmc_last_stage_ms(qmc_wf* wf, float* ms, int32_t n) {
+  if (!wf || !ms || n < 0 || n > 3) return fail(QMC_ERR_ARG, "bad argument");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  if (!wf->timed_once) return fail(QMC_ERR_ARG, "no timed evaluation yet");
+  DeviceGuard guard(wf->device);
+  cudaError_t r = cudaEventSynchronize(wf->ev[3]);
+  for (int k = 0; k < n && r == cudaSuccess; ++k) r = cudaEventElapsedTime(&ms[k], wf->ev[k], wf->ev[k + 1]);
+  return r == cudaSuccess ? QMC_OK : cuda_fail(r, "event timing");
 }
 
 const char* qmc_last_error(void) { return g_err.c_str(); }

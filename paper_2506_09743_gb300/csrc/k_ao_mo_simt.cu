@@ -51,9 +51,7 @@ __global__ void __launch_bounds__(128) k_ao_mo_simt(WfDev wf, const double* __re
     const ShellDev& sh = sh_s[s];
     if (sh.atom != cur_atom) {
       cur_atom = sh.atom;
-      dx = T(rx - wf.atom_xyz[cur_atom][0]);
-      dy = T(ry - wf.atom_xyz[cur_atom][1]);
-      dz = T(rz - wf.atom_xyz[cur_atom][2]);
+      displacement(rx, ry, rz, wf.atom_xyz[cur_atom], dx, dy, dz);
       r2 = dx * dx + dy * dy + dz * dz;
       irho = T(1) / sqrt(r2);
       rho = r2 * irho;
@@ -81,13 +79,12 @@ __global__ void __launch_bounds__(128) k_ao_mo_simt(WfDev wf, const double* __re
       }
     }
   }
-  const int nmo = wf.n_mo;
+  // walker-major MO block: row (w, i, channel) of NMO entries
+  T* dst = mo_out + ((size_t)w * wf.n_elec + i) * NCH * NMO;
 #pragma unroll
   for (int m = 0; m < NMO; ++m) {
-    if (m < nmo) {
-      mo_out[((int64_t)(i * NCH) * nmo + m) * ldm + w] = acc0[m];
-      if (NCH == 2) mo_out[((int64_t)(i * NCH + 1) * nmo + m) * ldm + w] = acc1[m];
-    }
+    dst[m] = acc0[m];
+    if (NCH == 2) dst[NMO + m] = acc1[m];
   }
 }
 
@@ -112,6 +109,7 @@ static cudaError_t launch_t(const WfDev& wf, const double* walkers, int64_t W, i
     }                                                                                                       \
     return cudaGetLastError();                                                                              \
   }
+  if (ws.nmp != mo_row_pad(wf.n_mo, false)) return cudaErrorInvalidValue;
   QMC_AOMO(8)
   QMC_AOMO(16)
   QMC_AOMO(32)

@@ -1,8 +1,10 @@
 // AO evaluation fused with the AO->MO contraction on the 5th-generation
 // tensor cores (tcgen05, sm_103a).  Mixed forms only.
 //
-// CTA = 256 threads, 128 walkers x one electron.  Each walker row is computed
-// by two threads (they split the shells); the FP32 AO channels are written
+// CTA = 512 threads, 128 walkers x one electron.  Each walker row is computed
+// by four threads (they split the shells, balanced by AO count, so that 16
+// warps per SM hide the latency of the FP32 AO evaluation within the shared
+// memory the operand tiles need); the FP32 AO channels are written
 // into shared memory as the MMA A operand, split into TF32 high and low parts
 //     a = a_hi + a_lo,  a_hi = rna_tf32(a),  a_lo = rna_tf32(a - a_hi),
 // and one thread issues, per channel c (value / kinetic operator) and K step,
@@ -30,7 +32,8 @@ namespace qmc {
 namespace {
 
 constexpr int kRows = 128;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kParts = kThreads / kRows;
 constexpr int kNPad = 16;
 constexpr uint32_t kTmemCols = 32;
 
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
   __syncthreads();
 
   // ---- AO channels -> A operand (TF32 hi / lo) in shared memory
-  const int row = tid & (kRows - 1), half = tid >> 7;
+  const int row = tid & (kRows - 1), part = tid >> 7;
   const int64_t w = (int64_t)blockIdx.x * kRows + row;
   const int i = blockIdx.y;
   const bool live = w < W;
@@ -143,8 +146,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
         gjz = gradJ[(int64_t)(3 * i + 2) * ldm + w];
       }
     }
-    const int s_begin = half == 0 ? 0 : wf.shell_split;
-    const int s_end = half == 0 ? wf.shell_split : wf.n_shell;
+    const int s_begin = wf.shell_part[part];
+    const int s_end = wf.shell_part[part + 1];
     int cur_atom = -1;
     float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, rho = 0.f, irho = 0.f;
     float px[5], py[5], pz[5];
@@ -152,9 +155,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
       const ShellDev& sh = sh_s[s];
       if (sh.atom != cur_atom) {
         cur_atom = sh.atom;
-        dx = float(rx - wf.atom_xyz[cur_atom][0]);
-        dy = float(ry - wf.atom_xyz[cur_atom][1]);
-        dz = float(rz - wf.atom_xyz[cur_atom][2]);
+        displacement(rx, ry, rz, wf.atom_xyz[cur_atom], dx, dy, dz);
         r2 = dx * dx + dy * dy + dz * dz;
         irho = rsqrtf(r2);
         rho = r2 * irho;
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
         }
       }
     }
-    if (half == 1)
+    if (part == kParts - 1)
       for (int k = wf.n_ao; k < kp; ++k)
         for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
   }
@@ -211,7 +212,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
     if (tid == 0) atomicExch(err_flag, 1);
     const int ch = tid >> 7;
     if (ch < NCH && live)
-      for (int m = 0; m < wf.n_mo; ++m) mo_out[((int64_t)(i * NCH + ch) * wf.n_mo + m) * ldm + w] = __int_as_float(0x7fc00000);
+      for (int m = 0; m < kNPad; ++m)
+        mo_out[(((size_t)w * wf.n_elec + i) * NCH + ch) * kNPad + m] = __int_as_float(0x7fc00000);
   } else {
     // ---- epilogue: TMEM -> registers -> MO channels in HBM
     const int quad = warp & 3, ch = warp >> 2;
@@ -225,11 +227,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const int64_t wr = (int64_t)blockIdx.x * kRows + quad * 32 + (tid & 31);
-      if (wr < W) {
-        const int nmo = wf.n_mo;
+      if (wr < W) {  // walker-major MO block row (wr, i, ch): 16 floats, 64 B aligned
+        float4* dst = reinterpret_cast<float4*>(mo_out + (((size_t)wr * wf.n_elec + i) * NCH + ch) * kNPad);
 #pragma unroll
-        for (int m = 0; m < kNPad; ++m)
-          if (m < nmo) mo_out[((int64_t)(i * NCH + ch) * nmo + m) * ldm + wr] = __uint_as_float(v[m]);
+        for (int m = 0; m < kNPad / 4; ++m)
+          dst[m] = make_float4(__uint_as_float(v[4 * m]), __uint_as_float(v[4 * m + 1]),
+                               __uint_as_float(v[4 * m + 2]), __uint_as_float(v[4 * m + 3]));
       }
     }
   }

@@ -1,171 +1,222 @@
 // Determinants, excited-determinant tables and local-energy assembly.
-// All arithmetic in FP64.  One thread per walker, both spin channels.
+// All arithmetic in FP64 (the inputs are widened to FP64 exactly).
 //
-// Per spin channel s with n = n_s electrons (rows) and reference columns
-// 0..n-1 (A0 = Phi[:, 0:n], B = O Phi with O = lap + 2 grad J . grad):
-//   1. A0^-1 by Gauss-Jordan elimination with partial pivoting; det A0 is the
-//      signed product of the pivots.
-//   2. tr0 = Tr(A0^-1 B0)                           (Jacobi / eq. claudia_trace)
-//   3. for every virtual column p that an excitation uses:
-//        t      = A0^-1 Phi[:, p]                   (T_val column, all rows)
+// Work decomposition: a team of TS threads (TS = 1, 2, 4 or 8, a divisor of
+// the warp) owns one walker.  FP64 issue slots are the scarce resource on
+// GB300 (the FP64 pipe runs at 1/64 of the FP32 rate), so the work is split
+// without redundancy and the team keeps enough warps resident to hide
+// latency:
+//   0. stage: the walker's MO block of one spin (value channel Phi and
+//      kinetic channel B = (lap + 2 grad J . grad) Phi, rows = electrons,
+//      columns = orbitals) is read as one contiguous chunk, widened to FP64
+//      with integer bit operations and kept in shared memory;
+//   1. A0^-1 (A0 = Phi[:, 0:n]) by Gauss-Jordan elimination with partial
+//      pivoting, thread q owning column q; the pivot row index and pivot
+//      column are broadcast by warp shuffles; det A0 is the signed pivot
+//      product;
+//   2. tr0 = Tr(A0^-1 B0) (Jacobi formula / eq. claudia_trace), and per
+//      virtual column p (thread q takes p = n + q, n + q + TS, ...):
+//        t      = A0^-1 Phi[:, p]          T_val column
 //        y      = B[:, p] - B0 t
-//        Top[h] = (A0^-1 y)[h]   for holes h        (= (P M P) entries of Eq. table)
-//      so that for an excitation X with holes h_a, particles p_b:
-//        S_ab = T_val[h_a][p_b] = (P A0^-1 A_X P),   Mk_ab = Top[h_a][p_b] = (P M P)
-//        D_X / D_0 = det S                          (the k x k minor, k <= 2)
-//        Tr(A_X^-1 B_X) = tr0 + Tr(S^-1 Mk)         (Eq. table, App. F)
-//      and R Tr(S^-1 Mk) = Tr(adj(S) Mk) needs no division.
-//   4. Sigma / (D0_up D0_dn) = sum_n d_n R_n^up R_n^dn; the Slater kinetic part
+//        Top[h] = (A0^-1 y)[h]             for the holes h
+//      which gives, for an excitation X with holes h_a and particles p_b,
+//        S_ab = T_val[h_a][p_b] = (P A0^-1 A_X P),  Mk_ab = Top[h_a][p_b] = (P M P)
+//        D_X / D_0 = det S,  Tr(A_X^-1 B_X) = tr0 + Tr(S^-1 Mk)   (Eq. table, App. F)
+//      with R Tr(S^-1 Mk) = Tr(adj(S) Mk), free of divisions;
+//   3. the determinant list is split over the team:
+//        Sigma / (D0_up D0_dn) = sum_n d_n R_n^up R_n^dn
 //        [lap Sigma + 2 grad J . grad Sigma] / Sigma
-//          = sum_n d_n (R^up R^dn)(Tr_n^up + Tr_n^dn) / sum_n d_n R^up R^dn
-//      (Eqs. nabla_sigma, delta_sigma with the one-body operator O; the up-down
-//      cross term is zero without backflow).
-//   5. E_L = -1/2 (kinJ + Slater kinetic part) + V,  log|Psi| = J + log|Sigma|.
+//             = sum_n d_n (RT^up R^dn + R^up RT^dn) / sum_n d_n R^up R^dn
+//      (Eqs. nabla_sigma, delta_sigma; the up-down cross term vanishes
+//      without backflow) and reduced across the team by shuffles;
+//   4. E_L = -1/2 (kinJ + Slater kinetic part) + V, log|Psi| = J + log|Sigma|.
 #include "qmc_internal.cuh"
 
 namespace qmc {
 
-// Read MO channel c, row i (electron), column m for walker w.
-template <typename TA>
-__device__ __forceinline__ double ld_mo(const TA* __restrict__ mo, int nch, int nmo, int64_t ldm, int i, int c,
-                                        int m, int64_t w) {
-  return double(mo[((int64_t)(i * nch + c) * nmo + m) * ldm + w]);
+// Exact float -> double widening with integer operations only (no FP64-pipe
+// conversion).  Subnormal inputs are flushed to signed zero.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+  unsigned hi;
+  if (ex == 0u) hi = sign;
+  else if (ex == 0xffu) hi = sign | 0x7ff00000u | (man >> 3);
+  else hi = sign | ((ex + 896u) << 20) | (man >> 3);
+  const unsigned lo = ex == 0u ? 0u : (man << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+// |x| as an ordered integer key (the IEEE bit pattern with the sign cleared
+// orders like |x| for finite x), so pivot search needs no FP64 compare.
+__device__ __forceinline__ long long abs_key(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffll;
 }
 
-// In-place Gauss-Jordan inverse of a[0:n][0:n] (NS compile-time bound, rows
-// in registers) with partial pivoting.  Returns det through (sign, prod).
-template <int NS>
-__device__ __forceinline__ void gj_inverse(double (&a)[NS][NS], int n, double& det) {
-  int piv[NS];
-  det = 1.0;
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    if (k < n) {
-      int p = k;
-      double best = fabs(a[k][k]);
-#pragma unroll
-      for (int i = k + 1; i < NS; ++i) {
-        if (i < n && fabs(a[i][k]) > best) { best = fabs(a[i][k]); p = i; }
-      }
-      piv[k] = p;
-      if (p != k) det = -det;
-#pragma unroll
-      for (int i = k + 1; i < NS; ++i) {
-        const bool sw = (i == p);
-#pragma unroll
-        for (int j = 0; j < NS; ++j) {
-          const double t = a[k][j];
-          a[k][j] = sw ? a[i][j] : a[k][j];
-          a[i][j] = sw ? t : a[i][j];
-        }
-      }
-      const double pv = a[k][k];
-      det *= pv;
-      const double inv = 1.0 / pv;
-      a[k][k] = 1.0;
-#pragma unroll
-      for (int j = 0; j < NS; ++j) a[k][j] *= inv;
-#pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        if (i != k && i < n) {
-          const double f = a[i][k];
-          a[i][k] = 0.0;
-#pragma unroll
-          for (int j = 0; j < NS; ++j) a[i][j] -= f * a[k][j];
-        }
-      }
-    }
-  }
-  // undo the row interchanges as column interchanges, last first
-#pragma unroll
-  for (int k = NS - 1; k >= 0; --k) {
-    if (k < n) {
-      const int p = piv[k];
-#pragma unroll
-      for (int j = k + 1; j < NS; ++j) {
-        const bool sw = (j == p);
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-          const double t = a[i][k];
-          a[i][k] = sw ? a[i][j] : a[i][k];
-          a[i][j] = sw ? t : a[i][j];
-        }
-      }
-    }
-  }
+// Reciprocal by Newton-Raphson iteration r <- r + r (1 - a r) (quadratic
+// convergence) from an FP32 seed: the seed is built from the top bits of a
+// with integer operations, inverted with the FP32 reciprocal (error < 2^-22)
+// and widened back; two iterations reach the FP64 rounding level.  4 FP64
+// instructions instead of a full division.  Pivots outside the FP32 range
+// (never met by orbital matrices) take the IEEE division.
+__device__ __forceinline__ double recip(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const int e = (int)((u >> 52) & 0x7ffu);
+  if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / a;
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const float af = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+  const unsigned rb = __float_as_uint(__frcp_rn(af));
+  const unsigned re = (rb >> 23) & 0xffu;
+  double r = __hiloint2double((int)((rb & 0x80000000u) | ((re + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
+                              (int)(rb << 29));
+  r = fma(r, fma(-a, r, 1.0), r);
+  r = fma(r, fma(-a, r, 1.0), r);
+  return r;
 }
 
-template <int NS, typename TA, bool KIN>
-__global__ void __launch_bounds__(64) k_det(WfDev wf, int64_t W, const TA* __restrict__ mo, int64_t ldm,
-                                            const double* __restrict__ jscal, double* __restrict__ e_loc,
-                                            double* __restrict__ log_psi) {
+template <int TS>
+__device__ __forceinline__ double team_sum(double v) {
+#pragma unroll
+  for (int o = TS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NS, int TS, typename TA, bool KIN>
+__global__ void __launch_bounds__(256) k_det(WfDev wf, int64_t W, const TA* __restrict__ mo, int nmp,
+                                             const double* __restrict__ jscal, int64_t ldm, int stride,
+                                             double* __restrict__ e_loc, double* __restrict__ log_psi) {
+  constexpr int WPB = 256 / TS;
+  constexpr int NCH = KIN ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // excitation tables, [element][thread] so that 64-bit accesses are conflict-free
-  double* tab = reinterpret_cast<double*>(smem_raw);
-  int* exc_s = reinterpret_cast<int*>(tab + (size_t)wf.tab_elems * blockDim.x);
-  int* didx_s = exc_s + 2 * 5 * (wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1]);
-  const int nexc_max = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
+  const int nexc = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
+  double* walk_s = reinterpret_cast<double*>(smem_raw);  // [WPB][stride]
+  double* dw_s = walk_s + (size_t)WPB * stride;          // [n_det]
+  int* exc_s = reinterpret_cast<int*>(dw_s + wf.n_det);  // [2][nexc][5]
+  int* didx_s = exc_s + 10 * nexc;                       // [n_det][2]
   for (int s = 0; s < 2; ++s)
-    for (int k = threadIdx.x; k < wf.n_exc[s] * 5; k += blockDim.x)
-      exc_s[(s * nexc_max) * 5 + k] = wf.exc[s * kMaxExc * 5 + k];
+    for (int k = threadIdx.x; k < wf.n_exc[s] * 5; k += blockDim.x) exc_s[s * nexc * 5 + k] = wf.exc[s * kMaxExc * 5 + k];
   for (int k = threadIdx.x; k < wf.n_det * 2; k += blockDim.x) didx_s[k] = wf.det_idx[k];
+  for (int k = threadIdx.x; k < wf.n_det; k += blockDim.x) dw_s[k] = wf.det_w[k];
   __syncthreads();
 
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= W) return;
-  const int nch = KIN ? 2 : 1;
-  const int nmo = wf.n_mo;
-  const int T = blockDim.x, tid = threadIdx.x;
+  const int team = threadIdx.x / TS, q = threadIdx.x % TS;
+  const int lane0 = (threadIdx.x & 31) - q;  // first lane of the team
+  const int64_t w = (int64_t)blockIdx.x * WPB + team;
+  const bool live = w < W;
+  const int nmo = wf.n_mo, N = wf.n_elec;
+  double* my = walk_s + (size_t)team * stride;
+  // per-walker shared layout: stage [NCH][NS][nmo] | ainv [NS][NS] | tables
+  double* stage = my;
+  double* ainv = my + NCH * NS * nmo;
+  double* tab = ainv + NS * NS;
+  const TA* blk = mo + (size_t)(live ? w : 0) * N * NCH * nmp;
 
-  double logdet = 0.0, tr0u = 0.0, tr0d = 0.0;
+  double detprod = 1.0, tr0u = 0.0, tr0d = 0.0;
   int tab_off = 0;
   for (int s = 0; s < 2; ++s) {
     const int n = s == 0 ? wf.n_up : wf.n_down;
     const int i0 = s == 0 ? 0 : wf.n_up;
     if (n == 0) continue;
-    double a[NS][NS];
+    // ---- 0. stage rows i0 .. i0+n-1 (contiguous in the walker block)
+    {
+      const TA* src = blk + (size_t)i0 * NCH * nmp;
+      const int total = n * NCH * nmp;
+      for (int k = q; k < total; k += TS) {
+        const int m = k % nmp, rc = k / nmp, c = rc % NCH, r = rc / NCH;
+        if (m < nmo) stage[(c * NS + r) * nmo + m] = live ? widen(src[k]) : (r == m ? 1.0 : 0.0);
+      }
+    }
+    __syncwarp();
+    // ---- 1. Gauss-Jordan inverse, thread q owns column q
+    double col[NS];
 #pragma unroll
-    for (int r = 0; r < NS; ++r)
+    for (int r = 0; r < NS; ++r) col[r] = (r < n && q < n) ? stage[r * nmo + q] : 0.0;
+    int piv[NS];
+    double det = 1.0;
 #pragma unroll
-      for (int m = 0; m < NS; ++m) a[r][m] = (r < n && m < n) ? ld_mo(mo, nch, nmo, ldm, i0 + r, 0, m, w) : 0.0;
-    double det;
-    gj_inverse<NS>(a, n, det);  // a[m][r] = (A0^-1)_{m r}
-    logdet += log(fabs(det));
-    if (KIN) {
-      double t = 0.0;
+    for (int k = 0; k < NS; ++k) {
+      if (k < n) {
+        int p = k;
+        long long best = abs_key(col[k]);
+#pragma unroll
+        for (int i = k + 1; i < NS; ++i)
+          if (i < n && abs_key(col[i]) > best) { best = abs_key(col[i]); p = i; }
+        p = __shfl_sync(0xffffffffu, p, lane0 + k);
+        piv[k] = p;
+#pragma unroll
+        for (int i = k + 1; i < NS; ++i) {
+          const bool sw = (i == p);
+          const double t = col[k];
+          col[k] = sw ? col[i] : col[k];
+          col[i] = sw ? t : col[i];
+        }
+        double f[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) f[i] = __shfl_sync(0xffffffffu, col[i], lane0 + k);
+        const double pv = f[k];
+        det *= (p != k) ? -pv : pv;
+        const double inv = recip(pv);
+        const double ak = ((q == k) ? 1.0 : col[k]) * inv;
+        col[k] = ak;
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+          if (i != k && i < n) col[i] = ((q == k) ? 0.0 : col[i]) - f[i] * ak;
+      }
+    }
+    {  // undo the row interchanges as column interchanges
+      int src = q;
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        if (k < n) src = (src == k) ? piv[k] : (src == piv[k] ? k : src);
+#pragma unroll
+      for (int r = 0; r < NS; ++r) col[r] = __shfl_sync(0xffffffffu, col[r], lane0 + (src < TS ? src : 0));
+    }
+    if (q < n) {
 #pragma unroll
       for (int m = 0; m < NS; ++m)
+        if (m < n) ainv[m * NS + q] = col[m];  // (A0^-1)_{m q}
+    }
+    detprod *= det;  // one logarithm per walker, taken at the end
+    __syncwarp();
+    // ---- 2. tr0 and the excitation tables
+    if (KIN) {
+      double c = 0.0;
+      if (q < n) {
 #pragma unroll
         for (int r = 0; r < NS; ++r)
-          if (m < n && r < n) t += a[m][r] * ld_mo(mo, nch, nmo, ldm, i0 + r, 1, m, w);
-      if (s == 0) tr0u = t; else tr0d = t;
+          if (r < n) c += ainv[q * NS + r] * stage[(NS + r) * nmo + q];
+      }
+      c = team_sum<TS>(c);
+      if (s == 0) tr0u = c; else tr0d = c;
     }
     const int hl = wf.h_lo[s], nh = wf.nh[s], nv = wf.nv[s];
-    for (int pv = 0; pv < nv; ++pv) {
+    for (int pv = q; pv < nv; pv += TS) {
       const int p = n + pv;
-      double phi[NS], t[NS];
-#pragma unroll
-      for (int r = 0; r < NS; ++r) phi[r] = r < n ? ld_mo(mo, nch, nmo, ldm, i0 + r, 0, p, w) : 0.0;
+      double t[NS];
 #pragma unroll
       for (int m = 0; m < NS; ++m) {
         double acc = 0.0;
+        if (m < n) {
 #pragma unroll
-        for (int r = 0; r < NS; ++r) acc += a[m][r] * phi[r];
+          for (int r = 0; r < NS; ++r)
+            if (r < n) acc += ainv[m * NS + r] * stage[r * nmo + p];
+        }
         t[m] = acc;
       }
 #pragma unroll
       for (int m = 0; m < NS; ++m)
-        if (m >= hl && m < n) tab[(size_t)(tab_off + (m - hl) * nv + pv) * T + tid] = t[m];
+        if (m >= hl && m < n) tab[tab_off + (m - hl) * nv + pv] = t[m];
       if (KIN) {
         double y[NS];
 #pragma unroll
         for (int r = 0; r < NS; ++r) {
           double acc = 0.0;
           if (r < n) {
-            acc = ld_mo(mo, nch, nmo, ldm, i0 + r, 1, p, w);
+            acc = stage[(NS + r) * nmo + p];
 #pragma unroll
             for (int m = 0; m < NS; ++m)
-              if (m < n) acc -= ld_mo(mo, nch, nmo, ldm, i0 + r, 1, m, w) * t[m];
+              if (m < n) acc -= stage[(NS + r) * nmo + m] * t[m];
           }
           y[r] = acc;
         }
@@ -174,18 +225,20 @@ __global__ void __launch_bounds__(64) k_det(WfDev wf, int64_t W, const TA* __res
           if (m >= hl && m < n) {
             double acc = 0.0;
 #pragma unroll
-            for (int r = 0; r < NS; ++r) acc += a[m][r] * y[r];
-            tab[(size_t)(tab_off + nh * nv + (m - hl) * nv + pv) * T + tid] = acc;
+            for (int r = 0; r < NS; ++r)
+              if (r < n) acc += ainv[m * NS + r] * y[r];
+            tab[tab_off + nh * nv + (m - hl) * nv + pv] = acc;
           }
         }
       }
     }
-    tab_off += (KIN ? 2 : 1) * nh * nv;
+    tab_off += NCH * nh * nv;
+    __syncwarp();
   }
 
-  // determinant expansion
+  // ---- 3. determinant expansion, split over the team
   double sum_r = 0.0, sum_k = 0.0;
-  for (int d = 0; d < wf.n_det; ++d) {
+  for (int d = q; d < wf.n_det; d += TS) {
     double R[2], RT[2];
     int off = 0;
 #pragma unroll
@@ -193,73 +246,92 @@ __global__ void __launch_bounds__(64) k_det(WfDev wf, int64_t W, const TA* __res
       const double tr0s = s == 0 ? tr0u : tr0d;
       const int n = s == 0 ? wf.n_up : wf.n_down;
       const int hl = wf.h_lo[s], nh = wf.nh[s], nv = wf.nv[s];
-      const int* e = exc_s + (s * nexc_max + didx_s[2 * d + s]) * 5;
+      const int* e = exc_s + (s * nexc + didx_s[2 * d + s]) * 5;
       const int rank = e[0];
-      const double* tv = tab + (size_t)off * T + tid;
-      const double* tk = tab + (size_t)(off + nh * nv) * T + tid;
+      const double* tv = tab + off;
+      const double* tk = tab + off + nh * nv;
       if (rank == 0) {
-        R[s] = 1.0; RT[s] = tr0s;
+        R[s] = 1.0;
+        RT[s] = tr0s;
       } else if (rank == 1) {
-        const int q = (e[1] - hl) * nv + (e[3] - n);
-        R[s] = tv[(size_t)q * T];
-        RT[s] = R[s] * tr0s + (KIN ? tk[(size_t)q * T] : 0.0);
+        const int qq = (e[1] - hl) * nv + (e[3] - n);
+        R[s] = tv[qq];
+        RT[s] = KIN ? R[s] * tr0s + tk[qq] : 0.0;
       } else {
         const int q00 = (e[1] - hl) * nv + (e[3] - n), q01 = (e[1] - hl) * nv + (e[4] - n);
         const int q10 = (e[2] - hl) * nv + (e[3] - n), q11 = (e[2] - hl) * nv + (e[4] - n);
-        const double s00 = tv[(size_t)q00 * T], s01 = tv[(size_t)q01 * T];
-        const double s10 = tv[(size_t)q10 * T], s11 = tv[(size_t)q11 * T];
+        const double s00 = tv[q00], s01 = tv[q01], s10 = tv[q10], s11 = tv[q11];
         R[s] = s00 * s11 - s01 * s10;
-        RT[s] = R[s] * tr0s;
-        if (KIN)
-          RT[s] += s11 * tk[(size_t)q00 * T] - s01 * tk[(size_t)q10 * T] - s10 * tk[(size_t)q01 * T] +
-                   s00 * tk[(size_t)q11 * T];
+        RT[s] = KIN ? R[s] * tr0s + s11 * tk[q00] - s01 * tk[q10] - s10 * tk[q01] + s00 * tk[q11] : 0.0;
       }
-      off += (KIN ? 2 : 1) * nh * nv;
+      off += NCH * nh * nv;
     }
-    const double dw = wf.det_w[d];
+    const double dw = dw_s[d];
     sum_r += dw * R[0] * R[1];
     if (KIN) sum_k += dw * (RT[0] * R[1] + R[0] * RT[1]);
   }
-  const double J = jscal[w];
-  const double lp = J + logdet + log(fabs(sum_r));
-  if (log_psi) log_psi[w] = lp;
-  if (KIN) {
-    const double kinJ = jscal[ldm + w], V = jscal[2 * ldm + w];
-    e_loc[w] = -0.5 * (kinJ + sum_k / sum_r) + V;
+  sum_r = team_sum<TS>(sum_r);
+  if (KIN) sum_k = team_sum<TS>(sum_k);
+  if (q == 0 && live) {
+    const double lp = jscal[w] + log(fabs(detprod * sum_r));
+    if (log_psi) log_psi[w] = lp;
+    if (KIN) e_loc[w] = -0.5 * (jscal[ldm + w] + sum_k / sum_r) + jscal[2 * ldm + w];
   }
 }
 
-template <int NS, typename TA>
+// doubles per walker in shared memory, padded to 8 mod 16: 64-bit shared
+// accesses are served per half warp (two teams of 8), and this offset puts
+// the second team on the other 16 bank pairs both for broadcast reads and
+// for row reads of 8 consecutive doubles
+static int walker_stride(const WfDev& wf, int NS, bool kin) {
+  const int nch = kin ? 2 : 1;
+  const int tab = kin ? wf.tab_elems : (wf.nh[0] * wf.nv[0] + wf.nh[1] * wf.nv[1]);
+  int s = nch * NS * wf.n_mo + NS * NS + tab;
+  while (s % 16 != 8) ++s;
+  return s;
+}
+
+size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin) {
+  const int nexc = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
+  return sizeof(double) * ((size_t)(256 / TS) * walker_stride(wf, NS, kin) + wf.n_det) +
+         sizeof(int) * (10 * (size_t)nexc + 2 * (size_t)wf.n_det);
+}
+
+template <int NS, int TS, typename TA>
 static cudaError_t launch_ns(const WfDev& wf, int64_t W, const Workspace& ws, bool kin, double* e_loc,
                              double* log_psi, cudaStream_t st) {
-  const int block = 64;
-  const dim3 grid((unsigned)((W + block - 1) / block));
-  const int nexc_max = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
-  const int tab = kin ? wf.tab_elems : (wf.nh[0] * wf.nv[0] + wf.nh[1] * wf.nv[1]);
-  const size_t smem = sizeof(double) * (size_t)tab * block + sizeof(int) * (10 * nexc_max + 2 * wf.n_det);
-  WfDev w2 = wf;
-  w2.tab_elems = tab;
+  constexpr int WPB = 256 / TS;
+  const dim3 grid((unsigned)((W + WPB - 1) / WPB));
+  const int stride = walker_stride(wf, NS, kin);
+  const size_t smem = det_smem_bytes(wf, NS, TS, kin);
   const TA* mo = static_cast<const TA*>(ws.mo);
-  if (kin) {
-    auto kern = k_det<NS, TA, true>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, block, smem, st>>>(w2, W, mo, ws.ldm, ws.jscal, e_loc, log_psi);
-  } else {
-    auto kern = k_det<NS, TA, false>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, block, smem, st>>>(w2, W, mo, ws.ldm, ws.jscal, e_loc, log_psi);
-  }
+  auto kern = kin ? k_det<NS, TS, TA, true> : k_det<NS, TS, TA, false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<grid, 256, smem, st>>>(wf, W, mo, ws.nmp, ws.jscal, ws.ldm, stride, e_loc, log_psi);
   return cudaGetLastError();
+}
+
+// team size: enough threads for the widest of the n columns and nv virtual
+// columns, at most 8
+int det_team_size(const WfDev& wf) {
+  const int ns = wf.n_up > wf.n_down ? wf.n_up : wf.n_down;
+  const int nv = wf.nv[0] > wf.nv[1] ? wf.nv[0] : wf.nv[1];
+  const int need = ns > nv ? ns : nv;
+  return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
 }
 
 template <typename TA>
 static cudaError_t launch_t(const WfDev& wf, int64_t W, const Workspace& ws, bool kin, double* e_loc,
                            double* log_psi, cudaStream_t st) {
   const int ns = wf.n_up > wf.n_down ? wf.n_up : wf.n_down;
-  if (ns <= 1) return launch_ns<1, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-  if (ns <= 2) return launch_ns<2, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-  if (ns <= 4) return launch_ns<4, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-  if (ns <= 8) return launch_ns<8, TA>(wf, W, ws, kin, e_loc, log_psi, st);
+  const int ts = det_team_size(wf);
+#define QMC_DET(NS_, TS_) \
+  if (ns == NS_ && ts == TS_) return launch_ns<NS_, TS_, TA>(wf, W, ws, kin, e_loc, log_psi, st);
+  QMC_DET(1, 1) QMC_DET(1, 2) QMC_DET(1, 4) QMC_DET(1, 8)
+  QMC_DET(2, 2) QMC_DET(2, 4) QMC_DET(2, 8)
+  QMC_DET(3, 4) QMC_DET(3, 8) QMC_DET(4, 4) QMC_DET(4, 8)
+  QMC_DET(5, 8) QMC_DET(6, 8) QMC_DET(7, 8) QMC_DET(8, 8)
+#undef QMC_DET
   return cudaErrorInvalidValue;
 }
 

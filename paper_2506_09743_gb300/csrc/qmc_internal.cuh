@@ -4,11 +4,14 @@
 //   walkers        double [3N][ldw]            caller-owned, coordinate-major
 //   grad J         TA     [3N][ldm]            Jastrow gradient per electron
 //   jastrow scal.  double [3][ldm]             J, sum_i(lap_i J + |grad_i J|^2), V
-//   MO channels    TA     [N][NCH][n_mo][ldm]  channel 0 = Phi_{i,m},
-//                                              channel 1 = (lap + 2 grad J . grad) Phi_{i,m}
-// with TA = double (FP64 form) or float (other forms).  Every kernel maps
-// consecutive threads to consecutive walkers, so all of these accesses are
-// coalesced.
+//   MO channels    TA     [W][N][NCH][nmp]     walker-major blocks; channel 0 =
+//                                              Phi_{i,m}, channel 1 =
+//                                              (lap + 2 grad J . grad) Phi_{i,m};
+//                                              orbitals padded to nmp (8/16/32)
+// with TA = double (FP64 form) or float (other forms).  Coordinate-major
+// arrays are read by thread-per-walker kernels (consecutive threads,
+// consecutive walkers); each walker's MO block is one contiguous chunk, read
+// whole by the determinant team of that walker.
 #pragma once
 
 #include <cstdint>
@@ -30,6 +33,8 @@ struct ShellDev {
   int n_prim, ao_first, n_ao, pad;
   double expo[QMC_MAX_PRIM];
   double coef[QMC_MAX_PRIM];
+  float expo_f[QMC_MAX_PRIM];  // FP32 copies: FP32 kernels must not convert
+  float coef_f[QMC_MAX_PRIM];  // (double->float runs on the FP64 pipe)
 };
 
 // Everything a kernel needs, passed by value (pointers are device memory).
@@ -56,20 +61,50 @@ struct WfDev {
   const uint32_t* mo_tc_hi;
   const uint32_t* mo_tc_lo;
   int k_pad;        // AO dimension padded to a multiple of the MMA K step
-  int shell_split;  // tensor-core AO stage: threads of half 0 take shells [0, split)
+  int shell_part[5];  // tensor-core AO stage: thread part q takes shells [part[q], part[q+1])
 };
 
 struct Workspace {
   int64_t ldm;
+  int nmp;         // padded orbital count of an MO row
   void* gradJ;     // TA [3N][ldm]
   double* jscal;   // [3][ldm]
-  void* mo;        // TA [N][NCH][n_mo][ldm]
+  void* mo;        // TA [W][N][NCH][nmp]
   double* prop;    // [3N][ldm] proposed positions (sampling)
   double* lp;      // [ldm] current log|Psi| (sampling)
   double* lp_new;  // [ldm] proposed log|Psi| (sampling)
 };
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// padded orbital count of an MO row: the tensor-core forms always use 16
+inline int mo_row_pad(int n_mo, bool tensor_core) {
+  if (tensor_core) return 16;
+  return n_mo <= 8 ? 8 : n_mo <= 16 ? 16 : 32;
+}
+
+#ifdef __CUDACC__
+// Split a double into two floats hi + lo (hi = d truncated to 24 bits,
+// lo = the next 24 bits) using integer operations and an integer->float
+// conversion only; relative error 2^-48.  Magnitudes below 2^-70 give 0.
+__device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ffu);
+  if (e < 953) {
+    hi = __uint_as_float(sign);
+    lo = 0.0f;
+    return;
+  }
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+  const float l = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull)) * __uint_as_float((unsigned)(e - 948) << 23);
+  lo = sign ? -l : l;
+}
+#endif
+
+int det_team_size(const WfDev& wf);
+size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin);
 
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
