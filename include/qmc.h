@@ -169,6 +169,34 @@ qmc_status qmc_local_energy(qmc_wf* wf, const double* walkers, int64_t n_walkers
 qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_walkers,
                                  double* e_loc, double* log_psi, void* stream);
 
+/* Bytes of the library's static device scratch array used by
+ * qmc_local_energy_noalloc.  Every GPU that loads the library holds this
+ * much device memory until the process exits. */
+#define QMC_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* qmc_local_energy for callers that must not allocate device memory during a
+ * call.  The paper has no counterpart; this is an integration aid.  Such
+ * callers include a serving loop that runs requests concurrently on several
+ * streams under a fixed device-memory budget (a cudaMalloc stalls the whole
+ * device and can fail once memory is fragmented), processes whose device
+ * memory is owned by another allocator (a framework's caching pool), and
+ * latency-bound callers that cannot absorb an allocation inside a request.
+ * Same computation and results as qmc_local_energy, but the device scratch is
+ * a fixed static array of QMC_NOALLOC_SCRATCH_BYTES inside the library: no
+ * cudaMalloc, cudaFree or allocating library routine is called.
+ * Limit: qmc_workspace_size(wf, n_walkers) <= QMC_NOALLOC_SCRATCH_BYTES;
+ * larger batches return QMC_ERR_ARG with the largest admissible count in the
+ * message (split them into several calls).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents (what must start at zero is cleared by the call
+ * itself): calls that overlap on the GPU, on any stream or from any thread,
+ * race on it and must be serialised by the caller.
+ * walkers, e_loc, log_psi: as for qmc_local_energy. */
+qmc_status qmc_local_energy_noalloc(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw,
+                                    double* e_loc, double* log_psi, void* stream);
+
 /* Metropolis-Hastings walker steps (App. B): every step moves all electrons
  * of a walker by step * z, z ~ N(0, 1) per coordinate, and accepts with
  * probability min(1, |Psi'/Psi|^2).  Random numbers: Philox4x32-10 with key

@@ -141,6 +141,25 @@ class Wavefunction:
                                               _dptr(workspace), ws_bytes, _stream_handle(stream)))
         return e_loc, log_psi
 
+    def local_energy_noalloc(self, walkers, n_walkers: int | None = None, e_loc=None, log_psi=None, stream=None,
+                             want_log_psi: bool = True):
+        """As local_energy, for callers that must not allocate device memory
+        during a call: the scratch is the library's static device array (see
+        qmc_local_energy_noalloc in include/qmc.h for the batch limit and the
+        rule that overlapping calls race on that array)."""
+        import torch
+
+        assert walkers.is_cuda and walkers.dtype == torch.float64 and walkers.dim() == 2
+        assert walkers.stride(1) == 1 and walkers.shape[0] == 3 * self.n_elec
+        W = walkers.shape[1] if n_walkers is None else int(n_walkers)
+        if e_loc is None:
+            e_loc = torch.empty(W, dtype=torch.float64, device=walkers.device)
+        if log_psi is None and want_log_psi:
+            log_psi = torch.empty(W, dtype=torch.float64, device=walkers.device)
+        _lib.check(self._lib.qmc_local_energy_noalloc(self._h, _dptr(walkers), W, walkers.stride(0), _dptr(e_loc),
+                                                      _dptr(log_psi), _stream_handle(stream)))
+        return e_loc, log_psi
+
     def local_energy_host(self, walkers: np.ndarray, e_loc: np.ndarray | None = None,
                           log_psi: np.ndarray | None = None, stream=None):
         """E_L from HOST buffers: walkers float64 [3N, W] C-contiguous (pinned

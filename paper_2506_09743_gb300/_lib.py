@@ -21,7 +21,7 @@ PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "mixed_tf32": QMC_MIXED_TF32, 
 # every exported symbol declared in include/qmc.h
 EXPORTED = (
     "qmc_create_wf", "qmc_destroy_wf", "qmc_set_geometry", "qmc_workspace_size", "qmc_local_energy",
-    "qmc_local_energy_host", "qmc_sample", "qmc_param_layout", "qmc_set_timing", "qmc_last_stage_ms",
+    "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_set_timing", "qmc_last_stage_ms",
     "qmc_last_error",
 )
 
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.qmc_local_energy.restype = c_int32
     lib.qmc_local_energy_host.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
     lib.qmc_local_energy_host.restype = c_int32
+    lib.qmc_local_energy_noalloc.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p]
+    lib.qmc_local_energy_noalloc.restype = c_int32
     lib.qmc_sample.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_double, c_uint64, c_uint64,
                                c_uint64, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
     lib.qmc_sample.restype = c_int32

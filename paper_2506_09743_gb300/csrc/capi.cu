@@ -594,6 +594,54 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
   return QMC_OK;
 }
 
+// ---- allocation-free variant of qmc_local_energy ---------------------------
+// The scratch lives in a static device array of this translation unit; host
+// code only ever uses the address obtained for it by cudaGetSymbolAddress (the
+// array's name is a host-side shadow in host code), looked up once per device
+// with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QMC_NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256] = {};
+
+qmc_status qmc_local_energy_noalloc(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw,
+                                    double* e_loc, double* log_psi, void* stream) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  if (n_walkers < 0 || ldw < n_walkers) return fail(QMC_ERR_ARG, "bad walker count or leading dimension");
+  if (n_walkers == 0) return QMC_OK;
+  if (!walkers || !e_loc) return fail(QMC_ERR_ARG, "null walkers or e_loc");
+  const size_t need = workspace_bytes(wf, n_walkers);
+  if (need > QMC_NOALLOC_SCRATCH_BYTES) {
+    int64_t lo = 0, hi = n_walkers;  // largest admissible batch, for the message
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) / 2;
+      if (workspace_bytes(wf, mid) <= QMC_NOALLOC_SCRATCH_BYTES) lo = mid; else hi = mid - 1;
+    }
+    return fail(QMC_ERR_ARG, "n_walkers = " + std::to_string(n_walkers) + " needs " + std::to_string(need) +
+                                 " bytes of scratch; the static scratch holds " +
+                                 std::to_string((size_t)QMC_NOALLOC_SCRATCH_BYTES) +
+                                 " bytes (at most " + std::to_string(lo) +
+                                 " walkers for this wavefunction per call)");
+  }
+  if (wf->device < 0 || wf->device >= 256) return fail(QMC_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  void* base;
+  {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[wf->device]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "static scratch address");
+      g_noalloc_ptr[wf->device] = p;
+    }
+    base = g_noalloc_ptr[wf->device];
+  }
+  int* err_flag;
+  Workspace ws = carve(wf, base, n_walkers, &err_flag);
+  return eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, log_psi,
+                   static_cast<cudaStream_t>(stream));
+}
+
 qmc_status qmc_set_timing(qmc_wf* wf, int32_t enable) {
   if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
   std::lock_guard<std::mutex> lock(wf->mu);
