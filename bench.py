@@ -37,6 +37,9 @@ METRIC = "walker local-energy evals/s (CO, 14 e-) vs FP64 plain; p99 request lat
 UNIT = "walker-evals/s"
 WORKLOAD = "CO 14e- 58 GTO 14 MO 100 det, 262144 walkers"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)
+# DRAM bytes (read + write) per walker of the mixed-form k_det launch, from the ncu capture in
+# profiles/k_det_co_mixed.md (242.8 MB for 131,072 walkers); None once that kernel changes.
+DET_TRAFFIC_BYTES_PER_WALKER = 242.824192e6 / 131072
 
 
 def det_stage_flops(mol) -> float:
@@ -81,7 +84,8 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)  # let the sampler start before the timed region
         except OSError:
             self.proc = None
         return self
@@ -225,26 +229,26 @@ def main():
         for _ in range(warmup):
             wf.local_energy(x, e_loc=e, log_psi=lp)
         barrier()
-        step_ms, stage = [], []
+        stage = []
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        with ClockSampler(local) as clk:
-            for k in range(steps):
-                flush.zero_()  # evict L2 between steps (outside the timed events)
-                ev[k][0].record(stream)
-                wf.local_energy(x, e_loc=e, log_psi=lp)
-                ev[k][1].record(stream)
-                stage.append(wf.last_stage_ms())  # waits for this step; outside the events
-            barrier()
+        for k in range(steps):
+            flush.zero_()  # evict L2 between steps (outside the timed events)
+            ev[k][0].record(stream)
+            wf.local_energy(x, e_loc=e, log_psi=lp)
+            ev[k][1].record(stream)
+            stage.append(wf.last_stage_ms())  # waits for this step; outside the events
+        barrier()
         step_ms = [a.elapsed_time(b) for a, b in ev]
         wf.set_timing(False)
         finite = float(torch.isfinite(e).double().mean().item())
-        return float(np.sum(step_ms)), np.mean(np.asarray(stage), axis=0), finite, clk.summary()
+        return float(np.sum(step_ms)), np.mean(np.asarray(stage), axis=0), finite
 
     wf_mixed = Wavefunction(mol, precision="mixed_tf32", device=local)
     wf_fp64 = Wavefunction(mol, precision="fp64", device=local)
 
-    tot_mixed, stage_mixed, fin_mixed, clocks = timed_device(wf_mixed, args.steps, args.warmup)
-    tot_fp64, stage_fp64, fin_fp64, clocks64 = timed_device(wf_fp64, max(3, args.steps // 4), 3)
+    clk = ClockSampler(local).__enter__()
+    tot_mixed, stage_mixed, fin_mixed = timed_device(wf_mixed, args.steps, args.warmup)
+    tot_fp64, stage_fp64, fin_fp64 = timed_device(wf_fp64, max(3, args.steps // 4), 3)
     k64 = max(3, args.steps // 4)
     tot_mixed = max_over_ranks(tot_mixed)
     tot_fp64 = max_over_ranks(tot_fp64)
@@ -271,6 +275,8 @@ def main():
         b.synchronize()
         t_e2e.append(a.elapsed_time(b))
     barrier()
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
     e2e_ms = max_over_ranks(float(np.sum(t_e2e)))
     e2e_value = world * W * e2e_steps / (e2e_ms / 1e3)
 
@@ -280,7 +286,8 @@ def main():
     flops_ao64 = ao_mo_stage_flops(mol) * W
     roofline = {"kernel": "k_det (determinants, tables, E_L; mixed form)", "bound": "alu", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None,
+                "traffic": None if DET_TRAFFIC_BYTES_PER_WALKER is None else DET_TRAFFIC_BYTES_PER_WALKER * W,
+                "traffic_unit": "bytes per launch (ncu dram read+write, scaled from 131,072 walkers)",
                 "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "flops_per_launch": flops_det, "kernel_ms": det_ms}
     line = {

@@ -8,6 +8,7 @@
 //   k_det       A0^-1, tables, excited determinants, E_L, log|Psi|
 // One Metropolis step (App. B): k_propose, the value-only form of the same
 // three stages on the proposal, k_accept.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -311,7 +312,18 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
       mo32[(size_t)b * nmo + m] = (float)mo64[(size_t)b * nmo + m];
     }
 
-  // ---- determinants: unique excitation records per spin
+  // ---- determinants: unique excitation records per spin.  The expansion is
+  // stored sorted by (rank up, rank down): the determinant stage hands
+  // consecutive determinants to the lanes of a warp, and a sorted list keeps
+  // their rank branches uniform (the sum is order independent).
+  std::vector<int> order(dets->n_det);
+  for (int n = 0; n < dets->n_det; ++n) order[n] = n;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ka = dets->exc[a * 10] * 3 + dets->exc[a * 10 + 5], kb = dets->exc[b * 10] * 3 + dets->exc[b * 10 + 5];
+    return ka < kb;
+  });
+  std::vector<double> det_w_sorted(dets->n_det);
+  for (int n = 0; n < dets->n_det; ++n) det_w_sorted[n] = dets->weight[order[n]];
   std::vector<int> exc(2 * kMaxExc * 5, -1);
   std::vector<int> det_idx(2 * dets->n_det);
   for (int s = 0; s < 2; ++s) {
@@ -322,7 +334,8 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
     for (int k = 0; k < 5; ++k) exc[(s * kMaxExc + 0) * 5 + k] = g[k];
     int h_lo = ns, p_hi = ns;
     for (int n = 0; n < dets->n_det; ++n) {
-      std::vector<int> e(dets->exc + (n * 2 + s) * 5, dets->exc + (n * 2 + s) * 5 + 5);
+      const int src = order[n];
+      std::vector<int> e(dets->exc + (src * 2 + s) * 5, dets->exc + (src * 2 + s) * 5 + 5);
       const int rank = e[0];
       bool ok = rank >= 0 && rank <= 2;
       if (ok && rank == 0) e = g;
@@ -331,7 +344,7 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
       if (ok && rank == 1) { e[2] = -1; e[4] = -1; }
       if (!ok) {
         delete wf;
-        return fail(QMC_ERR_ARG, "bad excitation record of determinant " + std::to_string(n));
+        return fail(QMC_ERR_ARG, "bad excitation record of determinant " + std::to_string(src));
       }
       auto it = seen.find(e);
       int idx;
@@ -391,7 +404,7 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
       {shells.data(), sizeof(ShellDev) * shells.size()}, {ao_pow.data(), sizeof(int) * nao},
       {mo64.data(), sizeof(double) * mo64.size()},       {mo32.data(), sizeof(float) * mo32.size()},
       {exc.data(), sizeof(int) * exc.size()},           {det_idx.data(), sizeof(int) * det_idx.size()},
-      {dets->weight, sizeof(double) * dets->n_det},      {tc_hi.data(), sizeof(uint32_t) * tc_hi.size()},
+      {det_w_sorted.data(), sizeof(double) * dets->n_det},      {tc_hi.data(), sizeof(uint32_t) * tc_hi.size()},
       {tc_lo.data(), sizeof(uint32_t) * tc_lo.size()}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
