@@ -216,6 +216,30 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
                       double* log_psi, int64_t* n_accept, void* workspace, size_t workspace_bytes,
                       void* stream);
 
+/* Mean and variance of E_L over the batch, the low-variance energy gradient
+ * (Eq. nabla_loss, Sec. 2.2) and the forces on the nuclei (Eq. force,
+ * Sec. 2.3), with E_v the batch mean and ln rho = 2 log|Psi|:
+ *   grad[p]   = (2/M) sum_m d_p log|Psi(r_m)| (E_L(r_m) - E_v)
+ *   forces[a] = -(1/M) sum_m [d_a E_L(r_m) + (E_L(r_m) - E_v) d_a ln rho(r_m)]
+ * The parameter derivatives of log|Psi| are evaluated in closed form (Jacobi
+ * formula through the backflow map, AOs recomputed per walker rather than
+ * stored); the nuclear derivatives of E_L and log|Psi| by forward-mode
+ * tangents through the whole local-energy evaluation.  Sums run in a fixed
+ * order (results are bitwise reproducible).
+ * Scope: FP64 form, one determinant, <= 8 electrons, <= 4 per spin
+ * (QMC_ERR_UNSUPPORTED otherwise).
+ * walkers: device [3N][ldw].  e_stats: host [2] (mean, variance).  grad:
+ * device [n_param] in qmc_param_layout order, or NULL.  forces: device
+ * [n_atom][3], or NULL.  Synchronises the stream. */
+qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_stats,
+                           double* grad, double* forces, void* stream);
+
+/* Replace the variational parameters (host [n_param] in qmc_param_layout
+ * order: exponents, MO coefficients, CI weights, Jastrow b, backflow w) and
+ * rebuild the device tables.  Waits for work in flight on the device.
+ * Exponents must be positive; on error the previous parameters stay. */
+qmc_status qmc_set_params(qmc_wf* wf, const double* params);
+
 /* Number of variational parameters and the offsets of the gradient blocks:
  * offsets[0] exponents (one per primitive, prim_exp order), [1] MO
  * coefficients (row-major n_ao x n_mo), [2] CI weights, [3] Jastrow b,

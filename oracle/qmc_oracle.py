@@ -357,8 +357,11 @@ def slater_dets(wf, Phi):
 
 
 def log_psi(wf, r):
-    """(log|Psi|, sign Psi) with Psi = exp(J) sum_n d_n D_n^up D_n^dn."""
-    rt = backflow(wf, r) if wf.has_backflow else r
+    """(log|Psi|, sign Psi) with Psi = exp(J) sum_n d_n D_n^up D_n^dn.
+
+    The backflow map is always applied (it is the identity at w = 0), so that
+    log|Psi| stays differentiable in w there too."""
+    rt = backflow(wf, r)
     Phi = ao_eval(wf, rt) @ wf.mo
     D = slater_dets(wf, Phi)
     Sigma = (wf.det_weight * D[..., 0] * D[..., 1]).sum(-1)
@@ -681,7 +684,8 @@ def energy_grad(wf, r):
     """
     params = list(wf.params().values())
     M = r.shape[0]
-    E, lp, _ = local_energy(wf, r, return_parts=True)
+    E = local_energy(wf, r)
+    lp, _ = log_psi(wf, r)
     Ev = E.mean().detach()
     dE = (E - Ev).detach()
     g = torch.autograd.grad((2.0 * lp * dE).sum() / M, params, allow_unused=True, retain_graph=True)

@@ -112,6 +112,30 @@ class Wavefunction:
         _lib.check(self._lib.qmc_param_layout(self._h, ctypes.byref(n), off))
         return int(n.value), [int(v) for v in off]
 
+    def set_params(self, params):
+        """Replace the variational parameters (flat, param_layout order)."""
+        a = np.ascontiguousarray(params, dtype=np.float64).reshape(-1)
+        n, _ = self.param_layout()
+        assert a.shape[0] == n, (a.shape, n)
+        _lib.check(self._lib.qmc_set_params(self._h, _ptr(a, ctypes.c_double)))
+
+    def energy_grad(self, walkers, n_walkers: int | None = None, want_grad: bool = True, want_forces: bool = True,
+                    stream=None):
+        """(E mean, E variance, gradient [n_param] (Eq. nabla_loss), forces [n_atom, 3] (Eq. force)) for
+        CUDA float64 walkers [3N, ldw]; gradient and forces are CUDA tensors (or None)."""
+        import torch
+
+        assert walkers.is_cuda and walkers.dtype == torch.float64 and walkers.stride(1) == 1
+        W = walkers.shape[1] if n_walkers is None else int(n_walkers)
+        n, _ = self.param_layout()
+        grad = torch.empty(n, dtype=torch.float64, device=walkers.device) if want_grad else None
+        forces = torch.empty(self.mol.n_atom, 3, dtype=torch.float64, device=walkers.device) if want_forces else None
+        stats = np.zeros(2, dtype=np.float64)
+        _lib.check(self._lib.qmc_energy_grad(self._h, _dptr(walkers), W, walkers.stride(0),
+                                             stats.ctypes.data_as(ctypes.c_void_p), _dptr(grad), _dptr(forces),
+                                             _stream_handle(stream)))
+        return float(stats[0]), float(stats[1]), grad, forces
+
     def set_timing(self, enable: bool = True):
         """Record per-stage CUDA events on the call's stream (tracing aid)."""
         _lib.check(self._lib.qmc_set_timing(self._h, 1 if enable else 0))
@@ -186,3 +210,36 @@ class Wavefunction:
                                         int(seed), int(first_walker), int(step_offset), _dptr(log_psi),
                                         _dptr(n_accept), _dptr(workspace), ws_bytes, _stream_handle(stream)))
         return walkers
+
+
+def _torch_energy_function():
+    import torch
+
+    class VariationalEnergy(torch.autograd.Function):
+        """E_v = <E_L> over the given walkers as a differentiable function of
+        the variational parameters and the nuclear coordinates.  Forward sets
+        them on the device wavefunction and runs qmc_energy_grad; backward
+        returns the low-variance gradient estimator (Eq. nabla_loss) for the
+        parameters and minus the force estimator (Eq. force) for the nuclei
+        (the walkers are held fixed, as in the paper's estimators)."""
+
+        @staticmethod
+        def forward(ctx, params, atom_xyz, wf, walkers):
+            wf.set_params(params.detach().cpu().numpy())
+            wf.set_geometry(atom_xyz.detach().cpu().numpy())
+            e_mean, e_var, grad, forces = wf.energy_grad(walkers)
+            ctx.save_for_backward(grad.to(params.device), forces.to(atom_xyz.device))
+            ctx.e_var = e_var
+            return params.new_tensor(e_mean)
+
+        @staticmethod
+        def backward(ctx, g):
+            grad, forces = ctx.saved_tensors
+            return g * grad, -g * forces, None, None
+
+    return VariationalEnergy
+
+
+def variational_energy(params, atom_xyz, wf: Wavefunction, walkers):
+    """Differentiable <E_L> (torch.autograd.Function over qmc_energy_grad)."""
+    return _torch_energy_function().apply(params, atom_xyz, wf, walkers)

@@ -21,7 +21,8 @@ PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "mixed_tf32": QMC_MIXED_TF32, 
 # every exported symbol declared in include/qmc.h
 EXPORTED = (
     "qmc_create_wf", "qmc_destroy_wf", "qmc_set_geometry", "qmc_workspace_size", "qmc_local_energy",
-    "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_set_timing", "qmc_last_stage_ms",
+    "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_energy_grad",
+    "qmc_set_params", "qmc_set_timing", "qmc_last_stage_ms",
     "qmc_last_error",
 )
 
@@ -92,6 +93,10 @@ def load(path: str = LIB_PATH):
     lib.qmc_sample.restype = c_int32
     lib.qmc_param_layout.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int64)]
     lib.qmc_param_layout.restype = c_int32
+    lib.qmc_energy_grad.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.qmc_energy_grad.restype = c_int32
+    lib.qmc_set_params.argtypes = [c_void_p, PD]
+    lib.qmc_set_params.restype = c_int32
     lib.qmc_set_timing.argtypes = [c_void_p, c_int32]
     lib.qmc_set_timing.restype = c_int32
     lib.qmc_last_stage_ms.argtypes = [c_void_p, POINTER(ctypes.c_float), c_int32]

@@ -62,13 +62,26 @@ struct DeviceGuard {
 
 }  // namespace
 
+// Host copy of the inputs of qmc_create_wf (parameters are updated in place by
+// qmc_set_params, geometry by qmc_set_geometry; the device tables are rebuilt
+// from it).
+struct HostSpec {
+  int na = 0, nup = 0, ndn = 0, nao = 0, nmo = 0, ndet = 0;
+  std::vector<double> xyz, z;
+  std::vector<int> ao_atom, ao_kind, ao_pow, prim_start;
+  std::vector<double> prim_exp, prim_coef, mo, det_w;
+  std::vector<int> det_exc;
+  double w0p = 0.25, w0a = 0.5, b = 1.0, w = 0.0;
+};
+
 struct qmc_wf {
   int device = 0;
   int precision = QMC_FP64;
+  HostSpec spec;
   WfDev dev{};
-  // host copies kept for set_geometry / layout queries
-  int n_prim = 0;
-  std::vector<double> atom_xyz, atom_z;
+  // energy-gradient scratch (library-owned)
+  void* gws = nullptr;
+  size_t gws_bytes = 0;
   // device allocations
   void* blob = nullptr;
   // library-owned workspace and host-call staging buffers
@@ -183,72 +196,53 @@ qmc_status launch_status(cudaError_t e, const char* where) {
   return e == cudaSuccess ? QMC_OK : cuda_fail(e, where);
 }
 
-}  // namespace
-
-extern "C" {
-
-qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const qmc_mos* mos, const qmc_dets* dets,
-                         const qmc_jastrow* jastrow, const qmc_options* opt, qmc_wf** out) {
-  if (!atoms || !basis || !mos || !dets || !jastrow || !opt || !out) return fail(QMC_ERR_ARG, "null argument");
-  *out = nullptr;
-  const int na = atoms->n_atom, nup = atoms->n_up, ndn = atoms->n_down;
-  if (na < 1 || na > QMC_MAX_ATOMS || !atoms->xyz || !atoms->z) return fail(QMC_ERR_ARG, "bad atoms");
-  if (nup < 0 || ndn < 0 || nup + ndn < 1) return fail(QMC_ERR_ARG, "bad electron counts");
-  if (nup > QMC_MAX_SPIN_ELECTRONS || ndn > QMC_MAX_SPIN_ELECTRONS)
-    return fail(QMC_ERR_UNSUPPORTED, "more than 8 electrons per spin");
-  const int nao = basis->n_ao, nmo = mos->n_mo;
-  if (nao < 1 || nao > QMC_MAX_AO || !basis->ao_atom || !basis->ao_kind || !basis->ao_pow ||
-      !basis->ao_prim_start || !basis->prim_exp || !basis->prim_coef)
-    return fail(QMC_ERR_ARG, "bad basis");
-  if (nmo < 1 || nmo > QMC_MAX_MO || !mos->coeff) return fail(QMC_ERR_ARG, "bad MO table");
-  if (nmo < nup || nmo < ndn) return fail(QMC_ERR_ARG, "fewer MOs than electrons of one spin");
-  const int prec = opt->precision;
-  if (prec < QMC_FP64 || prec > QMC_MIXED_BF16) return fail(QMC_ERR_ARG, "bad precision");
+// Validate wf->spec and (re)build every device table from it.  On failure the
+// previous tables (if any) are kept.
+qmc_status build_tables(qmc_wf* wf) {
+  const HostSpec& h = wf->spec;
+  const int na = h.na, nup = h.nup, ndn = h.ndn, nao = h.nao, nmo = h.nmo, ndet = h.ndet;
+  const int prec = wf->precision;
   const bool tc = prec == QMC_MIXED_TF32 || prec == QMC_MIXED_BF16;
   if (tc && (nmo > 16 || nao > 64)) return fail(QMC_ERR_UNSUPPORTED, "tensor-core forms need n_mo <= 16, n_ao <= 64");
   if (prec == QMC_MIXED_BF16) return fail(QMC_ERR_UNSUPPORTED, "BF16 form not built");
-  if (!dets->weight || !dets->exc || dets->n_det < 1 || dets->n_det > kMaxDets)
-    return fail(QMC_ERR_ARG, "bad determinant list");
-  if (jastrow->backflow_w != 0.0) return fail(QMC_ERR_UNSUPPORTED, "backflow form not built");
-
-  qmc_wf* wf = new qmc_wf();
-  wf->device = opt->device;
-  wf->precision = prec;
-  WfDev& d = wf->dev;
+  WfDev d{};
   d.n_atom = na;
   d.n_up = nup;
   d.n_down = ndn;
   d.n_elec = nup + ndn;
   d.n_ao = nao;
   d.n_mo = nmo;
-  d.w0_par = jastrow->w0_par;
-  d.w0_anti = jastrow->w0_anti;
-  d.jb = jastrow->b;
-  d.bf_w = jastrow->backflow_w;
+  d.n_det = ndet;
+  d.w0_par = h.w0p;
+  d.w0_anti = h.w0a;
+  d.jb = h.b;
+  d.bf_w = h.w;
   for (int a = 0; a < na; ++a) {
-    for (int k = 0; k < 3; ++k) d.atom_xyz[a][k] = atoms->xyz[3 * a + k];
-    d.atom_z[a] = atoms->z[a];
+    for (int k = 0; k < 3; ++k) d.atom_xyz[a][k] = h.xyz[3 * a + k];
+    d.atom_z[a] = h.z[a];
   }
   d.vnn = vnn_of(d);
-  wf->atom_xyz.assign(atoms->xyz, atoms->xyz + 3 * na);
-  wf->atom_z.assign(atoms->z, atoms->z + na);
+  if (h.w != 0.0) {
+    if (prec != QMC_FP64) return fail(QMC_ERR_UNSUPPORTED, "backflow wavefunctions run in the FP64 form only");
+    if (!general_supported(d))
+      return fail(QMC_ERR_UNSUPPORTED, "backflow needs one determinant, <= 8 electrons, <= 4 per spin");
+  }
 
   // ---- basis: shells, normalisation, angular factors
   std::vector<ShellDev> shells;
   std::vector<int> ao_pow(nao);
   std::vector<double> ang(nao);
-  wf->n_prim = basis->ao_prim_start[nao];
   for (int b = 0; b < nao; ++b) {
-    const int atom = basis->ao_atom[b], kind = basis->ao_kind[b];
-    const int kx = basis->ao_pow[4 * b], ky = basis->ao_pow[4 * b + 1], kz = basis->ao_pow[4 * b + 2],
-              kn = basis->ao_pow[4 * b + 3];
-    const int s0 = basis->ao_prim_start[b], s1 = basis->ao_prim_start[b + 1];
+    const int atom = h.ao_atom[b], kind = h.ao_kind[b];
+    const int kx = h.ao_pow[4 * b], ky = h.ao_pow[4 * b + 1], kz = h.ao_pow[4 * b + 2], kn = h.ao_pow[4 * b + 3];
+    const int s0 = h.prim_start[b], s1 = h.prim_start[b + 1];
     if (atom < 0 || atom >= na || (kind != 0 && kind != 1) || kx < 0 || ky < 0 || kz < 0 || kn < 0 || kx > 4 ||
         ky > 4 || kz > 4 || kx + ky + kz > 4 || kn > 8 || s1 <= s0 || (kind == 0 && s1 - s0 != 1) ||
-        s1 - s0 > QMC_MAX_PRIM) {
-      delete wf;
+        s1 - s0 > QMC_MAX_PRIM)
       return fail(QMC_ERR_ARG, "bad AO " + std::to_string(b));
-    }
+    for (int p = s0; p < s1; ++p)
+      if (!(h.prim_exp[p] > 0.0) || !std::isfinite(h.prim_exp[p]))
+        return fail(QMC_ERR_ARG, "AO exponents must be positive and finite (AO " + std::to_string(b) + ")");
     const int l = kx + ky + kz;
     ao_pow[b] = kx | (ky << 4) | (kz << 8);
     const double df = dfact(2 * kx - 1) * dfact(2 * ky - 1) * dfact(2 * kz - 1);
@@ -261,19 +255,19 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
     sh.ao_first = b;
     sh.n_ao = 1;
     if (kind == 0) {
-      const double zeta = basis->prim_exp[s0];
+      const double zeta = h.prim_exp[s0];
       const int n = kn + l + 1;
       ang[b] = std::sqrt(dfact(2 * l + 1) / (4.0 * M_PI * df));
       sh.expo[0] = zeta;
-      sh.coef[0] = basis->prim_coef[s0] * std::pow(2.0 * zeta, n + 0.5) / std::sqrt(fact(2 * n));
+      sh.coef[0] = h.prim_coef[s0] * std::pow(2.0 * zeta, n + 0.5) / std::sqrt(fact(2 * n));
       sh.expo_f[0] = (float)sh.expo[0];
       sh.coef_f[0] = (float)sh.coef[0];
     } else {
       ang[b] = 1.0 / std::sqrt(df);
       for (int p = s0; p < s1; ++p) {
-        const double al = basis->prim_exp[p];
+        const double al = h.prim_exp[p];
         sh.expo[p - s0] = al;
-        sh.coef[p - s0] = basis->prim_coef[p] * std::pow(2.0 * al / M_PI, 0.75) * std::pow(4.0 * al, 0.5 * l);
+        sh.coef[p - s0] = h.prim_coef[p] * std::pow(2.0 * al / M_PI, 0.75) * std::pow(4.0 * al, 0.5 * l);
         sh.expo_f[p - s0] = (float)sh.expo[p - s0];
         sh.coef_f[p - s0] = (float)sh.coef[p - s0];
       }
@@ -290,10 +284,7 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
     }
     if (!merged) shells.push_back(sh);
   }
-  if ((int)shells.size() > kMaxShells) {
-    delete wf;
-    return fail(QMC_ERR_UNSUPPORTED, "too many shells");
-  }
+  if ((int)shells.size() > kMaxShells) return fail(QMC_ERR_UNSUPPORTED, "too many shells");
   d.n_shell = (int)shells.size();
   {  // balance the AO count between the four thread parts of the tensor-core AO stage
     int acc = 0, part = 1;
@@ -308,7 +299,7 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
   std::vector<float> mo32((size_t)nao * nmo);
   for (int b = 0; b < nao; ++b)
     for (int m = 0; m < nmo; ++m) {
-      mo64[(size_t)b * nmo + m] = mos->coeff[(size_t)b * nmo + m] * ang[b];
+      mo64[(size_t)b * nmo + m] = h.mo[(size_t)b * nmo + m] * ang[b];
       mo32[(size_t)b * nmo + m] = (float)mo64[(size_t)b * nmo + m];
     }
 
@@ -316,16 +307,15 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
   // stored sorted by (rank up, rank down): the determinant stage hands
   // consecutive determinants to the lanes of a warp, and a sorted list keeps
   // their rank branches uniform (the sum is order independent).
-  std::vector<int> order(dets->n_det);
-  for (int n = 0; n < dets->n_det; ++n) order[n] = n;
+  std::vector<int> order(ndet);
+  for (int n = 0; n < ndet; ++n) order[n] = n;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    const int ka = dets->exc[a * 10] * 3 + dets->exc[a * 10 + 5], kb = dets->exc[b * 10] * 3 + dets->exc[b * 10 + 5];
-    return ka < kb;
+    return h.det_exc[a * 10] * 3 + h.det_exc[a * 10 + 5] < h.det_exc[b * 10] * 3 + h.det_exc[b * 10 + 5];
   });
-  std::vector<double> det_w_sorted(dets->n_det);
-  for (int n = 0; n < dets->n_det; ++n) det_w_sorted[n] = dets->weight[order[n]];
+  std::vector<double> det_w_sorted(ndet);
+  for (int n = 0; n < ndet; ++n) det_w_sorted[n] = h.det_w[order[n]];
   std::vector<int> exc(2 * kMaxExc * 5, -1);
-  std::vector<int> det_idx(2 * dets->n_det);
+  std::vector<int> det_idx(2 * ndet);
   for (int s = 0; s < 2; ++s) {
     const int ns = s == 0 ? nup : ndn;
     std::map<std::vector<int>, int> seen;
@@ -333,27 +323,21 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
     seen[g] = 0;
     for (int k = 0; k < 5; ++k) exc[(s * kMaxExc + 0) * 5 + k] = g[k];
     int h_lo = ns, p_hi = ns;
-    for (int n = 0; n < dets->n_det; ++n) {
+    for (int n = 0; n < ndet; ++n) {
       const int src = order[n];
-      std::vector<int> e(dets->exc + (src * 2 + s) * 5, dets->exc + (src * 2 + s) * 5 + 5);
+      std::vector<int> e(h.det_exc.begin() + (src * 2 + s) * 5, h.det_exc.begin() + (src * 2 + s) * 5 + 5);
       const int rank = e[0];
       bool ok = rank >= 0 && rank <= 2;
       if (ok && rank == 0) e = g;
       if (ok && rank >= 1) ok = e[1] >= 0 && e[1] < ns && e[3] >= ns && e[3] < nmo;
       if (ok && rank == 2) ok = e[2] > e[1] && e[2] < ns && e[4] > e[3] && e[4] < nmo;
       if (ok && rank == 1) { e[2] = -1; e[4] = -1; }
-      if (!ok) {
-        delete wf;
-        return fail(QMC_ERR_ARG, "bad excitation record of determinant " + std::to_string(src));
-      }
+      if (!ok) return fail(QMC_ERR_ARG, "bad excitation record of determinant " + std::to_string(src));
       auto it = seen.find(e);
       int idx;
       if (it == seen.end()) {
         idx = (int)seen.size();
-        if (idx >= kMaxExc) {
-          delete wf;
-          return fail(QMC_ERR_UNSUPPORTED, "too many distinct excitations");
-        }
+        if (idx >= kMaxExc) return fail(QMC_ERR_UNSUPPORTED, "too many distinct excitations");
         seen[e] = idx;
         for (int k = 0; k < 5; ++k) exc[(s * kMaxExc + idx) * 5 + k] = e[k];
       } else {
@@ -369,15 +353,9 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
     d.nh[s] = ns - h_lo;
     d.nv[s] = p_hi - ns;
   }
-  d.n_det = dets->n_det;
   d.tab_elems = 2 * (d.nh[0] * d.nv[0] + d.nh[1] * d.nv[1]);
-  {
-    const int ns = std::max(nup, ndn);
-    if (det_smem_bytes(d, ns, det_team_size(d), true) > 227 * 1024) {
-      delete wf;
-      return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
-    }
-  }
+  if (det_smem_bytes(d, std::max(nup, ndn), det_team_size(d), true) > 227 * 1024)
+    return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
 
   // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
   d.k_pad = tc ? (int)round_up(nao, 8) : 0;
@@ -404,25 +382,25 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
       {shells.data(), sizeof(ShellDev) * shells.size()}, {ao_pow.data(), sizeof(int) * nao},
       {mo64.data(), sizeof(double) * mo64.size()},       {mo32.data(), sizeof(float) * mo32.size()},
       {exc.data(), sizeof(int) * exc.size()},           {det_idx.data(), sizeof(int) * det_idx.size()},
-      {det_w_sorted.data(), sizeof(double) * dets->n_det},      {tc_hi.data(), sizeof(uint32_t) * tc_hi.size()},
-      {tc_lo.data(), sizeof(uint32_t) * tc_lo.size()}};
+      {det_w_sorted.data(), sizeof(double) * ndet},      {tc_hi.data(), sizeof(uint32_t) * tc_hi.size()},
+      {tc_lo.data(), sizeof(uint32_t) * tc_lo.size()},  {ang.data(), sizeof(double) * nao},
+      {h.prim_start.data(), sizeof(int) * (nao + 1)}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
-  cudaError_t e = cudaMalloc(&wf->blob, total);
+  void* blob = nullptr;
+  cudaError_t e = cudaMalloc(&blob, total);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    delete wf;
     return fail(QMC_ERR_OOM, std::string("table allocation: ") + cudaGetErrorString(e));
   }
   std::vector<char*> ptr;
-  char* base = static_cast<char*>(wf->blob);
+  char* base = static_cast<char*>(blob);
   for (auto& p : parts) {
     ptr.push_back(base);
     if (p.second) {
       e = cudaMemcpy(base, p.first, p.second, cudaMemcpyHostToDevice);
       if (e != cudaSuccess) {
-        cudaFree(wf->blob);
-        delete wf;
+        cudaFree(blob);
         return cuda_fail(e, "table upload");
       }
     }
@@ -437,6 +415,67 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
   d.det_w = reinterpret_cast<const double*>(ptr[6]);
   d.mo_tc_hi = reinterpret_cast<const uint32_t*>(ptr[7]);
   d.mo_tc_lo = reinterpret_cast<const uint32_t*>(ptr[8]);
+  d.ao_ang = reinterpret_cast<const double*>(ptr[9]);
+  d.ao_prim = reinterpret_cast<const int*>(ptr[10]);
+  // the previous tables may still be read by work in flight on any stream
+  if (wf->blob) {
+    cudaDeviceSynchronize();
+    cudaFree(wf->blob);
+  }
+  wf->blob = blob;
+  wf->dev = d;
+  return QMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const qmc_mos* mos, const qmc_dets* dets,
+                         const qmc_jastrow* jastrow, const qmc_options* opt, qmc_wf** out) {
+  if (!atoms || !basis || !mos || !dets || !jastrow || !opt || !out) return fail(QMC_ERR_ARG, "null argument");
+  *out = nullptr;
+  const int na = atoms->n_atom, nup = atoms->n_up, ndn = atoms->n_down;
+  if (na < 1 || na > QMC_MAX_ATOMS || !atoms->xyz || !atoms->z) return fail(QMC_ERR_ARG, "bad atoms");
+  if (nup < 0 || ndn < 0 || nup + ndn < 1) return fail(QMC_ERR_ARG, "bad electron counts");
+  if (nup > QMC_MAX_SPIN_ELECTRONS || ndn > QMC_MAX_SPIN_ELECTRONS)
+    return fail(QMC_ERR_UNSUPPORTED, "more than 8 electrons per spin");
+  const int nao = basis->n_ao, nmo = mos->n_mo;
+  if (nao < 1 || nao > QMC_MAX_AO || !basis->ao_atom || !basis->ao_kind || !basis->ao_pow ||
+      !basis->ao_prim_start || !basis->prim_exp || !basis->prim_coef)
+    return fail(QMC_ERR_ARG, "bad basis");
+  if (nmo < 1 || nmo > QMC_MAX_MO || !mos->coeff) return fail(QMC_ERR_ARG, "bad MO table");
+  if (nmo < nup || nmo < ndn) return fail(QMC_ERR_ARG, "fewer MOs than electrons of one spin");
+  const int prec = opt->precision;
+  if (prec < QMC_FP64 || prec > QMC_MIXED_BF16) return fail(QMC_ERR_ARG, "bad precision");
+  if (!dets->weight || !dets->exc || dets->n_det < 1 || dets->n_det > kMaxDets)
+    return fail(QMC_ERR_ARG, "bad determinant list");
+  const int n_prim = basis->ao_prim_start[nao];
+  if (basis->ao_prim_start[0] != 0 || n_prim < nao || n_prim > nao * QMC_MAX_PRIM)
+    return fail(QMC_ERR_ARG, "bad primitive offsets");
+
+  qmc_wf* wf = new qmc_wf();
+  wf->device = opt->device;
+  wf->precision = prec;
+  HostSpec& h = wf->spec;
+  h.na = na; h.nup = nup; h.ndn = ndn; h.nao = nao; h.nmo = nmo; h.ndet = dets->n_det;
+  h.xyz.assign(atoms->xyz, atoms->xyz + 3 * na);
+  h.z.assign(atoms->z, atoms->z + na);
+  h.ao_atom.assign(basis->ao_atom, basis->ao_atom + nao);
+  h.ao_kind.assign(basis->ao_kind, basis->ao_kind + nao);
+  h.ao_pow.assign(basis->ao_pow, basis->ao_pow + 4 * nao);
+  h.prim_start.assign(basis->ao_prim_start, basis->ao_prim_start + nao + 1);
+  h.prim_exp.assign(basis->prim_exp, basis->prim_exp + n_prim);
+  h.prim_coef.assign(basis->prim_coef, basis->prim_coef + n_prim);
+  h.mo.assign(mos->coeff, mos->coeff + (size_t)nao * nmo);
+  h.det_w.assign(dets->weight, dets->weight + dets->n_det);
+  h.det_exc.assign(dets->exc, dets->exc + 10 * (size_t)dets->n_det);
+  h.w0p = jastrow->w0_par; h.w0a = jastrow->w0_anti; h.b = jastrow->b; h.w = jastrow->backflow_w;
+  qmc_status st = build_tables(wf);
+  if (st != QMC_OK) {
+    delete wf;
+    return st;
+  }
   *out = wf;
   return QMC_OK;
 }
@@ -448,6 +487,7 @@ void qmc_destroy_wf(qmc_wf* wf) {
     if (wf->blob) cudaFree(wf->blob);
     if (wf->ws) cudaFree(wf->ws);
     if (wf->stage) cudaFree(wf->stage);
+    if (wf->gws) cudaFree(wf->gws);
     for (auto& e : wf->ev)
       if (e) cudaEventDestroy(e);
   }
@@ -456,10 +496,14 @@ void qmc_destroy_wf(qmc_wf* wf) {
 
 qmc_status qmc_set_geometry(qmc_wf* wf, const double* xyz) {
   if (!wf || !xyz) return fail(QMC_ERR_ARG, "null argument");
+  std::lock_guard<std::mutex> lock(wf->mu);
   for (int a = 0; a < wf->dev.n_atom; ++a)
-    for (int k = 0; k < 3; ++k) wf->dev.atom_xyz[a][k] = xyz[3 * a + k];
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(xyz[3 * a + k])) return fail(QMC_ERR_ARG, "non-finite nuclear coordinate");
+      wf->dev.atom_xyz[a][k] = xyz[3 * a + k];
+    }
   wf->dev.vnn = vnn_of(wf->dev);
-  wf->atom_xyz.assign(xyz, xyz + 3 * wf->dev.n_atom);
+  wf->spec.xyz.assign(xyz, xyz + 3 * wf->dev.n_atom);
   return QMC_OK;
 }
 
@@ -472,7 +516,7 @@ qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[
   if (!wf || !n_param) return fail(QMC_ERR_ARG, "null argument");
   int64_t o[6];
   o[0] = 0;
-  o[1] = o[0] + wf->n_prim;
+  o[1] = o[0] + (int64_t)wf->spec.prim_exp.size();
   o[2] = o[1] + (int64_t)wf->dev.n_ao * wf->dev.n_mo;
   o[3] = o[2] + wf->dev.n_det;
   o[4] = o[3] + 1;
@@ -491,6 +535,15 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
                             int* err_flag, bool kinetic, double* e_loc, double* log_psi, cudaStream_t st) {
   const WfDev& d = wf->dev;
   mark(wf, 0, st);
+  if (d.bf_w != 0.0) {  // backflow: one general kernel (Jastrow, orbitals, Eq. nabla_d, E_L)
+    qmc_status s = launch_status(launch_eloc_general(d, walkers, W, ldw, kinetic, e_loc, log_psi, st), "general");
+    if (s) return s;
+    mark(wf, 1, st);
+    mark(wf, 2, st);
+    mark(wf, 3, st);
+    if (wf->timing) wf->timed_once = true;
+    return QMC_OK;
+  }
   qmc_status s = launch_status(launch_jastrow(d, wf->precision, walkers, W, ldw, ws, kinetic, st), "jastrow");
   if (s) return s;
   mark(wf, 1, st);
@@ -653,6 +706,85 @@ qmc_status qmc_local_energy_noalloc(qmc_wf* wf, const double* walkers, int64_t n
   Workspace ws = carve(wf, base, n_walkers, &err_flag);
   return eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, log_psi,
                    static_cast<cudaStream_t>(stream));
+}
+
+qmc_status qmc_set_params(qmc_wf* wf, const double* params) {
+  if (!wf || !params) return fail(QMC_ERR_ARG, "null argument");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  HostSpec old = wf->spec;
+  HostSpec& h = wf->spec;
+  size_t k = 0;
+  for (auto& v : h.prim_exp) v = params[k++];
+  for (auto& v : h.mo) v = params[k++];
+  for (auto& v : h.det_w) v = params[k++];
+  h.b = params[k++];
+  h.w = params[k++];
+  for (size_t q = 0; q < k; ++q)
+    if (!std::isfinite(params[q])) {
+      wf->spec = old;
+      return fail(QMC_ERR_ARG, "non-finite parameter " + std::to_string(q));
+    }
+  qmc_status st = build_tables(wf);
+  if (st != QMC_OK) wf->spec = old;
+  return st;
+}
+
+qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_stats,
+                           double* grad, double* forces, void* stream) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  if (n_walkers < 1 || ldw < n_walkers) return fail(QMC_ERR_ARG, "need n_walkers >= 1 and ldw >= n_walkers");
+  if (!walkers || !e_stats) return fail(QMC_ERR_ARG, "null walkers or e_stats");
+  if (wf->precision != QMC_FP64) return fail(QMC_ERR_UNSUPPORTED, "energy gradients are computed in the FP64 form");
+  if (!general_supported(wf->dev))
+    return fail(QMC_ERR_UNSUPPORTED, "energy gradients need one determinant, <= 8 electrons, <= 4 per spin");
+  int64_t n_param = 0;
+  qmc_param_layout(wf, &n_param, nullptr);
+  if (grad && grad_smem_bytes(wf->dev, (int)n_param) > 227 * 1024)
+    return fail(QMC_ERR_UNSUPPORTED, "too many parameters for the gradient kernel's shared memory");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* base;
+  qmc_status s = get_workspace(wf, n_walkers, nullptr, 0, &base);
+  if (s) return s;
+  int* err_flag;
+  Workspace ws = carve(wf, base, n_walkers, &err_flag);
+  // gradient scratch: e_loc [W], stats [2], block partial sums
+  const int64_t nb = general_blocks(n_walkers);
+  const size_t need = align256(sizeof(double) * n_walkers) + align256(sizeof(double) * 2) +
+                      align256(sizeof(double) * nb * std::max<int64_t>(n_param, 3 * wf->dev.n_atom));
+  if (wf->gws_bytes < need) {
+    if (wf->gws) cudaFree(wf->gws);
+    wf->gws = nullptr;
+    wf->gws_bytes = 0;
+    cudaError_t e = cudaMalloc(&wf->gws, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QMC_ERR_OOM, std::string("gradient scratch allocation: ") + cudaGetErrorString(e));
+    }
+    wf->gws_bytes = need;
+  }
+  char* p = static_cast<char*>(wf->gws);
+  double* e_loc = reinterpret_cast<double*>(p);
+  double* stats = reinterpret_cast<double*>(p + align256(sizeof(double) * n_walkers));
+  double* partial = reinterpret_cast<double*>(p + align256(sizeof(double) * n_walkers) + align256(16));
+  s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, nullptr, st);
+  if (s) return s;
+  s = launch_status(launch_mean_var(e_loc, n_walkers, stats, st), "mean/variance");
+  if (s) return s;
+  if (grad) {
+    s = launch_status(launch_grad(wf->dev, walkers, n_walkers, ldw, e_loc, stats, wf->dev.ao_ang, wf->dev.ao_prim,
+                                  (int)n_param, partial, grad, st),
+                      "parameter gradient");
+    if (s) return s;
+  }
+  if (forces) {
+    s = launch_status(launch_forces(wf->dev, walkers, n_walkers, ldw, e_loc, stats, partial, forces, st), "forces");
+    if (s) return s;
+  }
+  cudaError_t e = cudaMemcpyAsync(e_stats, stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? QMC_OK : cuda_fail(e, "energy statistics");
 }
 
 qmc_status qmc_set_timing(qmc_wf* wf, int32_t enable) {

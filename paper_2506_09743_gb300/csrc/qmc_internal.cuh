@@ -60,6 +60,8 @@ struct WfDev {
   // core-matrix layout [n_mo_pad=16][k_pad], 32-bit words
   const uint32_t* mo_tc_hi;
   const uint32_t* mo_tc_lo;
+  const double* ao_ang;  // [n_ao] angular normalisation factors (folded into mo64)
+  const int* ao_prim;    // [n_ao + 1] first input primitive of each AO (gradient layout)
   int k_pad;        // AO dimension padded to a multiple of the MMA K step
   int shell_part[5];  // tensor-core AO stage: thread part q takes shells [part[q], part[q+1])
 };
@@ -105,6 +107,19 @@ __device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
 
 int det_team_size(const WfDev& wf);
 size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin);
+
+// general single-determinant FP64 path (backflow, forces, parameter gradient)
+bool general_supported(const WfDev& wf);
+int general_blocks(int64_t W);
+size_t grad_smem_bytes(const WfDev& wf, int n_param);
+cudaError_t launch_eloc_general(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, bool kinetic,
+                                double* e_loc, double* log_psi, cudaStream_t st);
+cudaError_t launch_mean_var(const double* x, int64_t W, double* stats, cudaStream_t st);
+cudaError_t launch_forces(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const double* e_loc,
+                          const double* stats, double* partial, double* forces, cudaStream_t st);
+cudaError_t launch_grad(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const double* e_loc,
+                        const double* stats, const double* ang, const int* prim_start, int n_param, double* partial,
+                        double* grad, cudaStream_t st);
 
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
