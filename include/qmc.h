@@ -258,6 +258,74 @@ qmc_status qmc_set_timing(qmc_wf* wf, int32_t enable);
  * QMC_ERR_ARG if timing was never enabled or nothing was timed yet. */
 qmc_status qmc_last_stage_ms(qmc_wf* wf, float* ms, int32_t n);
 
+/* ---- Continuous-batching request server --------------------------------
+ * A request evaluates one registered wavefunction (a molecule at one
+ * geometry): its walkers are uploaded or drawn on the device, n_steps
+ * Metropolis steps are run (App. B), then the local energies (Eq. Hmol) and
+ * their mean and variance, the Monte Carlo estimate of Sec. 1.  Requests are
+ * queued on submission and admitted, in arrival order, as soon as one of
+ * max_in_flight stream slots is free and the request's device memory
+ * (walkers, scratch) fits in the server's arena of hbm_budget_bytes; admitted
+ * requests run concurrently on their own streams.  The arena is allocated
+ * once at creation: admission allocates nothing.  A result depends only on
+ * the request, not on the other requests in flight.  Single host thread:
+ * call the server functions from one thread. */
+typedef struct qmc_server qmc_server;
+
+typedef struct {
+  int32_t wf_id;          /* from qmc_server_add_wf */
+  int64_t n_walkers;      /* >= 1 */
+  int32_t n_steps;        /* Metropolis steps before the energy (>= 0) */
+  double step;            /* proposal width, bohr (> 0 if n_steps > 0) */
+  uint64_t seed;          /* Philox key of the chain (and of the initial positions) */
+  const double* walkers;  /* host [3N][n_walkers] initial positions, kept valid until the
+                             result is returned; or NULL: electron i drawn N(home nucleus,
+                             1 bohr^2) on the device (nuclei dealt by Z, spins alternating,
+                             Philox step index 2^64 - 1) */
+} qmc_request;
+
+typedef struct {
+  int64_t ticket;
+  int32_t status;       /* QMC_OK or the error of this request */
+  int32_t wf_id;
+  int64_t n_walkers;
+  double e_mean;        /* mean local energy, Ha */
+  double e_var;         /* variance of the local energy, Ha^2 */
+  double accept_rate;   /* accepted moves / (n_walkers n_steps) */
+  double t_submit;      /* qmc_server_clock() at submission, admission and completion, s */
+  double t_admit;
+  double t_done;
+} qmc_result;
+
+/* Create a server on `device` with a device-memory arena of hbm_budget_bytes
+ * and max_in_flight concurrent request slots (streams). */
+qmc_status qmc_server_create(int32_t device, size_t hbm_budget_bytes, int32_t max_in_flight, qmc_server** out);
+
+/* Wait for the requests in flight and free the server (not the wavefunctions). */
+void qmc_server_destroy(qmc_server* srv);
+
+/* Register a wavefunction (not owned; keep it alive while the server runs). */
+qmc_status qmc_server_add_wf(qmc_server* srv, qmc_wf* wf, int32_t* wf_id);
+
+/* Queue a request (never blocks).  QMC_ERR_OOM if it can never fit. */
+qmc_status qmc_server_submit(qmc_server* srv, const qmc_request* req, int64_t* ticket);
+
+/* Retire finished requests and admit queued ones; returns the numbers in
+ * flight and still queued.  Call it repeatedly (it does not block). */
+qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n_queued);
+
+/* Move up to `capacity` finished results into out (oldest first). */
+qmc_status qmc_server_results(qmc_server* srv, qmc_result* out, int32_t capacity, int32_t* n_out);
+
+/* Bytes of the arena currently free. */
+size_t qmc_server_free_bytes(const qmc_server* srv);
+
+/* The server's monotonic clock, seconds. */
+double qmc_server_clock(void);
+
+/* Message of the last failed qmc_server_* call on this thread. */
+const char* qmc_server_last_error(void);
+
 /* Message of the last failed call on this thread ("" if none yet).  The
  * pointer stays valid until the next library call on the same thread. */
 const char* qmc_last_error(void);

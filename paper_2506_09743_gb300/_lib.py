@@ -22,7 +22,9 @@ PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "mixed_tf32": QMC_MIXED_TF32, 
 EXPORTED = (
     "qmc_create_wf", "qmc_destroy_wf", "qmc_set_geometry", "qmc_workspace_size", "qmc_local_energy",
     "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_energy_grad",
-    "qmc_set_params", "qmc_set_timing", "qmc_last_stage_ms",
+    "qmc_set_params", "qmc_server_create", "qmc_server_destroy", "qmc_server_add_wf", "qmc_server_submit",
+    "qmc_server_progress", "qmc_server_results", "qmc_server_free_bytes", "qmc_server_clock",
+    "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms",
     "qmc_last_error",
 )
 
@@ -53,6 +55,17 @@ class Jastrow(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("device", c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("wf_id", c_int32), ("n_walkers", c_int64), ("n_steps", c_int32), ("step", c_double),
+                ("seed", c_uint64), ("walkers", c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("ticket", c_int64), ("status", c_int32), ("wf_id", c_int32), ("n_walkers", c_int64),
+                ("e_mean", c_double), ("e_var", c_double), ("accept_rate", c_double), ("t_submit", c_double),
+                ("t_admit", c_double), ("t_done", c_double)]
 
 
 class QmcError(RuntimeError):
@@ -101,6 +114,24 @@ def load(path: str = LIB_PATH):
     lib.qmc_set_timing.restype = c_int32
     lib.qmc_last_stage_ms.argtypes = [c_void_p, POINTER(ctypes.c_float), c_int32]
     lib.qmc_last_stage_ms.restype = c_int32
+    lib.qmc_server_create.argtypes = [c_int32, c_size_t, c_int32, POINTER(c_void_p)]
+    lib.qmc_server_create.restype = c_int32
+    lib.qmc_server_destroy.argtypes = [c_void_p]
+    lib.qmc_server_destroy.restype = None
+    lib.qmc_server_add_wf.argtypes = [c_void_p, c_void_p, POINTER(c_int32)]
+    lib.qmc_server_add_wf.restype = c_int32
+    lib.qmc_server_submit.argtypes = [c_void_p, POINTER(Request), POINTER(c_int64)]
+    lib.qmc_server_submit.restype = c_int32
+    lib.qmc_server_progress.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int32)]
+    lib.qmc_server_progress.restype = c_int32
+    lib.qmc_server_results.argtypes = [c_void_p, POINTER(Result), c_int32, POINTER(c_int32)]
+    lib.qmc_server_results.restype = c_int32
+    lib.qmc_server_free_bytes.argtypes = [c_void_p]
+    lib.qmc_server_free_bytes.restype = c_size_t
+    lib.qmc_server_clock.argtypes = []
+    lib.qmc_server_clock.restype = c_double
+    lib.qmc_server_last_error.argtypes = []
+    lib.qmc_server_last_error.restype = c_char_p
     lib.qmc_last_error.argtypes = []
     lib.qmc_last_error.restype = c_char_p
     _lib = lib
@@ -110,4 +141,10 @@ def load(path: str = LIB_PATH):
 def check(status: int):
     if status != QMC_OK:
         msg = _lib.qmc_last_error().decode() if _lib is not None else ""
+        raise QmcError(status, msg)
+
+
+def check_server(status: int):
+    if status != QMC_OK:
+        msg = _lib.qmc_server_last_error().decode() if _lib is not None else ""
         raise QmcError(status, msg)

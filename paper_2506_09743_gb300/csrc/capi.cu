@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "qmc_internal.cuh"
+#include "wf_internal.cuh"
 
 using namespace qmc;
 
@@ -47,54 +48,11 @@ double fact(int n) {
   return r;
 }
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
+
 
 }  // namespace
 
-// Host copy of the inputs of qmc_create_wf (parameters are updated in place by
-// qmc_set_params, geometry by qmc_set_geometry; the device tables are rebuilt
-// from it).
-struct HostSpec {
-  int na = 0, nup = 0, ndn = 0, nao = 0, nmo = 0, ndet = 0;
-  std::vector<double> xyz, z;
-  std::vector<int> ao_atom, ao_kind, ao_pow, prim_start;
-  std::vector<double> prim_exp, prim_coef, mo, det_w;
-  std::vector<int> det_exc;
-  double w0p = 0.25, w0a = 0.5, b = 1.0, w = 0.0;
-};
 
-struct qmc_wf {
-  int device = 0;
-  int precision = QMC_FP64;
-  HostSpec spec;
-  WfDev dev{};
-  // energy-gradient scratch (library-owned)
-  void* gws = nullptr;
-  size_t gws_bytes = 0;
-  // device allocations
-  void* blob = nullptr;
-  // library-owned workspace and host-call staging buffers
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  double* stage = nullptr;
-  size_t stage_bytes = 0;
-  // optional per-stage timing events
-  bool timing = false;
-  bool timed_once = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  std::mutex mu;
-};
 
 namespace {
 

@@ -69,6 +69,58 @@ __global__ void __launch_bounds__(128) k_accept(int n3, double* __restrict__ wal
   }
 }
 
+// Initial walkers for the serving loop: electron i at R_home(i) + N(0, 1) per
+// coordinate, Gaussians from the same Philox stream layout with the reserved
+// step index 2^64 - 1 (never reached by a chain).
+__global__ void __launch_bounds__(128) k_init_walkers(InitSpec spec, int64_t W, int64_t ldw,
+                                                      double* __restrict__ walkers, uint64_t seed) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const int n3 = 3 * spec.n_elec;
+  const double two_pi = 6.283185307179586;
+  for (int j = 0; 4 * j < n3; ++j) {
+    const u4 x = philox4x32_10(u4{(uint32_t)j, (uint32_t)w, 0xFFFFFFFFu, 0xFFFFFFFFu}, (uint32_t)seed,
+                               (uint32_t)(seed >> 32));
+    double z[4];
+    const double r1 = sqrt(-2.0 * log(u01(x.x))), r2 = sqrt(-2.0 * log(u01(x.z)));
+    double s1, c1, s2, c2;
+    sincos(two_pi * u01(x.y), &s1, &c1);
+    sincos(two_pi * u01(x.w), &s2, &c2);
+    z[0] = r1 * c1; z[1] = r1 * s1; z[2] = r2 * c2; z[3] = r2 * s2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * j + q;
+      if (k < n3) walkers[(int64_t)k * ldw + w] = spec.home_xyz[k / 3][k % 3] + z[q];
+    }
+  }
+}
+
+// sum of the per-walker acceptance counts into out[0] (fixed order)
+__global__ void k_sum_counts(const int64_t* __restrict__ c, int64_t W, double* __restrict__ out) {
+  __shared__ long long red[256];
+  long long s = 0;
+  for (int64_t k = threadIdx.x; k < W; k += blockDim.x) s += c[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = (double)red[0];
+}
+
+cudaError_t launch_init_walkers(const InitSpec& spec, int64_t W, int64_t ldw, double* walkers, uint64_t seed,
+                                cudaStream_t st) {
+  if (W == 0) return cudaSuccess;
+  k_init_walkers<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(spec, W, ldw, walkers, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_counts(const int64_t* counts, int64_t W, double* out, cudaStream_t st) {
+  k_sum_counts<<<1, 256, 0, st>>>(counts, W, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_propose(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                            double step, uint64_t seed, uint64_t first_walker, uint64_t gstep, cudaStream_t st) {
   if (W == 0) return cudaSuccess;

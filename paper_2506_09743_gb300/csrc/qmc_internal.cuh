@@ -108,6 +108,15 @@ __device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
 int det_team_size(const WfDev& wf);
 size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin);
 
+// initial walker positions for the serving loop: home nucleus per electron
+struct InitSpec {
+  int n_elec;
+  double home_xyz[2 * QMC_MAX_SPIN_ELECTRONS][3];
+};
+cudaError_t launch_init_walkers(const InitSpec& spec, int64_t W, int64_t ldw, double* walkers, uint64_t seed,
+                                cudaStream_t st);
+cudaError_t launch_sum_counts(const int64_t* counts, int64_t W, double* out, cudaStream_t st);
+
 // general single-determinant FP64 path (backflow, forces, parameter gradient)
 bool general_supported(const WfDev& wf);
 int general_blocks(int64_t W);
