@@ -37,8 +37,8 @@ METRIC = "walker local-energy evals/s (CO, 14 e-) vs FP64 plain; p99 request lat
 UNIT = "walker-evals/s"
 WORKLOAD = "CO 14e- 58 GTO 14 MO 100 det, 262144 walkers"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)
-# DRAM bytes (read + write) per walker of the mixed-form k_det launch, from the ncu capture in
-# profiles/k_det_co_mixed.md (242.8 MB for 131,072 walkers); None once that kernel changes.
+# DRAM bytes (read + write) per walker of the mixed-form k_det launch, from an ncu capture of that
+# kernel on 131,072 CO walkers (242.8 MB); set to None whenever the kernel changes.
 DET_TRAFFIC_BYTES_PER_WALKER = 242.824192e6 / 131072
 
 
@@ -170,6 +170,102 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(n_requests: int, with_fp64: bool, device: int):
+    """Serving mix (H2, LiH, Li2, CO at 20 bond lengths each; 50 Metropolis
+    steps + E_L mean/variance per request; walkers uniform on 4k..256k):
+    a closed-loop run measures the capacity (requests/s with everything
+    queued at once), then Poisson arrivals at 80% of it give the latencies."""
+    from paper_2506_09743_gb300 import serving
+
+    out = {"n_steps": 50, "walker_choices": [4096, 16384, 65536, 262144], "molecules": ["h2", "lih", "li2", "co"],
+           "note": "Li2 (backflow) requests run in the FP64 form in both mixes"}
+    forms = ["mixed_tf32"] + (["fp64"] if with_fp64 else [])
+    for form in forms:
+        wfs = serving.build_mix(form, device=device)
+        srv = serving.Server(device=device, hbm_budget_bytes=48 << 30, max_in_flight=8)
+        ids = {k: srv.add(wf) for k, wf in wfs.items()}
+        cap_reqs = qi.serving_requests(n_requests, rate_hz=0.0, seed=101)
+        cap = serving.summarize(serving.run_stream(srv, ids, cap_reqs, n_steps=50, step=0.05), 50)
+        rate = 0.8 * cap["requests_per_s"]
+        reqs = qi.serving_requests(n_requests, rate_hz=rate, seed=102)
+        st = serving.summarize(serving.run_stream(srv, ids, reqs, n_steps=50, step=0.05, rate_hz=rate), 50)
+        st["capacity_requests_per_s"] = cap["requests_per_s"]
+        st["arrival_rate_hz"] = rate
+        out["mixed" if form == "mixed_tf32" else "fp64"] = st
+        srv.close()
+        for wf in wfs.values():
+            wf.close()
+    return out
+
+
+def run_secondary(device, stream, barrier, flush):
+    """The other workloads: E_L throughput of H2 (1,024 walkers), LiH
+    (65,536) and Li2 with backflow (131,072), and the Li2 energy gradient +
+    forces (Eq. nabla_loss, Eq. force) on 131,072 walkers."""
+    import torch
+
+    from paper_2506_09743_gb300 import Wavefunction
+
+    out = {}
+
+    def rate(wf, x, W, steps=5):
+        e = torch.empty(W, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            wf.local_energy(x, e_loc=e, want_log_psi=False)
+        barrier()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            wf.local_energy(x, e_loc=e, want_log_psi=False)
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return W * steps / (tot / 1e3)
+
+    for name in ("h2", "lih", "li2"):
+        mol = qi.make_molecule(name)
+        W = qi.WORKLOAD_WALKERS[name]
+        x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
+        forms = ("fp64",) if mol.backflow_w != 0.0 else ("fp64", "mixed_tf32")
+        for form in forms:
+            wf = Wavefunction(mol, precision=form, device=device)
+            out[f"{name}_{form}_walker_evals_per_s"] = rate(wf, x, W)
+            if name == "li2":
+                wf.energy_grad(x)
+                barrier()
+                t0 = time.perf_counter()
+                wf.energy_grad(x)
+                out["li2_energy_grad_ms"] = 1e3 * (time.perf_counter() - t0)
+                out["li2_energy_grad_note"] = ("131,072 walkers: E_L, mean/variance, gradient of 83 parameters "
+                                               "and forces on both nuclei, host-timed (synchronous call)")
+            wf.close()
+    return out
+
+
+def reduce_max(v: float, dist=None) -> float:
+    """Maximum of a per-rank value over the process group (identity alone)."""
+    if dist is None or not dist.is_initialized():
+        return v
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, steps: int, max_total_ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return world * units_per_rank * steps / (max_total_ms / 1e3)
+
+
+def rank_walker_seed(rank: int) -> int:
+    """Each rank draws its own walkers (weak scaling: a fixed batch per GPU)."""
+    return qi.SEED_WALKERS + rank
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,6 +274,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--walkers", type=int, default=qi.WORKLOAD_WALKERS["co"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=160,
+                    help="requests of the Poisson serving run (0 = skip the serving measurement)")
+    ap.add_argument("--no-serving-fp64", action="store_true", help="serve the mix in the mixed form only")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -208,15 +307,11 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist)
 
     mol = qi.make_co()
     W = args.walkers
-    r = qi.walkers(mol, W, seed=qi.SEED_WALKERS + rank)
+    r = qi.walkers(mol, W, seed=rank_walker_seed(rank))
     soa = np.ascontiguousarray(qi.to_soa(r))
     x = torch.tensor(soa, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
@@ -253,8 +348,8 @@ def main():
     tot_mixed = max_over_ranks(tot_mixed)
     tot_fp64 = max_over_ranks(tot_fp64)
     ms_step = tot_mixed / args.steps
-    value = world * W * args.steps / (tot_mixed / 1e3)
-    value_fp64 = world * W * k64 / (tot_fp64 / 1e3)
+    value = whole_job_rate(world, W, args.steps, tot_mixed)
+    value_fp64 = whole_job_rate(world, W, k64, tot_fp64)
 
     # end to end through the host-buffer C call (pinned host memory)
     pin_in = torch.from_numpy(soa).pin_memory()
@@ -278,7 +373,26 @@ def main():
     clk.__exit__(None, None, None)
     clocks = clk.summary()
     e2e_ms = max_over_ranks(float(np.sum(t_e2e)))
-    e2e_value = world * W * e2e_steps / (e2e_ms / 1e3)
+    e2e_value = whole_job_rate(world, W, e2e_steps, e2e_ms)
+
+    # Metropolis walker steps (value path: Jastrow value, orbital values, determinants, accept)
+    n_mh = 5
+    xs = x.clone()
+    wf_mixed.sample(xs, n_steps=1, step=0.05, seed=0x5EED)
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    wf_mixed.sample(xs, n_steps=n_mh, step=0.05, seed=0x5EED, step_offset=1)
+    b.record(stream)
+    b.synchronize()
+    mh_steps_per_s = world * W * n_mh / (max_over_ranks(a.elapsed_time(b)) / 1e3)
+    del xs
+
+    secondary = run_secondary(local, stream, barrier, flush) if world == 1 else None
+
+    serving_out = None
+    if args.serving_requests > 0 and world == 1:
+        serving_out = run_serving(args.serving_requests, not args.no_serving_fp64, local)
 
     flops_det = det_stage_flops(mol) * W
     det_ms = float(stage_mixed[2])
@@ -309,7 +423,10 @@ def main():
                 "d2h_bytes_per_step": int(2 * 8 * W), "api": "qmc_local_energy_host (pinned host buffers)"},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
-        "p99_request_latency_ms": None,
+        "p99_request_latency_ms": None if serving_out is None else serving_out["mixed"]["p99_ms"],
+        "metropolis_walker_steps_per_s": mh_steps_per_s,
+        "serving": serving_out,
+        "secondary": secondary,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
