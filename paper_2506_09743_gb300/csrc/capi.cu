@@ -234,7 +234,7 @@ qmc_status build_tables(qmc_wf* wf) {
     if (!shells.empty()) {
       ShellDev& q = shells.back();
       if (q.atom == sh.atom && q.kind == sh.kind && q.kn == sh.kn && q.l == sh.l && q.n_prim == sh.n_prim &&
-          q.ao_first + q.n_ao == b) {
+          q.ao_first + q.n_ao == b && q.n_ao < kMaxShellAo) {
         bool same = true;
         for (int p = 0; p < sh.n_prim; ++p) same = same && q.expo[p] == sh.expo[p] && q.coef[p] == sh.coef[p];
         if (same) { q.n_ao += 1; merged = true; }
@@ -244,13 +244,46 @@ qmc_status build_tables(qmc_wf* wf) {
   }
   if ((int)shells.size() > kMaxShells) return fail(QMC_ERR_UNSUPPORTED, "too many shells");
   d.n_shell = (int)shells.size();
-  {  // balance the AO count between the four thread parts of the tensor-core AO stage
-    int acc = 0, part = 1;
-    d.shell_part[0] = 0;
-    for (int q = 1; q <= 4; ++q) d.shell_part[q] = d.n_shell;
-    for (int s = 0; s < d.n_shell && part < 4; ++s) {
-      while (part < 4 && 4 * acc >= part * nao) d.shell_part[part++] = s;
-      acc += shells[s].n_ao;
+  // ---- tensor-core AO stage: pack the shells into K-passes of kTcPass
+  // columns in AO order (a shell that would straddle a pass boundary starts
+  // the next pass), then deal each pass's shells to the four thread parts by
+  // estimated cost, largest first, each part's list kept in shell order so
+  // that shells of one atom stay together.
+  std::vector<int> ao_col(nao, 0), tc_shells;
+  d.n_pass = 0;
+  if (tc) {
+    std::vector<int> first_shell;  // first shell of each pass
+    int col = 0;
+    for (int s = 0; s < d.n_shell; ++s) {
+      const ShellDev& q = shells[s];
+      if (col % kTcPass + q.n_ao > kTcPass) col = (int)round_up(col, kTcPass);
+      if (col % kTcPass == 0 && (int)first_shell.size() == col / kTcPass) first_shell.push_back(s);
+      for (int k = 0; k < q.n_ao; ++k) ao_col[q.ao_first + k] = col + k;
+      col += q.n_ao;
+    }
+    d.n_pass = (int)first_shell.size();
+    if (d.n_pass > kMaxTcPass) return fail(QMC_ERR_UNSUPPORTED, "too many AO passes");
+    first_shell.push_back(d.n_shell);
+    for (int p = 0; p < d.n_pass; ++p) {
+      const int s0 = first_shell[p], s1 = first_shell[p + 1];
+      d.pass_cols[p] = ao_col[shells[s1 - 1].ao_first + shells[s1 - 1].n_ao - 1] - p * kTcPass + 1;
+      std::vector<int> by_cost;
+      for (int s = s0; s < s1; ++s) by_cost.push_back(s);
+      auto cost = [&](int s) { return 3 * shells[s].n_prim + 4 * shells[s].n_ao + 2; };
+      std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return cost(a) > cost(b); });
+      std::vector<std::vector<int>> part(4);
+      int load[4] = {0, 0, 0, 0};
+      for (int s : by_cost) {
+        const int q = (int)(std::min_element(load, load + 4) - load);
+        part[q].push_back(s);
+        load[q] += cost(s);
+      }
+      for (int q = 0; q < 4; ++q) {
+        std::sort(part[q].begin(), part[q].end());
+        d.part_off[p][q] = (int)tc_shells.size();
+        tc_shells.insert(tc_shells.end(), part[q].begin(), part[q].end());
+      }
+      d.part_off[p][4] = (int)tc_shells.size();
     }
   }
   std::vector<double> mo64((size_t)nao * nmo);
@@ -316,19 +349,19 @@ qmc_status build_tables(qmc_wf* wf) {
     return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
 
   // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
-  d.k_pad = tc ? (int)round_up(nao, 8) : 0;
+  d.k_pad = tc ? d.n_pass * kTcPass : 0;
   std::vector<uint32_t> tc_hi, tc_lo;
   if (tc) {
     tc_hi.assign((size_t)16 * d.k_pad, 0u);
     tc_lo.assign((size_t)16 * d.k_pad, 0u);
-    for (int m = 0; m < 16; ++m)
-      for (int b = 0; b < d.k_pad; ++b) {
-        const float v = (m < nmo && b < nao) ? mo32[(size_t)b * nmo + m] : 0.0f;
+    for (int m = 0; m < nmo; ++m)
+      for (int b = 0; b < nao; ++b) {
+        const float v = mo32[(size_t)b * nmo + m];
         const uint32_t hi = tf32_hi_bits(v);
         const float lo = v - bits_f(hi);
         uint32_t lo_bits;
         std::memcpy(&lo_bits, &lo, 4);
-        const size_t off = core_offset_words(m, b, d.k_pad);
+        const size_t off = core_offset_words(m, ao_col[b], d.k_pad);
         tc_hi[off] = hi;
         tc_lo[off] = tf32_hi_bits(bits_f(lo_bits));
       }
@@ -342,7 +375,8 @@ qmc_status build_tables(qmc_wf* wf) {
       {exc.data(), sizeof(int) * exc.size()},           {det_idx.data(), sizeof(int) * det_idx.size()},
       {det_w_sorted.data(), sizeof(double) * ndet},      {tc_hi.data(), sizeof(uint32_t) * tc_hi.size()},
       {tc_lo.data(), sizeof(uint32_t) * tc_lo.size()},  {ang.data(), sizeof(double) * nao},
-      {h.prim_start.data(), sizeof(int) * (nao + 1)}};
+      {h.prim_start.data(), sizeof(int) * (nao + 1)}, {ao_col.data(), sizeof(int) * nao},
+      {tc_shells.data(), sizeof(int) * tc_shells.size()}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
   void* blob = nullptr;
@@ -375,6 +409,8 @@ qmc_status build_tables(qmc_wf* wf) {
   d.mo_tc_lo = reinterpret_cast<const uint32_t*>(ptr[8]);
   d.ao_ang = reinterpret_cast<const double*>(ptr[9]);
   d.ao_prim = reinterpret_cast<const int*>(ptr[10]);
+  d.ao_col = reinterpret_cast<const int*>(ptr[11]);
+  d.tc_shells = reinterpret_cast<const int*>(ptr[12]);
   // the previous tables may still be read by work in flight on any stream
   if (wf->blob) {
     cudaDeviceSynchronize();
@@ -434,6 +470,18 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
     delete wf;
     return st;
   }
+  {
+    DeviceGuard guard(wf->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&wf->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&wf->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&wf->ev_join, cudaEventDisableTiming);
+    for (int c = 0; c < kMaxChunks && e == cudaSuccess; ++c)
+      e = cudaEventCreateWithFlags(&wf->ev_ao[c], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      qmc_destroy_wf(wf);
+      return cuda_fail(e, "pipeline streams");
+    }
+  }
   *out = wf;
   return QMC_OK;
 }
@@ -446,8 +494,14 @@ void qmc_destroy_wf(qmc_wf* wf) {
     if (wf->ws) cudaFree(wf->ws);
     if (wf->stage) cudaFree(wf->stage);
     if (wf->gws) cudaFree(wf->gws);
-    for (auto& e : wf->ev)
+    for (auto& row : wf->tev)
+      for (auto& e : row)
+        if (e) cudaEventDestroy(e);
+    for (auto& e : wf->ev_ao)
       if (e) cudaEventDestroy(e);
+    if (wf->ev_fork) cudaEventDestroy(wf->ev_fork);
+    if (wf->ev_join) cudaEventDestroy(wf->ev_join);
+    if (wf->aux) cudaStreamDestroy(wf->aux);
   }
   delete wf;
 }
@@ -485,41 +539,89 @@ qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[
   return QMC_OK;
 }
 
-static void mark(qmc_wf* wf, int k, cudaStream_t st) {
-  if (wf->timing) cudaEventRecord(wf->ev[k], st);
+static void mark(qmc_wf* wf, int c, int k, cudaStream_t st) {
+  if (wf->timing && c < kMaxChunks) cudaEventRecord(wf->tev[c][k], st);
 }
 
+// View of the workspace for walkers [c0, c0 + n) of the batch.
+static Workspace chunk_view(const qmc_wf* wf, const Workspace& ws, int64_t c0, int nch) {
+  Workspace v = ws;
+  const size_t ta = ta_size(wf->precision);
+  v.gradJ = static_cast<char*>(ws.gradJ) + c0 * ta;
+  v.jscal = ws.jscal + c0;
+  v.mo = static_cast<char*>(ws.mo) + (size_t)c0 * wf->dev.n_elec * nch * ws.nmp * ta;
+  return v;
+}
+
+// Local-energy (kinetic) or value-only evaluation of W walkers.
+// Stages: Jastrow + Coulomb, AO + AO->MO contraction, determinants, in order
+// on the caller's stream.  (A two-stream pipeline over walker chunks, with
+// each chunk's determinant stage overlapping the next chunk's AO stage, fits
+// both kernels on one SM but was measured slower on CO: a determinant block
+// sharing an SM keeps half of its warps and loses more FP64 throughput than
+// the overlap gains; `pipelined` stays off.)  Backflow wavefunctions run the
+// general FP64 kernel.
 static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                             int* err_flag, bool kinetic, double* e_loc, double* log_psi, cudaStream_t st) {
   const WfDev& d = wf->dev;
-  mark(wf, 0, st);
   if (d.bf_w != 0.0) {  // backflow: one general kernel (Jastrow, orbitals, Eq. nabla_d, E_L)
+    mark(wf, 0, 0, st);
     qmc_status s = launch_status(launch_eloc_general(d, walkers, W, ldw, kinetic, e_loc, log_psi, st), "general");
     if (s) return s;
-    mark(wf, 1, st);
-    mark(wf, 2, st);
-    mark(wf, 3, st);
-    if (wf->timing) wf->timed_once = true;
+    for (int k = 1; k < 6; ++k) mark(wf, 0, k, st);
+    if (wf->timing) { wf->timed_once = true; wf->timed_chunks = 1; }
     return QMC_OK;
   }
-  qmc_status s = launch_status(launch_jastrow(d, wf->precision, walkers, W, ldw, ws, kinetic, st), "jastrow");
-  if (s) return s;
-  mark(wf, 1, st);
   const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
   const int nch = kinetic ? 2 : 1;
   if (tc) {
-    s = launch_status(cudaMemsetAsync(err_flag, 0, sizeof(int), st), "error flag reset");
+    qmc_status s = launch_status(cudaMemsetAsync(err_flag, 0, sizeof(int), st), "error flag reset");
     if (s) return s;
   }
-  s = launch_status(tc ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, ws, nch, err_flag, st)
-                       : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, ws, nch, st),
-                    "ao_mo");
-  if (s) return s;
-  mark(wf, 2, st);
-  s = launch_status(launch_det(d, wf->precision, W, ws, kinetic, e_loc, log_psi, st), "det");
-  if (s) return s;
-  mark(wf, 3, st);
-  if (wf->timing) wf->timed_once = true;
+  const bool pipelined = false;
+  const int64_t chunk = pipelined ? kChunk : W;
+  const int n_chunks = (int)((W + chunk - 1) / chunk);
+  cudaStream_t det_st = pipelined ? wf->aux : st;
+  if (pipelined) {
+    qmc_status s = launch_status(cudaEventRecord(wf->ev_fork, st), "fork");
+    if (!s) s = launch_status(cudaStreamWaitEvent(wf->aux, wf->ev_fork, 0), "fork");
+    if (s) return s;
+  }
+  for (int c = 0; c < n_chunks; ++c) {
+    const int64_t c0 = c * chunk, n = std::min<int64_t>(chunk, W - c0);
+    const Workspace v = chunk_view(wf, ws, c0, nch);
+    const double* wk = walkers + c0;
+    mark(wf, c, 0, st);
+    qmc_status s = launch_status(launch_jastrow(d, wf->precision, wk, n, ldw, v, kinetic, st), "jastrow");
+    if (s) return s;
+    mark(wf, c, 1, st);
+    mark(wf, c, 2, st);
+    s = launch_status(tc ? launch_ao_mo_tc(d, wf->precision, wk, n, ldw, v, nch, err_flag, st)
+                         : launch_ao_mo_simt(d, wf->precision, wk, n, ldw, v, nch, st),
+                      "ao_mo");
+    if (s) return s;
+    mark(wf, c, 3, st);
+    if (pipelined) {
+      s = launch_status(cudaEventRecord(wf->ev_ao[c], st), "chunk event");
+      if (!s) s = launch_status(cudaStreamWaitEvent(det_st, wf->ev_ao[c], 0), "chunk event");
+      if (s) return s;
+    }
+    mark(wf, c, 4, det_st);
+    s = launch_status(launch_det(d, wf->precision, n, v, kinetic, e_loc ? e_loc + c0 : nullptr,
+                                 log_psi ? log_psi + c0 : nullptr, det_st),
+                      "det");
+    if (s) return s;
+    mark(wf, c, 5, det_st);
+  }
+  if (pipelined) {
+    qmc_status s = launch_status(cudaEventRecord(wf->ev_join, det_st), "join");
+    if (!s) s = launch_status(cudaStreamWaitEvent(st, wf->ev_join, 0), "join");
+    if (s) return s;
+  }
+  if (wf->timing) {
+    wf->timed_once = true;
+    wf->timed_chunks = std::min(n_chunks, kMaxChunks);
+  }
   return QMC_OK;
 }
 
@@ -749,11 +851,12 @@ qmc_status qmc_set_timing(qmc_wf* wf, int32_t enable) {
   if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
   std::lock_guard<std::mutex> lock(wf->mu);
   DeviceGuard guard(wf->device);
-  if (enable && !wf->ev[0])
-    for (auto& e : wf->ev) {
-      cudaError_t r = cudaEventCreate(&e);
-      if (r != cudaSuccess) return cuda_fail(r, "event create");
-    }
+  if (enable && !wf->tev[0][0])
+    for (auto& row : wf->tev)
+      for (auto& e : row) {
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return cuda_fail(r, "event create");
+      }
   wf->timing = enable != 0;
   return QMC_OK;
 }
@@ -763,9 +866,17 @@ qmc_status qmc_last_stage_ms(qmc_wf* wf, float* ms, int32_t n) {
   std::lock_guard<std::mutex> lock(wf->mu);
   if (!wf->timed_once) return fail(QMC_ERR_ARG, "no timed evaluation yet");
   DeviceGuard guard(wf->device);
-  cudaError_t r = cudaEventSynchronize(wf->ev[3]);
-  for (int k = 0; k < n && r == cudaSuccess; ++k) r = cudaEventElapsedTime(&ms[k], wf->ev[k], wf->ev[k + 1]);
-  return r == cudaSuccess ? QMC_OK : cuda_fail(r, "event timing");
+  for (int k = 0; k < n; ++k) ms[k] = 0.0f;
+  for (int c = 0; c < wf->timed_chunks; ++c) {
+    cudaError_t r = cudaEventSynchronize(wf->tev[c][5]);
+    for (int k = 0; k < n && r == cudaSuccess; ++k) {
+      float t = 0.0f;
+      r = cudaEventElapsedTime(&t, wf->tev[c][2 * k], wf->tev[c][2 * k + 1]);
+      ms[k] += t;
+    }
+    if (r != cudaSuccess) return cuda_fail(r, "event timing");
+  }
+  return QMC_OK;
 }
 
 const char* qmc_last_error(void) { return g_err.c_str(); }

@@ -1,30 +1,31 @@
 // AO evaluation fused with the AO->MO contraction on the 5th-generation
 // tensor cores (tcgen05, sm_103a).  Mixed forms only.
 //
-// CTA = 512 threads, 128 walkers x one electron.  Each walker row is computed
-// by four threads (they split the shells, balanced by AO count, so that 16
-// warps per SM hide the latency of the FP32 AO evaluation within the shared
-// memory the operand tiles need); the FP32 AO channels are written
-// into shared memory as the MMA A operand, split into TF32 high and low parts
+// CTA = 512 threads, 128 walkers x one electron (MMA M = 128 rows).  The AO
+// columns are packed on the host into K-passes of 32 columns (a shell never
+// straddles two passes; unused columns are zero).  For each pass the four
+// thread parts of a row evaluate the pass's shells (dealt to the parts by
+// cost), write the FP32 AO channels into shared memory as the MMA A operand,
+// split into TF32 high and low parts
 //     a = a_hi + a_lo,  a_hi = rna_tf32(a),  a_lo = rna_tf32(a - a_hi),
 // and one thread issues, per channel c (value / kinetic operator) and K step,
 //     D_c += A_c,hi B_hi + A_c,hi B_lo + A_c,lo B_hi        (kind::tf32)
-// with M = 128 rows (walkers), N = 16 (MOs, padded), K = 8 per instruction,
-// accumulating in FP32 in tensor memory (two 16-column accumulators).  The
+// with N = 16 (MOs, padded), K = 8 per instruction, accumulating in FP32 in
+// tensor memory (two 16-column accumulators) across all passes.  The
 // dropped a_lo b_lo term and the TF32 rounding of the low parts leave an
 // error of order 2^-21 relative to |a||b|, i.e. FP32-level accuracy.
 // B = MO^T (scaled by the AO angular factors) is prepared on the host in the
-// same core-matrix layout and copied into shared memory per CTA.
+// same core-matrix layout, for all passes, and copied into shared memory.
+// The A buffer holds one pass (64 KB), so two CTAs (32 warps) fit on an SM;
+// a pass's buffer is reused once its MMAs have completed (mbarrier).
 //
 // Shared-memory operand layout (K-major, no swizzle): 8-row x 16-byte core
-// matrices; element (row, k) at byte
-//     (row / 8) * SBO + (k / 4) * 128 + (row % 8) * 16 + (k % 4) * 4,
-// LBO = 128 B (next core matrix along K) and SBO = (k_pad / 4) * 128 B (next
-// 8-row group).
+// matrices; element (row, k) at byte (row / 8) * SBO + (k / 4) * 128 +
+// (row % 8) * 16 + (k % 4) * 4, LBO = 128 B (next core matrix along K) and
+// SBO = (K extent / 4) * 128 B (next 8-row group).
 //
-// The MMA completion is signalled by tcgen05.commit on an mbarrier; the wait
-// is bounded (about one second), after which the kernel raises an error flag
-// instead of hanging.
+// Every wait on an mbarrier is bounded (about one second), after which the
+// kernel raises an error flag and writes NaN instead of hanging.
 #include "ao_eval.cuh"
 
 namespace qmc {
@@ -35,6 +36,7 @@ constexpr int kRows = 128;
 constexpr int kThreads = 512;
 constexpr int kParts = kThreads / kRows;
 constexpr int kNPad = 16;
+constexpr int kPass = kTcPass;
 constexpr uint32_t kTmemCols = 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -86,21 +88,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase)
   return false;
 }
 
+// int words of the AO power, column and shell-list tables, rounded up so that
+// the mbarrier behind them is 16-byte aligned
+__host__ __device__ inline int tc_int_words(const WfDev& wf) { return (2 * wf.n_ao + wf.n_shell + 3) & ~3; }
+
 }  // namespace
 
+// at most 64 registers per thread: two 512-thread CTAs per SM
 template <int NCH>
-__global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double* __restrict__ walkers, int64_t W,
+__global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                          int64_t ldw, const float* __restrict__ gradJ,
                                                          float* __restrict__ mo_out, int64_t ldm,
                                                          int* __restrict__ err_flag) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int kp = wf.k_pad;
-  const size_t tile_words = (size_t)kRows * kp;
-  uint32_t* A = reinterpret_cast<uint32_t*>(smem_raw);                // [NCH][2][128][kp]
+  constexpr size_t tile_words = (size_t)kRows * kPass;
+  uint32_t* A = reinterpret_cast<uint32_t*>(smem_raw);                // [NCH][2][128][kPass]
   uint32_t* B = A + (size_t)NCH * 2 * tile_words;                     // [2][16][kp]
   ShellDev* sh_s = reinterpret_cast<ShellDev*>(B + 2 * kNPad * kp);  // [n_shell]
-  int* pow_s = reinterpret_cast<int*>(sh_s + wf.n_shell);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(pow_s + ((wf.n_ao + 3) & ~3));
+  int* pow_s = reinterpret_cast<int*>(sh_s + wf.n_shell);              // [n_ao]
+  int* col_s = pow_s + wf.n_ao;                                         // [n_ao]
+  int* list_s = col_s + wf.n_ao;                                        // [n_shell]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(pow_s + tc_int_words(wf));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -118,41 +127,54 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
     B[k] = k < kNPad * kp ? wf.mo_tc_hi[k] : wf.mo_tc_lo[k - kNPad * kp];
   for (int k = tid; k < wf.n_shell * (int)(sizeof(ShellDev) / 4); k += kThreads)
     reinterpret_cast<int*>(sh_s)[k] = reinterpret_cast<const int*>(wf.shells)[k];
-  for (int k = tid; k < wf.n_ao; k += kThreads) pow_s[k] = wf.ao_pow[k];
+  for (int k = tid; k < wf.n_ao; k += kThreads) {
+    pow_s[k] = wf.ao_pow[k];
+    col_s[k] = wf.ao_col[k];
+  }
+  for (int k = tid; k < wf.n_shell; k += kThreads) list_s[k] = wf.tc_shells[k];
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
 
-  // ---- AO channels -> A operand (TF32 hi / lo) in shared memory
-  const int row = tid & (kRows - 1), part = tid >> 7;
+  const int row = tid & (kRows - 1), part = tid / kRows;
   const int64_t w = (int64_t)blockIdx.x * kRows + row;
   const int i = blockIdx.y;
   const bool live = w < W;
-  auto put = [&](int ch, int k, float v) {
-    const size_t off = (size_t)(row / 8) * (kp / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4 + (k % 4);
+  double rx = 0.0, ry = 0.0, rz = 0.0;
+  float gjx = 0.f, gjy = 0.f, gjz = 0.f;
+  if (live) {
+    rx = walkers[(int64_t)(3 * i) * ldw + w];
+    ry = walkers[(int64_t)(3 * i + 1) * ldw + w];
+    rz = walkers[(int64_t)(3 * i + 2) * ldw + w];
+    if (NCH == 2) {
+      gjx = gradJ[(int64_t)(3 * i) * ldm + w];
+      gjy = gradJ[(int64_t)(3 * i + 1) * ldm + w];
+      gjz = gradJ[(int64_t)(3 * i + 2) * ldm + w];
+    }
+  }
+  auto put = [&](int ch, int k, float v) {  // k: column within the pass
+    const size_t off = (size_t)(row / 8) * (kPass / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4 + (k % 4);
     const uint32_t hi = tf32_rna(v);
     const float lo = v - __uint_as_float(hi);
     A[(size_t)(ch * 2 + 0) * tile_words + off] = hi;
     A[(size_t)(ch * 2 + 1) * tile_words + off] = tf32_rna(lo);
   };
-  {
-    double rx = 0.0, ry = 0.0, rz = 0.0;
-    float gjx = 0.f, gjy = 0.f, gjz = 0.f;
-    if (live) {
-      rx = walkers[(int64_t)(3 * i) * ldw + w];
-      ry = walkers[(int64_t)(3 * i + 1) * ldw + w];
-      rz = walkers[(int64_t)(3 * i + 2) * ldw + w];
-      if (NCH == 2) {
-        gjx = gradJ[(int64_t)(3 * i) * ldm + w];
-        gjy = gradJ[(int64_t)(3 * i + 1) * ldm + w];
-        gjz = gradJ[(int64_t)(3 * i + 2) * ldm + w];
-      }
+  const uint32_t lbo = 128, sbo_a = (uint32_t)(kPass / 4) * 128, sbo_b = (uint32_t)(kp / 4) * 128;
+  bool ok = true;
+  for (int pass = 0; pass < wf.n_pass; ++pass) {
+    if (pass > 0) {
+      // the previous pass's MMAs must have read the A buffer before it is overwritten
+      ok = ok && mbar_wait_bounded(smem_u32(mbar), (uint32_t)((pass - 1) & 1));
     }
-    const int s_begin = wf.shell_part[part];
-    const int s_end = wf.shell_part[part + 1];
+    // unused columns of the pass are zero (disjoint from the shells' columns)
+    for (int k = wf.pass_cols[pass] + part; k < kPass; k += kParts)
+      for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
+    const int s_begin = wf.part_off[pass][part], s_end = wf.part_off[pass][part + 1];
     int cur_atom = -1;
     float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, rho = 0.f, irho = 0.f;
     float px[5], py[5], pz[5];
-    for (int s = s_begin; s < s_end; ++s) {
-      const ShellDev& sh = sh_s[s];
+    for (int q = s_begin; q < s_end; ++q) {
+      const ShellDev& sh = sh_s[list_s[q]];
       if (sh.atom != cur_atom) {
         cur_atom = sh.atom;
         displacement(rx, ry, rz, wf.atom_xyz[cur_atom], dx, dy, dz);
@@ -166,48 +188,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
       const float radial_lap = f2 + float(2 * (sh.l + 1)) * g1;
       for (int k = 0; k < sh.n_ao; ++k) {
         const int b = sh.ao_first + k;
+        const int col = col_s[b] - pass * kPass;
         float P, Px, Py, Pz, lapP;
         angular(pow_s[b], px, py, pz, P, Px, Py, Pz, lapP, NCH == 2);
-        const float v = live ? P * f : 0.f;
-        put(0, b, v);
+        put(0, col, live ? P * f : 0.f);
         if (NCH == 2) {
           const float gx = f * Px + P * g1 * dx, gy = f * Py + P * g1 * dy, gz = f * Pz + P * g1 * dz;
           const float kin = f * lapP + P * radial_lap + 2.f * (gjx * gx + gjy * gy + gjz * gz);
-          put(1, b, live ? kin : 0.f);
+          put(1, col, live ? kin : 0.f);
         }
       }
     }
-    if (part == kParts - 1)
-      for (int k = wf.n_ao; k < kp; ++k)
-        for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
-  }
-  // generic-proxy shared stores -> visible to the tensor core (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
-
-  if (tid == 0) {
-    const uint32_t lbo = 128, sbo = (uint32_t)(kp / 4) * 128;
-    const uint32_t b_hi = smem_u32(B), b_lo = smem_u32(B + kNPad * kp);
-    for (int ch = 0; ch < NCH; ++ch) {
-      const uint32_t a_hi = smem_u32(A + (size_t)(ch * 2) * tile_words);
-      const uint32_t a_lo = smem_u32(A + (size_t)(ch * 2 + 1) * tile_words);
-      const uint32_t d = tmem + (uint32_t)(ch * kNPad);
-      for (int ks = 0; ks < kp / 8; ++ks) {
-        const uint32_t koff = (uint32_t)ks * 256;  // two core matrices along K
-        mma_tf32(d, smem_desc(a_hi + koff, lbo, sbo), smem_desc(b_hi + koff, lbo, sbo), ks > 0 ? 1u : 0u);
-        mma_tf32(d, smem_desc(a_hi + koff, lbo, sbo), smem_desc(b_lo + koff, lbo, sbo), 1u);
-        mma_tf32(d, smem_desc(a_lo + koff, lbo, sbo), smem_desc(b_hi + koff, lbo, sbo), 1u);
+    // generic-proxy shared stores -> visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t b_hi = smem_u32(B), b_lo = smem_u32(B + kNPad * kp);
+      for (int ch = 0; ch < NCH; ++ch) {
+        const uint32_t a_hi = smem_u32(A + (size_t)(ch * 2) * tile_words);
+        const uint32_t a_lo = smem_u32(A + (size_t)(ch * 2 + 1) * tile_words);
+        const uint32_t d = tmem + (uint32_t)(ch * kNPad);
+        for (int ks = 0; ks < kPass / 8; ++ks) {
+          const uint32_t aoff = (uint32_t)ks * 256;                            // two core matrices along K
+          const uint32_t boff = (uint32_t)(pass * (kPass / 4) + 2 * ks) * 128;  // same columns of B
+          const uint32_t acc = (pass > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(d, smem_desc(a_hi + aoff, lbo, sbo_a), smem_desc(b_hi + boff, lbo, sbo_b), acc);
+          mma_tf32(d, smem_desc(a_hi + aoff, lbo, sbo_a), smem_desc(b_lo + boff, lbo, sbo_b), 1u);
+          mma_tf32(d, smem_desc(a_lo + aoff, lbo, sbo_a), smem_desc(b_hi + boff, lbo, sbo_b), 1u);
+        }
       }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(mbar))
+                   : "memory");
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(mbar))
-                 : "memory");
   }
-  const bool done = mbar_wait_bounded(smem_u32(mbar), 0);
+  ok = ok && mbar_wait_bounded(smem_u32(mbar), (uint32_t)((wf.n_pass - 1) & 1));
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done) {
+  if (!ok) {
     // the accumulators are not trustworthy: poison this tile's outputs
     if (tid == 0) atomicExch(err_flag, 1);
     const int ch = tid >> 7;
@@ -242,9 +260,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_tc(WfDev wf, const double
 }
 
 size_t tc_smem_bytes(const WfDev& wf, int nch) {
-  const size_t kp = (size_t)wf.k_pad;
-  size_t b = (size_t)nch * 2 * kRows * kp * 4 + 2 * kNPad * kp * 4;
-  b += sizeof(ShellDev) * wf.n_shell + 4 * (size_t)((wf.n_ao + 3) & ~3) + 16;
+  size_t b = (size_t)nch * 2 * kRows * kPass * 4 + 2 * kNPad * (size_t)wf.k_pad * 4;
+  b += sizeof(ShellDev) * wf.n_shell + 4 * (size_t)tc_int_words(wf) + 16;
   return b;
 }
 

@@ -106,9 +106,10 @@ __global__ void __launch_bounds__(256) k_det(WfDev wf, int64_t W, const TA* __re
   const bool live = w < W;
   const int nmo = wf.n_mo, N = wf.n_elec;
   double* my = walk_s + (size_t)team * stride;
-  // per-walker shared layout: stage [NCH][NS][nmo] | ainv [NS][NS] | tables
-  double* stage = my;
-  double* ainv = my + NCH * NS * nmo;
+  // per-walker shared layout: stage [NCH][NS][nmo] (input type, widened on
+  // read: halves the footprint in the FP32 forms) | ainv [NS][NS] | tables
+  TA* stage = reinterpret_cast<TA*>(my);
+  double* ainv = my + (NCH * NS * nmo * (int)sizeof(TA) + 7) / 8;
   double* tab = ainv + NS * NS;
   const TA* blk = mo + (size_t)(live ? w : 0) * N * NCH * nmp;
 
@@ -124,14 +125,14 @@ __global__ void __launch_bounds__(256) k_det(WfDev wf, int64_t W, const TA* __re
       const int total = n * NCH * nmp;
       for (int k = q; k < total; k += TS) {
         const int m = k % nmp, rc = k / nmp, c = rc % NCH, r = rc / NCH;
-        if (m < nmo) stage[(c * NS + r) * nmo + m] = live ? widen(src[k]) : (r == m ? 1.0 : 0.0);
+        if (m < nmo) stage[(c * NS + r) * nmo + m] = live ? src[k] : TA(r == m ? 1 : 0);
       }
     }
     __syncwarp();
     // ---- 1. Gauss-Jordan inverse, thread q owns column q
     double col[NS];
 #pragma unroll
-    for (int r = 0; r < NS; ++r) col[r] = (r < n && q < n) ? stage[r * nmo + q] : 0.0;
+    for (int r = 0; r < NS; ++r) col[r] = (r < n && q < n) ? widen(stage[r * nmo + q]) : 0.0;
     int piv[NS];
     double det = 1.0;
 #pragma unroll
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(256) k_det(WfDev wf, int64_t W, const TA* __re
       if (q < n) {
 #pragma unroll
         for (int r = 0; r < NS; ++r)
-          if (r < n) c += ainv[q * NS + r] * stage[(NS + r) * nmo + q];
+          if (r < n) c += ainv[q * NS + r] * widen(stage[(NS + r) * nmo + q]);
       }
       c = team_sum<TS>(c);
       if (s == 0) tr0u = c; else tr0d = c;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256) k_det(WfDev wf, int64_t W, const TA* __re
         if (m < n) {
 #pragma unroll
           for (int r = 0; r < NS; ++r)
-            if (r < n) acc += ainv[m * NS + r] * stage[r * nmo + p];
+            if (r < n) acc += ainv[m * NS + r] * widen(stage[r * nmo + p]);
         }
         t[m] = acc;
       }
@@ -213,10 +214,10 @@ __global__ void __launch_bounds__(256) k_det(WfDev wf, int64_t W, const TA* __re
         for (int r = 0; r < NS; ++r) {
           double acc = 0.0;
           if (r < n) {
-            acc = stage[(NS + r) * nmo + p];
+            acc = widen(stage[(NS + r) * nmo + p]);
 #pragma unroll
             for (int m = 0; m < NS; ++m)
-              if (m < n) acc -= stage[(NS + r) * nmo + m] * t[m];
+              if (m < n) acc -= widen(stage[(NS + r) * nmo + m]) * t[m];
           }
           y[r] = acc;
         }
@@ -283,17 +284,17 @@ __global__ void __launch_bounds__(256) k_det(WfDev wf, int64_t W, const TA* __re
 // accesses are served per half warp (two teams of 8), and this offset puts
 // the second team on the other 16 bank pairs both for broadcast reads and
 // for row reads of 8 consecutive doubles
-static int walker_stride(const WfDev& wf, int NS, bool kin) {
+static int walker_stride(const WfDev& wf, int NS, bool kin, int ta_bytes) {
   const int nch = kin ? 2 : 1;
   const int tab = kin ? wf.tab_elems : (wf.nh[0] * wf.nv[0] + wf.nh[1] * wf.nv[1]);
-  int s = nch * NS * wf.n_mo + NS * NS + tab;
+  int s = (nch * NS * wf.n_mo * ta_bytes + 7) / 8 + NS * NS + tab;
   while (s % 16 != 8) ++s;
   return s;
 }
 
-size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin) {
+size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin, int ta_bytes) {
   const int nexc = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
-  return sizeof(double) * ((size_t)(256 / TS) * walker_stride(wf, NS, kin) + wf.n_det) +
+  return sizeof(double) * ((size_t)(256 / TS) * walker_stride(wf, NS, kin, ta_bytes) + wf.n_det) +
          sizeof(int) * (10 * (size_t)nexc + 2 * (size_t)wf.n_det);
 }
 
@@ -302,8 +303,8 @@ static cudaError_t launch_ns(const WfDev& wf, int64_t W, const Workspace& ws, bo
                              double* log_psi, cudaStream_t st) {
   constexpr int WPB = 256 / TS;
   const dim3 grid((unsigned)((W + WPB - 1) / WPB));
-  const int stride = walker_stride(wf, NS, kin);
-  const size_t smem = det_smem_bytes(wf, NS, TS, kin);
+  const int stride = walker_stride(wf, NS, kin, (int)sizeof(TA));
+  const size_t smem = det_smem_bytes(wf, NS, TS, kin, (int)sizeof(TA));
   const TA* mo = static_cast<const TA*>(ws.mo);
   auto kern = kin ? k_det<NS, TS, TA, true> : k_det<NS, TS, TA, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -24,6 +24,12 @@ namespace qmc {
 constexpr int kMaxShells = 128;
 constexpr int kMaxExc = 512;   // unique excitations per spin channel
 constexpr int kMaxDets = 4096;
+constexpr int kMaxShellAo = 16;  // AOs of one shell record (longer runs are split)
+constexpr int kTcPass = 32;      // AO columns per K-pass of the tensor-core AO stage
+constexpr int kMaxTcPass = 16;   // passes (QMC_MAX_AO columns, gaps of < kMaxShellAo per pass)
+// two-stream pipeline of the local-energy stages: chunk size and count bound
+constexpr int64_t kChunk = 32768;
+constexpr int kMaxChunks = 64;
 
 // One radial function shared by the AOs of a shell (same atom, kind, kn, l
 // and primitives).  Radial normalisation and contraction coefficients are
@@ -62,8 +68,17 @@ struct WfDev {
   const uint32_t* mo_tc_lo;
   const double* ao_ang;  // [n_ao] angular normalisation factors (folded into mo64)
   const int* ao_prim;    // [n_ao + 1] first input primitive of each AO (gradient layout)
-  int k_pad;        // AO dimension padded to a multiple of the MMA K step
-  int shell_part[5];  // tensor-core AO stage: thread part q takes shells [part[q], part[q+1])
+  // tensor-core AO stage: AO b sits in column ao_col[b] of the K dimension,
+  // packed into n_pass passes of kTcPass columns (no shell straddles two
+  // passes); in pass p, thread part q evaluates the shells
+  // tc_shells[part_off[p][q] .. part_off[p][q+1]), and columns
+  // [pass_cols[p], kTcPass) of the pass are unused (zero)
+  const int* ao_col;     // [n_ao]
+  const int* tc_shells;  // [n_shell]
+  int k_pad;             // n_pass * kTcPass (0 when the form has no tensor-core stage)
+  int n_pass;
+  int pass_cols[kMaxTcPass];
+  int part_off[kMaxTcPass][5];
 };
 
 struct Workspace {
@@ -106,7 +121,7 @@ __device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
 #endif
 
 int det_team_size(const WfDev& wf);
-size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin);
+size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin, int ta_bytes = 8);
 
 // initial walker positions for the serving loop: home nucleus per electron
 struct InitSpec {

@@ -54,6 +54,11 @@ struct qmc_wf {
   // optional per-stage timing events
   bool timing = false;
   bool timed_once = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int timed_chunks = 0;
+  cudaEvent_t tev[qmc::kMaxChunks][6] = {};  // per chunk: Jastrow, AO+MO, det (start, end)
+  // two-stream chunk pipeline (created with the wavefunction)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_ao[qmc::kMaxChunks] = {};
   std::mutex mu;
 };
