@@ -70,7 +70,7 @@ typedef enum { QMC_FP64 = 0, QMC_FP32 = 1, QMC_MIXED_TF32 = 2, QMC_MIXED_BF16 = 
 #define QMC_MAX_ATOMS 16
 #define QMC_MAX_SPIN_ELECTRONS 8 /* per spin channel */
 #define QMC_MAX_MO 32            /* MOs (tensor-core forms: 16) */
-#define QMC_MAX_AO 256           /* AOs (tensor-core forms: 64) */
+#define QMC_MAX_AO 256           /* AOs */
 #define QMC_MAX_PRIM 8           /* primitives per contracted Gaussian */
 
 /* Nuclei and electron counts (Eq. Hmol).  Host arrays. */

@@ -150,6 +150,17 @@ size_t core_offset_words(int row, int k, int k_pad) {
   return (size_t)(row / 8) * (k_pad / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4 + (k % 4);
 }
 
+// Position of the Cartesian monomial x^a y^b z^c (a + b + c = l <= 2) in the
+// canonical order s; x, y, z; xx, xy, xz, yy, yz, zz.
+int tc_canonical_index(int l, int a, int b, int c) {
+  if (l == 0) return 0;
+  if (l == 1) return a ? 0 : b ? 1 : 2;
+  if (a == 2) return 0;
+  if (a == 1) return b ? 1 : 2;
+  if (b == 2) return 3;
+  return b ? 4 : 5;
+}
+
 qmc_status launch_status(cudaError_t e, const char* where) {
   return e == cudaSuccess ? QMC_OK : cuda_fail(e, where);
 }
@@ -161,7 +172,7 @@ qmc_status build_tables(qmc_wf* wf) {
   const int na = h.na, nup = h.nup, ndn = h.ndn, nao = h.nao, nmo = h.nmo, ndet = h.ndet;
   const int prec = wf->precision;
   const bool tc = prec == QMC_MIXED_TF32 || prec == QMC_MIXED_BF16;
-  if (tc && (nmo > 16 || nao > 64)) return fail(QMC_ERR_UNSUPPORTED, "tensor-core forms need n_mo <= 16, n_ao <= 64");
+  if (tc && nmo > 16) return fail(QMC_ERR_UNSUPPORTED, "tensor-core forms need n_mo <= 16");
   if (prec == QMC_MIXED_BF16) return fail(QMC_ERR_UNSUPPORTED, "BF16 form not built");
   WfDev d{};
   d.n_atom = na;
@@ -254,11 +265,25 @@ qmc_status build_tables(qmc_wf* wf) {
   if (tc) {
     std::vector<int> first_shell;  // first shell of each pass
     int col = 0;
+    std::vector<int> shell_col(d.n_shell), shell_type(d.n_shell);
     for (int s = 0; s < d.n_shell; ++s) {
       const ShellDev& q = shells[s];
       if (col % kTcPass + q.n_ao > kTcPass) col = (int)round_up(col, kTcPass);
       if (col % kTcPass == 0 && (int)first_shell.size() == col / kTcPass) first_shell.push_back(s);
-      for (int k = 0; k < q.n_ao; ++k) ao_col[q.ao_first + k] = col + k;
+      // a complete Cartesian s, p or d shell gets its columns in the
+      // canonical order (x, y, z / xx, xy, xz, yy, yz, zz), which the kernel
+      // evaluates without per-AO power lookups
+      std::vector<int> canon(q.n_ao, -1);
+      bool complete = q.l <= 2 && q.n_ao == (q.l + 1) * (q.l + 2) / 2;
+      for (int k = 0; k < q.n_ao && complete; ++k) {
+        const int pw = ao_pow[q.ao_first + k];
+        const int j = tc_canonical_index(q.l, pw & 15, (pw >> 4) & 15, (pw >> 8) & 15);
+        for (int k2 = 0; k2 < k; ++k2) complete = complete && canon[k2] != j;
+        canon[k] = j;
+      }
+      shell_type[s] = complete ? 1 + q.l : 0;
+      shell_col[s] = col % kTcPass;
+      for (int k = 0; k < q.n_ao; ++k) ao_col[q.ao_first + k] = col + (complete ? canon[k] : k);
       col += q.n_ao;
     }
     d.n_pass = (int)first_shell.size();
@@ -281,7 +306,7 @@ qmc_status build_tables(qmc_wf* wf) {
       for (int q = 0; q < 4; ++q) {
         std::sort(part[q].begin(), part[q].end());
         d.part_off[p][q] = (int)tc_shells.size();
-        tc_shells.insert(tc_shells.end(), part[q].begin(), part[q].end());
+        for (int s : part[q]) tc_shells.push_back(s | (shell_col[s] << 8) | (shell_type[s] << 16));
       }
       d.part_off[p][4] = (int)tc_shells.size();
     }
@@ -350,6 +375,8 @@ qmc_status build_tables(qmc_wf* wf) {
 
   // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
   d.k_pad = tc ? d.n_pass * kTcPass : 0;
+  if (tc && tc_smem_bytes(d, 2) > 227 * 1024)
+    return fail(QMC_ERR_UNSUPPORTED, "tensor-core AO stage exceeds shared memory (too many AOs or shells)");
   std::vector<uint32_t> tc_hi, tc_lo;
   if (tc) {
     tc_hi.assign((size_t)16 * d.k_pad, 0u);

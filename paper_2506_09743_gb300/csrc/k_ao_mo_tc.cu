@@ -170,32 +170,57 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
     for (int k = wf.pass_cols[pass] + part; k < kPass; k += kParts)
       for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
     const int s_begin = wf.part_off[pass][part], s_end = wf.part_off[pass][part + 1];
-    int cur_atom = -1;
-    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, rho = 0.f, irho = 0.f;
+    int cur_atom = -1, pow_atom = -1;
+    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, rho = 0.f, irho = 0.f, G = 0.f;
     float px[5], py[5], pz[5];
+    // value channel P f and kinetic channel
+    //   (lap + 2 grad J . grad)(P f) = f lap P + P (f2 + 2 (l+1) g1 + 2 g1 gJ.d) + 2 f gJ.grad P
+    auto emit = [&](int col, float v, float kin) {
+      put(0, col, live ? v : 0.f);
+      if (NCH == 2) put(1, col, live ? kin : 0.f);
+    };
     for (int q = s_begin; q < s_end; ++q) {
-      const ShellDev& sh = sh_s[list_s[q]];
+      const int ent = list_s[q];
+      const ShellDev& sh = sh_s[ent & 0xff];
+      const int c0 = (ent >> 8) & 0xff, type = ent >> 16;
       if (sh.atom != cur_atom) {
         cur_atom = sh.atom;
         displacement(rx, ry, rz, wf.atom_xyz[cur_atom], dx, dy, dz);
         r2 = dx * dx + dy * dy + dz * dz;
         irho = rsqrtf(r2);
         rho = r2 * irho;
-        pow_table(dx, px); pow_table(dy, py); pow_table(dz, pz);
+        G = gjx * dx + gjy * dy + gjz * dz;
       }
-      float f, g1, f2;
+      float f, g1 = 0.f, f2 = 0.f;
       shell_radial(sh, r2, rho, irho, f, g1, f2, NCH == 2);
-      const float radial_lap = f2 + float(2 * (sh.l + 1)) * g1;
-      for (int k = 0; k < sh.n_ao; ++k) {
-        const int b = sh.ao_first + k;
-        const int col = col_s[b] - pass * kPass;
-        float P, Px, Py, Pz, lapP;
-        angular(pow_s[b], px, py, pz, P, Px, Py, Pz, lapP, NCH == 2);
-        put(0, col, live ? P * f : 0.f);
-        if (NCH == 2) {
-          const float gx = f * Px + P * g1 * dx, gy = f * Py + P * g1 * dy, gz = f * Pz + P * g1 * dz;
-          const float kin = f * lapP + P * radial_lap + 2.f * (gjx * gx + gjy * gy + gjz * gz);
-          put(1, col, live ? kin : 0.f);
+      const float RL = f2 + float(2 * (sh.l + 1)) * g1 + 2.f * g1 * G;
+      const float tf = 2.f * f;
+      if (type == 1) {
+        emit(c0, f, RL);
+      } else if (type == 2) {
+        emit(c0 + 0, dx * f, dx * RL + tf * gjx);
+        emit(c0 + 1, dy * f, dy * RL + tf * gjy);
+        emit(c0 + 2, dz * f, dz * RL + tf * gjz);
+      } else if (type == 3) {
+        const float fx = f * dx, fy = f * dy, fz = f * dz;
+        const float Rx = RL * dx, Ry = RL * dy, Rz = RL * dz;
+        emit(c0 + 0, fx * dx, tf + Rx * dx + 2.f * tf * gjx * dx);
+        emit(c0 + 1, fx * dy, Rx * dy + tf * (gjx * dy + gjy * dx));
+        emit(c0 + 2, fx * dz, Rx * dz + tf * (gjx * dz + gjz * dx));
+        emit(c0 + 3, fy * dy, tf + Ry * dy + 2.f * tf * gjy * dy);
+        emit(c0 + 4, fy * dz, Ry * dz + tf * (gjy * dz + gjz * dy));
+        emit(c0 + 5, fz * dz, tf + Rz * dz + 2.f * tf * gjz * dz);
+      } else {
+        if (pow_atom != cur_atom) {
+          pow_atom = cur_atom;
+          pow_table(dx, px); pow_table(dy, py); pow_table(dz, pz);
+        }
+        for (int k = 0; k < sh.n_ao; ++k) {
+          const int b = sh.ao_first + k;
+          const int col = col_s[b] - pass * kPass;
+          float P, Px, Py, Pz, lapP;
+          angular(pow_s[b], px, py, pz, P, Px, Py, Pz, lapP, NCH == 2);
+          emit(col, P * f, f * lapP + P * RL + tf * (gjx * Px + gjy * Py + gjz * Pz));
         }
       }
     }

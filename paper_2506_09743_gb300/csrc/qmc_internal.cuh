@@ -72,7 +72,10 @@ struct WfDev {
   // packed into n_pass passes of kTcPass columns (no shell straddles two
   // passes); in pass p, thread part q evaluates the shells
   // tc_shells[part_off[p][q] .. part_off[p][q+1]), and columns
-  // [pass_cols[p], kTcPass) of the pass are unused (zero)
+  // [pass_cols[p], kTcPass) of the pass are unused (zero).  A list entry is
+  // shell | first column within the pass << 8 | type << 16, type 1 + l for a
+  // complete s, p or d shell whose AOs sit in canonical Cartesian order
+  // (x, y, z; xx, xy, xz, yy, yz, zz) from that column, 0 otherwise
   const int* ao_col;     // [n_ao]
   const int* tc_shells;  // [n_shell]
   int k_pad;             // n_pass * kTcPass (0 when the form has no tensor-core stage)
@@ -121,6 +124,7 @@ __device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
 #endif
 
 int det_team_size(const WfDev& wf);
+size_t tc_smem_bytes(const WfDev& wf, int nch);
 size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin, int ta_bytes = 8);
 
 // initial walker positions for the serving loop: home nucleus per electron

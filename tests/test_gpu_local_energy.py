@@ -61,6 +61,54 @@ def test_reduced_precision_parity(pkg, name, precision):
     print(f"{name} {precision} |dE| Ha {st}")
 
 
+def _co_with_general_shells():
+    """CO plus AOs outside the complete s/p/d shells: a Cartesian f shell on C
+    (l = 3), an incomplete d shell (xy, zz) and a lone p_x on O, with small
+    random MO coefficients on the new AOs."""
+    import dataclasses
+
+    mol = qi.make_co(n_det=20)
+    rng = np.random.default_rng(17)
+    extra = [(0, (3, 0, 0)), (0, (2, 1, 0)), (0, (2, 0, 1)), (0, (1, 2, 0)), (0, (1, 1, 1)),
+             (0, (1, 0, 2)), (0, (0, 3, 0)), (0, (0, 2, 1)), (0, (0, 1, 2)), (0, (0, 0, 3)),
+             (1, (1, 1, 0)), (1, (0, 0, 2)), (1, (1, 0, 0))]
+    atom, pw, start = list(mol.ao_atom), [list(p) for p in mol.ao_pow], list(mol.ao_prim_start)
+    pexp, pcoef = list(mol.prim_exp), list(mol.prim_coef)
+    groups = {}
+    for k, (a, (x, y, z)) in enumerate(extra):
+        key = (a, x + y + z, k >= 12)
+        if key not in groups:
+            groups[key] = (np.sort(np.exp(rng.uniform(np.log(0.3), np.log(8.0), size=2)))[::-1],
+                           rng.uniform(0.2, 1.0, size=2))
+        al, c = groups[key]
+        atom.append(a)
+        pw.append([x, y, z, 0])
+        pexp.extend(al)
+        pcoef.extend(c)
+        start.append(len(pexp))
+    mo = np.vstack([mol.mo_coeff, 0.05 * rng.standard_normal((len(extra), mol.n_mo))])
+    return dataclasses.replace(
+        mol, name="co_general_shells", ao_atom=np.asarray(atom, np.int32),
+        ao_kind=np.concatenate([mol.ao_kind, np.full(len(extra), qi.GTO, np.int32)]),
+        ao_pow=np.asarray(pw, np.int32), ao_prim_start=np.asarray(start, np.int32),
+        prim_exp=np.asarray(pexp), prim_coef=np.asarray(pcoef), mo_coeff=mo)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_tf32"])
+def test_general_shells_parity(pkg, precision):
+    """f shells and incomplete shells take the general angular path of the AO
+    stages (the tensor-core stage evaluates complete s/p/d shells in a
+    canonical column order and everything else by powers)."""
+    mol = _co_with_general_shells()
+    r = qi.walkers(mol, 300, seed=23)
+    E_ref, _, sens = oracle_reference(mol, r)
+    E, _ = _run(pkg, mol, r, precision)
+    if precision == "fp64":
+        fp64_check(E, E_ref, sens, min_within=0.98)
+    else:
+        mixed_check(E, E_ref, sens)
+
+
 def test_closed_forms_on_gpu(pkg):
     mol = qi.make_hydrogenic(1.0, 1.0)
     r = qi.walkers(mol, 333, seed=4)
