@@ -39,7 +39,7 @@ WORKLOAD = "CO 14e- 58 GTO 14 MO 100 det, 262144 walkers"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)
 # DRAM bytes (read + write) per walker of the mixed-form k_det launch, from an ncu capture of that
 # kernel on 131,072 CO walkers (242.8 MB); set to None whenever the kernel changes.
-DET_TRAFFIC_BYTES_PER_WALKER = 242.824192e6 / 131072
+DET_TRAFFIC_BYTES_PER_WALKER = 243.006720e6 / 131072
 
 
 def det_stage_flops(mol) -> float:
@@ -244,6 +244,46 @@ def run_secondary(device, stream, barrier, flush):
     return out
 
 
+DET_SWEEP = (1, 4, 100, 876, 1716)
+
+
+def run_det_sweep(device, stream, barrier, flush, W=65536, steps=3):
+    """Explicit versus table determinants across expansion sizes (the shape of
+    the paper's comparison, Sec. 2.2 / App. A): CO-shaped wavefunction with
+    n_det determinants drawn from the (10e, 12o) space, mixed form, E_L
+    walker-evals/s for both methods on the same walkers."""
+    import torch
+
+    from paper_2506_09743_gb300 import Wavefunction
+
+    rows = []
+    for n_det in DET_SWEEP:
+        mol = qi.make_co(n_det=n_det)
+        x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
+        e = torch.empty(W, dtype=torch.float64, device="cuda")
+        row = {"n_det": n_det}
+        for method in ("table", "explicit"):
+            wf = Wavefunction(mol, precision="mixed_tf32", device=device)
+            wf.set_det_method(method)
+            for _ in range(3):
+                wf.local_energy(x, e_loc=e, want_log_psi=False)
+            barrier()
+            tot = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                wf.local_energy(x, e_loc=e, want_log_psi=False)
+                b.record(stream)
+                b.synchronize()
+                tot += a.elapsed_time(b)
+            row[f"{method}_walker_evals_per_s"] = W * steps / (tot / 1e3)
+            wf.close()
+        row["speedup"] = row["table_walker_evals_per_s"] / row["explicit_walker_evals_per_s"]
+        rows.append(row)
+    return {"walkers": W, "precision": "mixed_tf32", "rows": rows}
+
+
 def reduce_max(v: float, dist=None) -> float:
     """Maximum of a per-rank value over the process group (identity alone)."""
     if dist is None or not dist.is_initialized():
@@ -277,6 +317,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=160,
                     help="requests of the Poisson serving run (0 = skip the serving measurement)")
     ap.add_argument("--no-serving-fp64", action="store_true", help="serve the mix in the mixed form only")
+    ap.add_argument("--no-det-sweep", action="store_true", help="skip the explicit-versus-table sweep")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -389,6 +430,7 @@ def main():
     del xs
 
     secondary = run_secondary(local, stream, barrier, flush) if world == 1 else None
+    det_sweep = run_det_sweep(local, stream, barrier, flush) if world == 1 and not args.no_det_sweep else None
 
     serving_out = None
     if args.serving_requests > 0 and world == 1:
@@ -427,6 +469,7 @@ def main():
         "metropolis_walker_steps_per_s": mh_steps_per_s,
         "serving": serving_out,
         "secondary": secondary,
+        "det_sweep": det_sweep,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

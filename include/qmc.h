@@ -246,6 +246,22 @@ qmc_status qmc_set_params(qmc_wf* wf, const double* params);
  * [4] backflow w, [5] = n_param.  offsets may be NULL. */
 qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[6]);
 
+/* Determinant method of the local-energy and sampling calls.
+ *  QMC_DET_TABLE     (default) excited determinants from tables of the
+ *                    reference inverse: D_X / D_0 and the kinetic trace of
+ *                    each excitation from k x k minors (Eq. table, App. H).
+ *  QMC_DET_EXPLICIT  every distinct spin excitation X gets its own matrix
+ *                    A_X, factorised by LU with partial pivoting; D_X and
+ *                    Tr(A_X^-1 B_X) (Jacobi formula) from the factors.  The
+ *                    baseline of the paper's explicit-versus-table comparison
+ *                    (Sec. 2.2, App. A); O(n^3) per distinct excitation.
+ * Both give the same local energy up to rounding.  Backflow wavefunctions
+ * (single determinant) ignore the setting.  QMC_ERR_ARG for an unknown
+ * method; QMC_ERR_UNSUPPORTED when the explicit stage's shared-memory tables
+ * (both spins' distinct excitations) do not fit. */
+typedef enum { QMC_DET_TABLE = 0, QMC_DET_EXPLICIT = 1 } qmc_det_method;
+qmc_status qmc_set_det_method(qmc_wf* wf, int32_t method);
+
 /* Per-stage device timing (tracing aid; the paper has no counterpart).  When
  * enabled, every qmc_local_energy / qmc_sample evaluation records CUDA events
  * on its stream around its three stages: [0] Jastrow and Coulomb terms,

@@ -136,6 +136,12 @@ class Wavefunction:
                                              _stream_handle(stream)))
         return float(stats[0]), float(stats[1]), grad, forces
 
+    def set_det_method(self, method: str):
+        """'table' (default, Eq. table) or 'explicit' (LU of every distinct
+        excited matrix; the baseline of the paper's comparison)."""
+        code = {"table": 0, "explicit": 1}[method]
+        _lib.check(self._lib.qmc_set_det_method(self._h, code))
+
     def set_timing(self, enable: bool = True):
         """Record per-stage CUDA events on the call's stream (tracing aid)."""
         _lib.check(self._lib.qmc_set_timing(self._h, 1 if enable else 0))

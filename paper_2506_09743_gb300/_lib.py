@@ -24,7 +24,7 @@ EXPORTED = (
     "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_energy_grad",
     "qmc_set_params", "qmc_server_create", "qmc_server_destroy", "qmc_server_add_wf", "qmc_server_submit",
     "qmc_server_progress", "qmc_server_results", "qmc_server_free_bytes", "qmc_server_clock",
-    "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms",
+    "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method",
     "qmc_last_error",
 )
 
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
     lib.qmc_set_params.restype = c_int32
     lib.qmc_set_timing.argtypes = [c_void_p, c_int32]
     lib.qmc_set_timing.restype = c_int32
+    lib.qmc_set_det_method.argtypes = [c_void_p, c_int32]
+    lib.qmc_set_det_method.restype = c_int32
     lib.qmc_last_stage_ms.argtypes = [c_void_p, POINTER(ctypes.c_float), c_int32]
     lib.qmc_last_stage_ms.restype = c_int32
     lib.qmc_server_create.argtypes = [c_int32, c_size_t, c_int32, POINTER(c_void_p)]

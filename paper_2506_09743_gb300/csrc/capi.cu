@@ -497,18 +497,6 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
     delete wf;
     return st;
   }
-  {
-    DeviceGuard guard(wf->device);
-    cudaError_t e = cudaStreamCreateWithFlags(&wf->aux, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&wf->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&wf->ev_join, cudaEventDisableTiming);
-    for (int c = 0; c < kMaxChunks && e == cudaSuccess; ++c)
-      e = cudaEventCreateWithFlags(&wf->ev_ao[c], cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-      qmc_destroy_wf(wf);
-      return cuda_fail(e, "pipeline streams");
-    }
-  }
   *out = wf;
   return QMC_OK;
 }
@@ -521,14 +509,8 @@ void qmc_destroy_wf(qmc_wf* wf) {
     if (wf->ws) cudaFree(wf->ws);
     if (wf->stage) cudaFree(wf->stage);
     if (wf->gws) cudaFree(wf->gws);
-    for (auto& row : wf->tev)
-      for (auto& e : row)
-        if (e) cudaEventDestroy(e);
-    for (auto& e : wf->ev_ao)
+    for (auto& e : wf->tev)
       if (e) cudaEventDestroy(e);
-    if (wf->ev_fork) cudaEventDestroy(wf->ev_fork);
-    if (wf->ev_join) cudaEventDestroy(wf->ev_join);
-    if (wf->aux) cudaStreamDestroy(wf->aux);
   }
   delete wf;
 }
@@ -566,37 +548,27 @@ qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[
   return QMC_OK;
 }
 
-static void mark(qmc_wf* wf, int c, int k, cudaStream_t st) {
-  if (wf->timing && c < kMaxChunks) cudaEventRecord(wf->tev[c][k], st);
-}
-
-// View of the workspace for walkers [c0, c0 + n) of the batch.
-static Workspace chunk_view(const qmc_wf* wf, const Workspace& ws, int64_t c0, int nch) {
-  Workspace v = ws;
-  const size_t ta = ta_size(wf->precision);
-  v.gradJ = static_cast<char*>(ws.gradJ) + c0 * ta;
-  v.jscal = ws.jscal + c0;
-  v.mo = static_cast<char*>(ws.mo) + (size_t)c0 * wf->dev.n_elec * nch * ws.nmp * ta;
-  return v;
+static void mark(qmc_wf* wf, int k, cudaStream_t st) {
+  if (wf->timing) cudaEventRecord(wf->tev[k], st);
 }
 
 // Local-energy (kinetic) or value-only evaluation of W walkers.
-// Stages: Jastrow + Coulomb, AO + AO->MO contraction, determinants, in order
-// on the caller's stream.  (A two-stream pipeline over walker chunks, with
-// each chunk's determinant stage overlapping the next chunk's AO stage, fits
-// both kernels on one SM but was measured slower on CO: a determinant block
-// sharing an SM keeps half of its warps and loses more FP64 throughput than
-// the overlap gains; `pipelined` stays off.)  Backflow wavefunctions run the
-// general FP64 kernel.
+// Stages: Jastrow + Coulomb, AO + AO->MO contraction, determinants (table
+// method, or explicit per-excitation LU when selected), in order on the
+// caller's stream.  (A two-stream pipeline over walker chunks, with each
+// chunk's determinant stage overlapping the next chunk's AO stage, was
+// measured slower on CO: a determinant block sharing an SM keeps half of its
+// warps and loses more FP64 throughput than the overlap gains.)  Backflow
+// wavefunctions run the general FP64 kernel.
 static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                             int* err_flag, bool kinetic, double* e_loc, double* log_psi, cudaStream_t st) {
   const WfDev& d = wf->dev;
   if (d.bf_w != 0.0) {  // backflow: one general kernel (Jastrow, orbitals, Eq. nabla_d, E_L)
-    mark(wf, 0, 0, st);
+    mark(wf, 0, st);
     qmc_status s = launch_status(launch_eloc_general(d, walkers, W, ldw, kinetic, e_loc, log_psi, st), "general");
     if (s) return s;
-    for (int k = 1; k < 6; ++k) mark(wf, 0, k, st);
-    if (wf->timing) { wf->timed_once = true; wf->timed_chunks = 1; }
+    for (int k = 1; k < 6; ++k) mark(wf, k, st);
+    if (wf->timing) wf->timed_once = true;
     return QMC_OK;
   }
   const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
@@ -605,50 +577,25 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
     qmc_status s = launch_status(cudaMemsetAsync(err_flag, 0, sizeof(int), st), "error flag reset");
     if (s) return s;
   }
-  const bool pipelined = false;
-  const int64_t chunk = pipelined ? kChunk : W;
-  const int n_chunks = (int)((W + chunk - 1) / chunk);
-  cudaStream_t det_st = pipelined ? wf->aux : st;
-  if (pipelined) {
-    qmc_status s = launch_status(cudaEventRecord(wf->ev_fork, st), "fork");
-    if (!s) s = launch_status(cudaStreamWaitEvent(wf->aux, wf->ev_fork, 0), "fork");
-    if (s) return s;
-  }
-  for (int c = 0; c < n_chunks; ++c) {
-    const int64_t c0 = c * chunk, n = std::min<int64_t>(chunk, W - c0);
-    const Workspace v = chunk_view(wf, ws, c0, nch);
-    const double* wk = walkers + c0;
-    mark(wf, c, 0, st);
-    qmc_status s = launch_status(launch_jastrow(d, wf->precision, wk, n, ldw, v, kinetic, st), "jastrow");
-    if (s) return s;
-    mark(wf, c, 1, st);
-    mark(wf, c, 2, st);
-    s = launch_status(tc ? launch_ao_mo_tc(d, wf->precision, wk, n, ldw, v, nch, err_flag, st)
-                         : launch_ao_mo_simt(d, wf->precision, wk, n, ldw, v, nch, st),
-                      "ao_mo");
-    if (s) return s;
-    mark(wf, c, 3, st);
-    if (pipelined) {
-      s = launch_status(cudaEventRecord(wf->ev_ao[c], st), "chunk event");
-      if (!s) s = launch_status(cudaStreamWaitEvent(det_st, wf->ev_ao[c], 0), "chunk event");
-      if (s) return s;
-    }
-    mark(wf, c, 4, det_st);
-    s = launch_status(launch_det(d, wf->precision, n, v, kinetic, e_loc ? e_loc + c0 : nullptr,
-                                 log_psi ? log_psi + c0 : nullptr, det_st),
-                      "det");
-    if (s) return s;
-    mark(wf, c, 5, det_st);
-  }
-  if (pipelined) {
-    qmc_status s = launch_status(cudaEventRecord(wf->ev_join, det_st), "join");
-    if (!s) s = launch_status(cudaStreamWaitEvent(st, wf->ev_join, 0), "join");
-    if (s) return s;
-  }
-  if (wf->timing) {
-    wf->timed_once = true;
-    wf->timed_chunks = std::min(n_chunks, kMaxChunks);
-  }
+  const Workspace& v = ws;
+  mark(wf, 0, st);
+  qmc_status s = launch_status(launch_jastrow(d, wf->precision, walkers, W, ldw, v, kinetic, st), "jastrow");
+  if (s) return s;
+  mark(wf, 1, st);
+  mark(wf, 2, st);
+  s = launch_status(tc ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag, st)
+                       : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, v, nch, st),
+                    "ao_mo");
+  if (s) return s;
+  mark(wf, 3, st);
+  mark(wf, 4, st);
+  s = launch_status(wf->det_method == QMC_DET_EXPLICIT
+                        ? launch_det_explicit(d, wf->precision, W, v, kinetic, e_loc, log_psi, st)
+                        : launch_det(d, wf->precision, W, v, kinetic, e_loc, log_psi, st),
+                    "det");
+  if (s) return s;
+  mark(wf, 5, st);
+  if (wf->timing) wf->timed_once = true;
   return QMC_OK;
 }
 
@@ -874,16 +821,26 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
   return e == cudaSuccess ? QMC_OK : cuda_fail(e, "energy statistics");
 }
 
+qmc_status qmc_set_det_method(qmc_wf* wf, int32_t method) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  if (method != QMC_DET_TABLE && method != QMC_DET_EXPLICIT) return fail(QMC_ERR_ARG, "unknown determinant method");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  if (method == QMC_DET_EXPLICIT &&
+      det_explicit_smem_bytes(wf->dev, true, (int)ta_size(wf->precision)) > 227 * 1024)
+    return fail(QMC_ERR_UNSUPPORTED, "explicit determinant stage exceeds shared memory");
+  wf->det_method = method;
+  return QMC_OK;
+}
+
 qmc_status qmc_set_timing(qmc_wf* wf, int32_t enable) {
   if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
   std::lock_guard<std::mutex> lock(wf->mu);
   DeviceGuard guard(wf->device);
-  if (enable && !wf->tev[0][0])
-    for (auto& row : wf->tev)
-      for (auto& e : row) {
-        cudaError_t r = cudaEventCreate(&e);
-        if (r != cudaSuccess) return cuda_fail(r, "event create");
-      }
+  if (enable && !wf->tev[0])
+    for (auto& e : wf->tev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return cuda_fail(r, "event create");
+    }
   wf->timing = enable != 0;
   return QMC_OK;
 }
@@ -893,16 +850,9 @@ qmc_status qmc_last_stage_ms(qmc_wf* wf, float* ms, int32_t n) {
   std::lock_guard<std::mutex> lock(wf->mu);
   if (!wf->timed_once) return fail(QMC_ERR_ARG, "no timed evaluation yet");
   DeviceGuard guard(wf->device);
-  for (int k = 0; k < n; ++k) ms[k] = 0.0f;
-  for (int c = 0; c < wf->timed_chunks; ++c) {
-    cudaError_t r = cudaEventSynchronize(wf->tev[c][5]);
-    for (int k = 0; k < n && r == cudaSuccess; ++k) {
-      float t = 0.0f;
-      r = cudaEventElapsedTime(&t, wf->tev[c][2 * k], wf->tev[c][2 * k + 1]);
-      ms[k] += t;
-    }
-    if (r != cudaSuccess) return cuda_fail(r, "event timing");
-  }
+  cudaError_t r = cudaEventSynchronize(wf->tev[5]);
+  for (int k = 0; k < n && r == cudaSuccess; ++k) r = cudaEventElapsedTime(&ms[k], wf->tev[2 * k], wf->tev[2 * k + 1]);
+  if (r != cudaSuccess) return cuda_fail(r, "event timing");
   return QMC_OK;
 }
 

@@ -34,54 +34,6 @@
 
 namespace qmc {
 
-// Exact float -> double widening with integer operations only (no FP64-pipe
-// conversion).  Subnormal inputs are flushed to signed zero.
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
-  unsigned hi;
-  if (ex == 0u) hi = sign;
-  else if (ex == 0xffu) hi = sign | 0x7ff00000u | (man >> 3);
-  else hi = sign | ((ex + 896u) << 20) | (man >> 3);
-  const unsigned lo = ex == 0u ? 0u : (man << 29);
-  return __hiloint2double((int)hi, (int)lo);
-}
-__device__ __forceinline__ double widen(double d) { return d; }
-
-// |x| as an ordered integer key (the IEEE bit pattern with the sign cleared
-// orders like |x| for finite x), so pivot search needs no FP64 compare.
-__device__ __forceinline__ long long abs_key(double x) {
-  return __double_as_longlong(x) & 0x7fffffffffffffffll;
-}
-
-// Reciprocal by Newton-Raphson iteration r <- r + r (1 - a r) (quadratic
-// convergence) from an FP32 seed: the seed is built from the top bits of a
-// with integer operations, inverted with the FP32 reciprocal (error < 2^-22)
-// and widened back; two iterations reach the FP64 rounding level.  4 FP64
-// instructions instead of a full division.  Pivots outside the FP32 range
-// (never met by orbital matrices) take the IEEE division.
-__device__ __forceinline__ double recip(double a) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
-  const int e = (int)((u >> 52) & 0x7ffu);
-  if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / a;
-  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
-  const float af = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7fffffu));
-  const unsigned rb = __float_as_uint(__frcp_rn(af));
-  const unsigned re = (rb >> 23) & 0xffu;
-  double r = __hiloint2double((int)((rb & 0x80000000u) | ((re + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
-                              (int)(rb << 29));
-  r = fma(r, fma(-a, r, 1.0), r);
-  r = fma(r, fma(-a, r, 1.0), r);
-  return r;
-}
-
-template <int TS>
-__device__ __forceinline__ double team_sum(double v) {
-#pragma unroll
-  for (int o = TS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <int NS, int TS, typename TA, bool KIN>
 __global__ void __launch_bounds__(256) k_det(WfDev wf, int64_t W, const TA* __restrict__ mo, int nmp,
                                              const double* __restrict__ jscal, int64_t ldm, int stride,

@@ -54,11 +54,7 @@ struct qmc_wf {
   // optional per-stage timing events
   bool timing = false;
   bool timed_once = false;
-  int timed_chunks = 0;
-  cudaEvent_t tev[qmc::kMaxChunks][6] = {};  // per chunk: Jastrow, AO+MO, det (start, end)
-  // two-stream chunk pipeline (created with the wavefunction)
-  cudaStream_t aux = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  cudaEvent_t ev_ao[qmc::kMaxChunks] = {};
+  cudaEvent_t tev[6] = {};  // Jastrow, AO+MO, det (start, end)
+  int det_method = QMC_DET_TABLE;
   std::mutex mu;
 };

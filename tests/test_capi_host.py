@@ -93,6 +93,7 @@ def test_calls_on_null_handle_fail_cleanly(lib):
     assert lib.qmc_local_energy(None, None, 0, 0, None, None, None, 0, None) == _lib.QMC_ERR_ARG
     assert lib.qmc_sample(None, None, 1, 1, 1, 0.1, 0, 0, 0, None, None, None, 0, None) == _lib.QMC_ERR_ARG
     assert lib.qmc_workspace_size(None, 10) == 0
+    assert lib.qmc_set_det_method(None, 1) == _lib.QMC_ERR_ARG
     lib.qmc_destroy_wf(None)
 
 

@@ -109,6 +109,37 @@ def test_general_shells_parity(pkg, precision):
         mixed_check(E, E_ref, sens)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tf32"])
+@pytest.mark.parametrize("n_det", [1, 100, 1716])
+def test_explicit_method_parity(pkg, precision, n_det):
+    """Explicit per-excitation LU (the baseline of the paper's comparison,
+    Sec. 2.2 / App. A) against the oracle, and against the table method."""
+    mol = qi.make_co(n_det=n_det)
+    r = qi.walkers(mol, 200, seed=24)
+    E_ref, lp_ref, sens = oracle_reference(mol, r)
+    out = {}
+    for method in ("explicit", "table"):
+        wf = pkg.Wavefunction(mol, precision=precision)
+        wf.set_det_method(method)
+        x = torch.tensor(qi.to_soa(r), device="cuda")
+        e, lp = wf.local_energy(x)
+        torch.cuda.synchronize()
+        out[method] = (e.cpu().numpy(), lp.cpu().numpy())
+        wf.close()
+    E, lp = out["explicit"]
+    if precision == "fp64":
+        fp64_check(E, E_ref, sens, min_within=0.97)
+        scale = np.maximum(1.0, np.abs(lp_ref))
+        assert np.all(np.abs(lp - lp_ref) <= 128 * 2.0 ** -53 * sens * scale)
+    else:
+        mixed_check(E, E_ref, sens)
+    # both methods see the same MO values; they differ by rounding only
+    Et = out["table"][0]
+    bound = 128 * (2.0 ** -53) * sens * np.maximum(1.0, np.abs(E_ref))
+    if precision == "fp64":
+        assert np.all(np.abs(E - Et) <= 2 * bound)
+
+
 def test_closed_forms_on_gpu(pkg):
     mol = qi.make_hydrogenic(1.0, 1.0)
     r = qi.walkers(mol, 333, seed=4)
