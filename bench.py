@@ -241,6 +241,21 @@ def run_secondary(device, stream, barrier, flush):
                 out["li2_energy_grad_note"] = ("131,072 walkers: E_L, mean/variance, gradient of 83 parameters "
                                                "and forces on both nuclei, host-timed (synchronous call)")
             wf.close()
+    # one optimisation step of App. B (10^4 walkers: Eq. nabla_loss gradient, ADAM
+    # update, 500 Metropolis resampling steps), host-timed through qmc_optimize
+    for name in ("lih", "li2"):
+        mol = qi.make_molecule(name)
+        x = torch.tensor(qi.to_soa(qi.walkers(mol, 10000, seed=qi.SEED_WALKERS)), device="cuda")
+        wf = Wavefunction(mol, precision="fp64", device=device)
+        wf.optimize(x, n_iter=1, n_equil=50, n_resample=20, step=0.05, seed=0x5EED)
+        barrier()
+        t0 = time.perf_counter()
+        hist = wf.optimize(x, n_iter=2, n_equil=0, n_resample=500, step=0.05, seed=0x5EED)
+        out[f"{name}_opt_step_ms"] = 1e3 * (time.perf_counter() - t0) / 2
+        out[f"{name}_opt_accept"] = float(hist[:, 2].mean())
+        wf.close()
+    out["opt_step_note"] = ("one App. B optimisation step on 10^4 walkers: gradient (Eq. nabla_loss), ADAM "
+                            "update, parameter upload, 500 Metropolis steps of 0.05 bohr; FP64 form")
     return out
 
 

@@ -262,6 +262,53 @@ qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[
 typedef enum { QMC_DET_TABLE = 0, QMC_DET_EXPLICIT = 1 } qmc_det_method;
 qmc_status qmc_set_det_method(qmc_wf* wf, int32_t method);
 
+/* ---- Wavefunction optimisation (App. B) and batched forces (Sec. 3.3) ----
+ * qmc_optimize runs the optimisation loop of App. B on the FP64 form (the
+ * energy gradient's precondition: one determinant, at most 8 electrons and
+ * 4 per spin): n_equil Metropolis steps, then per optimisation step t = 1 ..
+ * n_iter the energy gradient of Eq. nabla_loss at the current walkers, one
+ * ADAM update of the optimised parameters (Kingma and Ba 2015, Algorithm 1;
+ * App. B: lr 1e-2), the new parameters installed as by qmc_set_params, and
+ * n_resample Metropolis steps with the updated wavefunction (App. B: 500).
+ * Metropolis steps are numbered globally from 0 (step_offset of qmc_sample),
+ * so the run is a pure function of its inputs; the ADAM moments start at zero
+ * on every call.  ADAM rounds each operation once, in the order
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g*g;
+ *   theta = theta - (lr (m / c1)) / (sqrt(v / c2) + eps),  c_k = 1 - b_k^t
+ * with b_k^t formed by repeated multiplication.
+ * walkers: device [3N][ldw], updated in place (the final samples).
+ * cfg->mask: host [n_param] (qmc_param_layout order), nonzero = optimised;
+ * NULL optimises every parameter.  history: host [n_iter][3]: E mean and
+ * variance at the samples of step t (before its update) and the acceptance
+ * rate of the resampling that follows it.  The wavefunction keeps the final
+ * parameters.  Synchronous.  Errors of the composed calls are returned as
+ * they are (the parameters then stay at the last successful update);
+ * QMC_ERR_ARG for bad counts or hyper-parameters (0 <= beta < 1, eps > 0). */
+typedef struct {
+  int32_t n_iter;     /* optimisation steps */
+  int32_t n_equil;    /* Metropolis steps before the first step */
+  int32_t n_resample; /* Metropolis steps after each update */
+  int32_t reserved;   /* must be 0 */
+  double step;        /* Gaussian proposal width per coordinate, bohr */
+  uint64_t seed;      /* Philox key */
+  double lr, beta1, beta2, eps;
+  const uint8_t* mask;
+} qmc_opt_config;
+qmc_status qmc_optimize(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ldw, const qmc_opt_config* cfg,
+                        double* history, void* stream);
+
+/* Forces of Eq. force per batch of samples, as used along the dissociation
+ * curves of Sec. 3.3: the walkers are split into n_batches consecutive
+ * slices (the last takes the remainder) and, with symmetrize != 0, every
+ * slice is joined by the images of its samples under x -> -x, y -> -y and
+ * both (all electrons together; the symmetry of a molecule on the z axis),
+ * before Eq. force is evaluated with that slice's mean energy.  FP64 form,
+ * same precondition as qmc_energy_grad.  walkers: device [3N][ldw].
+ * e_mean: host [n_batches] or NULL.  forces: host [n_batches][n_atom][3].
+ * Synchronous; QMC_ERR_ARG unless 1 <= n_batches <= n_walkers. */
+qmc_status qmc_force_batches(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_batches,
+                             int32_t symmetrize, double* e_mean, double* forces, void* stream);
+
 /* Per-stage device timing (tracing aid; the paper has no counterpart).  When
  * enabled, every qmc_local_energy / qmc_sample evaluation records CUDA events
  * on its stream around its three stages: [0] Jastrow and Coulomb terms,

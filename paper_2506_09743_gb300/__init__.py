@@ -136,6 +136,43 @@ class Wavefunction:
                                              _stream_handle(stream)))
         return float(stats[0]), float(stats[1]), grad, forces
 
+    def optimize(self, walkers, n_iter: int, n_equil: int, n_resample: int, step: float, seed: int,
+                 lr: float = 1e-2, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, mask=None,
+                 n_walkers: int | None = None, stream=None):
+        """The optimisation loop of App. B (qmc_optimize): equilibrate, then per step
+        the Eq. nabla_loss gradient, one ADAM update and n_resample Metropolis steps.
+        walkers (CUDA float64 [3N, ldw]) are updated in place; returns the history
+        [n_iter, 3] (E mean, E variance, acceptance) as a numpy array."""
+        import torch
+
+        assert walkers.is_cuda and walkers.dtype == torch.float64 and walkers.stride(1) == 1
+        W = walkers.shape[1] if n_walkers is None else int(n_walkers)
+        hist = np.zeros((max(n_iter, 1), 3), dtype=np.float64)
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+            assert m.shape == (self.param_layout()[0],)
+        cfg = _lib.OptConfig(n_iter, n_equil, n_resample, 0, step, seed, lr, beta1, beta2, eps,
+                             None if m is None else m.ctypes.data)
+        _lib.check(self._lib.qmc_optimize(self._h, _dptr(walkers), W, walkers.stride(0), ctypes.byref(cfg),
+                                          hist.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
+        return hist[:n_iter]
+
+    def force_batches(self, walkers, n_batches: int, symmetrize: bool = True, n_walkers: int | None = None,
+                      stream=None):
+        """Per-batch (E mean [n_batches], forces [n_batches, n_atom, 3]) of Eq. force, each batch
+        optionally symmetrised about the z axis (qmc_force_batches)."""
+        import torch
+
+        assert walkers.is_cuda and walkers.dtype == torch.float64 and walkers.stride(1) == 1
+        W = walkers.shape[1] if n_walkers is None else int(n_walkers)
+        e = np.zeros(n_batches, dtype=np.float64)
+        f = np.zeros((n_batches, self.mol.n_atom, 3), dtype=np.float64)
+        _lib.check(self._lib.qmc_force_batches(self._h, _dptr(walkers), W, walkers.stride(0), n_batches,
+                                               1 if symmetrize else 0, e.ctypes.data_as(ctypes.c_void_p),
+                                               f.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
+        return e, f
+
     def set_det_method(self, method: str):
         """'table' (default, Eq. table) or 'explicit' (LU of every distinct
         excited matrix; the baseline of the paper's comparison)."""

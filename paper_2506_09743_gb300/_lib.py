@@ -24,7 +24,7 @@ EXPORTED = (
     "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_energy_grad",
     "qmc_set_params", "qmc_server_create", "qmc_server_destroy", "qmc_server_add_wf", "qmc_server_submit",
     "qmc_server_progress", "qmc_server_results", "qmc_server_free_bytes", "qmc_server_clock",
-    "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method",
+    "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method", "qmc_optimize", "qmc_force_batches",
     "qmc_last_error",
 )
 
@@ -66,6 +66,12 @@ class Result(ctypes.Structure):
     _fields_ = [("ticket", c_int64), ("status", c_int32), ("wf_id", c_int32), ("n_walkers", c_int64),
                 ("e_mean", c_double), ("e_var", c_double), ("accept_rate", c_double), ("t_submit", c_double),
                 ("t_admit", c_double), ("t_done", c_double)]
+
+
+class OptConfig(ctypes.Structure):
+    _fields_ = [("n_iter", c_int32), ("n_equil", c_int32), ("n_resample", c_int32), ("reserved", c_int32),
+                ("step", c_double), ("seed", c_uint64), ("lr", c_double), ("beta1", c_double), ("beta2", c_double),
+                ("eps", c_double), ("mask", c_void_p)]
 
 
 class QmcError(RuntimeError):
@@ -114,6 +120,11 @@ def load(path: str = LIB_PATH):
     lib.qmc_set_timing.restype = c_int32
     lib.qmc_set_det_method.argtypes = [c_void_p, c_int32]
     lib.qmc_set_det_method.restype = c_int32
+    lib.qmc_optimize.argtypes = [c_void_p, c_void_p, c_int64, c_int64, POINTER(OptConfig), c_void_p, c_void_p]
+    lib.qmc_optimize.restype = c_int32
+    lib.qmc_force_batches.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32, c_void_p, c_void_p,
+                                      c_void_p]
+    lib.qmc_force_batches.restype = c_int32
     lib.qmc_last_stage_ms.argtypes = [c_void_p, POINTER(ctypes.c_float), c_int32]
     lib.qmc_last_stage_ms.restype = c_int32
     lib.qmc_server_create.argtypes = [c_int32, c_size_t, c_int32, POINTER(c_void_p)]

@@ -36,6 +36,12 @@ qmc_status cuda_fail(cudaError_t e, const char* where) {
   return QMC_ERR_CUDA;
 }
 
+}  // namespace
+
+qmc_status set_error(qmc_status s, const std::string& msg) { return fail(s, msg); }
+
+namespace {
+
 double dfact(int n) {
   double r = 1.0;
   while (n > 1) { r *= n; n -= 2; }

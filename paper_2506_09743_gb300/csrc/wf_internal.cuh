@@ -3,6 +3,7 @@
 #pragma once
 
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "qmc_internal.cuh"
@@ -23,6 +24,9 @@ struct DeviceGuard {
 };
 
 }  // namespace qmc
+
+// Records msg as the calling thread's qmc_last_error() text and returns s.
+qmc_status set_error(qmc_status s, const std::string& msg);
 
 // Host copy of the inputs of qmc_create_wf (parameters are updated in place by
 // qmc_set_params, geometry by qmc_set_geometry; the device tables are rebuilt
