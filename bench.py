@@ -241,6 +241,13 @@ def run_secondary(device, stream, barrier, flush):
                 out["li2_energy_grad_note"] = ("131,072 walkers: E_L, mean/variance, gradient of 83 parameters "
                                                "and forces on both nuclei, host-timed (synchronous call)")
             wf.close()
+    # several determinants with backflow: Li2, SD(6e, 6o) = 118 determinants
+    mol = qi.make_li2(n_mo=6, n_det=118)
+    W = qi.WORKLOAD_WALKERS["li2"]
+    x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
+    wf = Wavefunction(mol, precision="fp64", device=device)
+    out["li2_sd118_backflow_fp64_walker_evals_per_s"] = rate(wf, x, W, steps=3)
+    wf.close()
     # one optimisation step of App. B (10^4 walkers: Eq. nabla_loss gradient, ADAM
     # update, 500 Metropolis resampling steps), host-timed through qmc_optimize
     for name in ("lih", "li2"):

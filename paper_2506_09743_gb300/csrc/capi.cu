@@ -197,11 +197,8 @@ qmc_status build_tables(qmc_wf* wf) {
     d.atom_z[a] = h.z[a];
   }
   d.vnn = vnn_of(d);
-  if (h.w != 0.0) {
-    if (prec != QMC_FP64) return fail(QMC_ERR_UNSUPPORTED, "backflow wavefunctions run in the FP64 form only");
-    if (!general_supported(d))
-      return fail(QMC_ERR_UNSUPPORTED, "backflow needs one determinant, <= 8 electrons, <= 4 per spin");
-  }
+  if (h.w != 0.0 && prec != QMC_FP64)
+    return fail(QMC_ERR_UNSUPPORTED, "backflow wavefunctions run in the FP64 form only");
 
   // ---- basis: shells, normalisation, angular factors
   std::vector<ShellDev> shells;
@@ -376,6 +373,9 @@ qmc_status build_tables(qmc_wf* wf) {
     d.nv[s] = p_hi - ns;
   }
   d.tab_elems = 2 * (d.nh[0] * d.nv[0] + d.nh[1] * d.nv[1]);
+  if (h.w != 0.0 && !general_supported(d) && !bf_multidet_supported(d))
+    return fail(QMC_ERR_UNSUPPORTED,
+                "backflow needs <= 8 electrons, <= 4 per spin and (several determinants) <= 8 orbital columns");
   if (det_smem_bytes(d, std::max(nup, ndn), det_team_size(d), true) > 227 * 1024)
     return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
 

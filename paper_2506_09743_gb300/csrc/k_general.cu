@@ -209,20 +209,16 @@ __device__ void backflow_rows(const double (&r)[NE][3], const Pairs<NE>& P, int 
   }
 }
 
-}  // namespace
-
-// Local energy and log|Psi| of one walker.  T = double, or Dual<K> with the
-// nuclear coordinates R seeded for forces.  NE >= n_elec, NO >= occupied
-// orbitals per spin.
-template <typename T, int NE, int NO>
-__device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&r)[NE][3], const T (*R)[3],
-                            bool kinetic, T& eloc, T& logpsi) {
+// Pade Jastrow (Eq. pade_kernel) on the original coordinates: J, lap J
+// summed over electrons, grad_i J; and the Coulomb potential V (Eq. Hmol)
+// with nuclei at R.
+template <typename T, int NE>
+__device__ void jastrow_coulomb(const WfDev& wf, const double (&r)[NE][3], const T (*R)[3], const Pairs<NE>& P,
+                                double& J, double& lapJ, double (&gJ)[NE][3], T& V) {
   const int N = wf.n_elec, nu = wf.n_up;
-  const double w = wf.bf_w;
-  Pairs<NE> P;
-  pair_geometry<NE>(r, N, P);
-  // Jastrow (original coordinates) and electron-electron repulsion
-  double J = 0.0, lapJ = 0.0, Vee = 0.0, gJ[NE][3];
+  double Vee = 0.0;
+  J = 0.0;
+  lapJ = 0.0;
   for (int i = 0; i < NE; ++i)
     for (int d = 0; d < 3; ++d) gJ[i][d] = 0.0;
   for (int i = 0; i < N; ++i)
@@ -240,17 +236,7 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
         gJ[j][d] -= s;
       }
     }
-  // backflow positions
-  double rt[NE][3];
-  for (int i = 0; i < N; ++i)
-    for (int d = 0; d < 3; ++d) {
-      double acc = r[i][d];
-      for (int j = 0; j < N; ++j)
-        if (j != i) acc += w * P.inv[i][j] * (r[i][d] - r[j][d]);
-      rt[i][d] = acc;
-    }
-  // Coulomb terms that depend on the nuclei
-  T V = T(Vee);
+  V = T(Vee);
   for (int a = 0; a < wf.n_atom; ++a) {
     for (int i = 0; i < N; ++i) {
       const T dx = r[i][0] - R[a][0], dy = r[i][1] - R[a][1], dz = r[i][2] - R[a][2];
@@ -261,6 +247,37 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
       V += wf.atom_z[a] * wf.atom_z[b] / sqrt(dx * dx + dy * dy + dz * dz);
     }
   }
+}
+
+// backflow positions r~_i = r_i + sum_{j != i} (w / r_ij)(r_i - r_j)
+template <int NE>
+__device__ void backflow_positions(const double (&r)[NE][3], const Pairs<NE>& P, int N, double w,
+                                   double (&rt)[NE][3]) {
+  for (int i = 0; i < N; ++i)
+    for (int d = 0; d < 3; ++d) {
+      double acc = r[i][d];
+      for (int j = 0; j < N; ++j)
+        if (j != i) acc += w * P.inv[i][j] * (r[i][d] - r[j][d]);
+      rt[i][d] = acc;
+    }
+}
+
+}  // namespace
+
+// Local energy and log|Psi| of one walker.  T = double, or Dual<K> with the
+// nuclear coordinates R seeded for forces.  NE >= n_elec, NO >= occupied
+// orbitals per spin.
+template <typename T, int NE, int NO>
+__device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&r)[NE][3], const T (*R)[3],
+                            bool kinetic, T& eloc, T& logpsi) {
+  const int N = wf.n_elec, nu = wf.n_up;
+  const double w = wf.bf_w;
+  Pairs<NE> P;
+  pair_geometry<NE>(r, N, P);
+  double J, lapJ, gJ[NE][3], rt[NE][3];
+  T V;
+  jastrow_coulomb<T, NE>(wf, r, R, P, J, lapJ, gJ, V);
+  backflow_positions<NE>(r, P, N, w, rt);
   // orbitals at the backflow positions
   const int n_occ = nu > wf.n_down ? nu : wf.n_down;
   T phi[NE][NO], dphi[NE][NO][3], hphi[NE][NO][6];
@@ -333,6 +350,167 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
   eloc = -0.5 * kin + V;
 }
 
+// Multi-determinant local energy with backflow (FP64).  Every coordinate
+// x_k moves every row of both spins' matrices, so per coordinate and spin the
+// excited determinants' first and second log-derivatives come from tables of
+// the reference inverse (Eq. table for Tr(A_X^-1 d A_X) and
+// Tr(A_X^-1 d^2 A_X), Eq. table_squared for Tr((A_X^-1 d A_X)^2); App. F, H).
+// With t_p = A0^-1 Phi_p, X1 = A0^-1 dA, X2 = A0^-1 d^2A (all columns) and
+//   m1_p = X1[:, p] - X1[:, occ] t_p,  m2_p likewise from X2,  y_p = X1[:, occ] m1_p,
+// an excitation X (holes h_a, particles p_b) has S_ab = t_{p_b}[h_a],
+// (PMP)_ab = m1_{p_b}[h_a], (PYP)_ab = y_{p_b}[h_a], (PM2P)_ab = m2_{p_b}[h_a]
+// and, with R = det S and adj S its adjugate (k = 1, 2), division-free:
+//   R d D_X/D_X   = R tr1 + Tr(adj S PMP)
+//   R d^2 D_X/D_X = R (tr2 + tr1^2 - trsq) + Tr(adj S PM2P) + 2 tr1 Tr(adj S PMP)
+//                   + 2 det(PMP) - 2 Tr(adj S PYP)
+// (Eq. nabla_d; for k = 2 the terms (Tr Z)^2 - Tr(Z^2) = 2 det Z of
+// Z = S^-1 PMP collapse to 2 det(PMP) / R; for k = 1 they cancel), where
+// tr1 = Tr X1_occ, trsq = Tr(X1_occ^2), tr2 = Tr X2_occ.  Then
+// Eqs. nabla_sigma / delta_sigma with the up-down cross term.
+template <int NE, int NC>
+__device__ void eval_walker_md(const WfDev& wf, const GenShared& g, const double (&r)[NE][3], bool kinetic,
+                               double& eloc, double& logpsi) {
+  constexpr int NS = 4;  // occupied orbitals per spin
+  const int N = wf.n_elec, nu = wf.n_up;
+  const double w = wf.bf_w;
+  Pairs<NE> P;
+  pair_geometry<NE>(r, N, P);
+  double J, lapJ, gJ[NE][3], rt[NE][3], V;
+  jastrow_coulomb<double, NE>(wf, r, wf.atom_xyz, P, J, lapJ, gJ, V);
+  backflow_positions<NE>(r, P, N, w, rt);
+  const int ncol = wf.p_hi[0] > wf.p_hi[1] ? wf.p_hi[0] : wf.p_hi[1];
+  double phi[NE][NC], dphi[NE][NC][3], hphi[NE][NC][6];
+  for (int i = 0; i < N; ++i) mo_channels<double, NC>(wf, g, rt[i], wf.atom_xyz, ncol, phi[i], dphi[i], hphi[i], kinetic);
+  // reference inverses and the value tables t_p
+  double ainv[2][NS][NS], tv[2][NS][NC], det0 = 1.0;
+  for (int s = 0; s < 2; ++s) {
+    const int n = s == 0 ? nu : wf.n_down, i0 = s == 0 ? 0 : nu;
+    if (n == 0) continue;
+    for (int a = 0; a < n; ++a)
+      for (int m = 0; m < n; ++m) ainv[s][a][m] = phi[i0 + a][m];
+    det0 *= small_inverse<double, NS>(ainv[s], n);
+    for (int m = 0; m < n; ++m)
+      for (int c = n; c < wf.p_hi[s]; ++c) {
+        double acc = 0.0;
+        for (int a = 0; a < n; ++a) acc += ainv[s][m][a] * phi[i0 + a][c];
+        tv[s][m][c] = acc;
+      }
+  }
+  // determinant ratios R_s of every determinant (coordinate independent)
+  auto ratio = [&](int s, const int* e) -> double {
+    if (e[0] == 0) return 1.0;
+    if (e[0] == 1) return tv[s][e[1]][e[3]];
+    return tv[s][e[1]][e[3]] * tv[s][e[2]][e[4]] - tv[s][e[1]][e[4]] * tv[s][e[2]][e[3]];
+  };
+  double sum_r = 0.0;
+  for (int d = 0; d < wf.n_det; ++d) {
+    const int* eu = wf.exc + (0 * kMaxExc + wf.det_idx[2 * d]) * 5;
+    const int* ed = wf.exc + (1 * kMaxExc + wf.det_idx[2 * d + 1]) * 5;
+    sum_r += wf.det_w[d] * ratio(0, eu) * ratio(1, ed);
+  }
+  logpsi = J + log(fabs(det0 * sum_r));
+  if (!kinetic) return;
+  double kin = lapJ;
+  for (int kk = 0; kk < N; ++kk)
+    for (int e = 0; e < 3; ++e) {
+      double tr1[2] = {0.0, 0.0}, trsq[2] = {0.0, 0.0}, tr2[2] = {0.0, 0.0};
+      double pm1[2][NS][NC], py[2][NS][NC], pm2[2][NS][NC];
+      for (int s = 0; s < 2; ++s) {
+        const int n = s == 0 ? nu : wf.n_down, i0 = s == 0 ? 0 : nu;
+        if (n == 0) continue;
+        double dA[NS][NC], d2A[NS][NC];
+        for (int a = 0; a < n; ++a) {
+          const int i = i0 + a;
+          double j1[3], j2[3];
+          backflow_rows<NE>(r, P, N, w, i, kk, e, j1, j2);
+          for (int c = 0; c < wf.p_hi[s]; ++c) {
+            double v1 = 0.0, v2 = 0.0;
+            for (int dd = 0; dd < 3; ++dd) {
+              v1 += j1[dd] * dphi[i][c][dd];
+              v2 += j2[dd] * dphi[i][c][dd];
+              for (int f = 0; f < 3; ++f) v2 += (j1[dd] * j1[f]) * hphi[i][c][hidx(dd, f)];
+            }
+            dA[a][c] = v1;
+            d2A[a][c] = v2;
+          }
+        }
+        double X1[NS][NC], X2[NS][NC];
+        for (int m = 0; m < n; ++m)
+          for (int c = 0; c < wf.p_hi[s]; ++c) {
+            double a1 = 0.0, a2 = 0.0;
+            for (int a = 0; a < n; ++a) {
+              a1 += ainv[s][m][a] * dA[a][c];
+              a2 += ainv[s][m][a] * d2A[a][c];
+            }
+            X1[m][c] = a1;
+            X2[m][c] = a2;
+          }
+        for (int m = 0; m < n; ++m) {
+          tr1[s] += X1[m][m];
+          tr2[s] += X2[m][m];
+          for (int q = 0; q < n; ++q) trsq[s] += X1[m][q] * X1[q][m];
+        }
+        for (int c = n; c < wf.p_hi[s]; ++c) {
+          double m1[NS];
+          for (int m = 0; m < n; ++m) {
+            double a1 = X1[m][c], a2 = X2[m][c];
+            for (int q = 0; q < n; ++q) {
+              a1 -= X1[m][q] * tv[s][q][c];
+              a2 -= X2[m][q] * tv[s][q][c];
+            }
+            m1[m] = a1;
+            pm1[s][m][c] = a1;
+            pm2[s][m][c] = a2;
+          }
+          for (int m = 0; m < n; ++m) {
+            double acc = 0.0;
+            for (int q = 0; q < n; ++q) acc += X1[m][q] * m1[q];
+            py[s][m][c] = acc;
+          }
+        }
+      }
+      // R, R dD/D and R d^2D/D of one spin excitation
+      auto terms = [&](int s, const int* e, double& R, double& RG, double& RB) {
+        const double base = tr2[s] + tr1[s] * tr1[s] - trsq[s];
+        if (e[0] == 0) {
+          R = 1.0;
+          RG = tr1[s];
+          RB = base;
+        } else if (e[0] == 1) {
+          const int h = e[1], p = e[3];
+          R = tv[s][h][p];
+          const double q1 = pm1[s][h][p];
+          RG = R * tr1[s] + q1;
+          RB = R * base + pm2[s][h][p] + 2.0 * (tr1[s] * q1 - py[s][h][p]);
+        } else {
+          const int h1 = e[1], h2 = e[2], p1 = e[3], p2 = e[4];
+          const double s00 = tv[s][h1][p1], s01 = tv[s][h1][p2], s10 = tv[s][h2][p1], s11 = tv[s][h2][p2];
+          R = s00 * s11 - s01 * s10;
+          auto adj_tr = [&](const double (*Q)[NC]) {
+            return s11 * Q[h1][p1] - s01 * Q[h2][p1] - s10 * Q[h1][p2] + s00 * Q[h2][p2];
+          };
+          const double t1 = adj_tr(pm1[s]);
+          const double detq = pm1[s][h1][p1] * pm1[s][h2][p2] - pm1[s][h1][p2] * pm1[s][h2][p1];
+          RG = R * tr1[s] + t1;
+          RB = R * base + adj_tr(pm2[s]) + 2.0 * tr1[s] * t1 + 2.0 * detq - 2.0 * adj_tr(py[s]);
+        }
+      };
+      double acc_g = 0.0, acc_b = 0.0;
+      for (int d = 0; d < wf.n_det; ++d) {
+        double R0, G0, B0, R1, G1, B1;
+        terms(0, wf.exc + (0 * kMaxExc + wf.det_idx[2 * d]) * 5, R0, G0, B0);
+        terms(1, wf.exc + (1 * kMaxExc + wf.det_idx[2 * d + 1]) * 5, R1, G1, B1);
+        const double dw = wf.det_w[d];
+        acc_g += dw * (G0 * R1 + R0 * G1);
+        acc_b += dw * (B0 * R1 + 2.0 * G0 * G1 + R0 * B1);
+      }
+      const double dS = acc_g / sum_r, d2S = acc_b / sum_r;
+      const double gj = gJ[kk][e];
+      kin += gj * gj + 2.0 * gj * dS + d2S;
+    }
+  eloc = -0.5 * kin + V;
+}
+
 // ----------------------------------------------------------------------------
 // kernels
 
@@ -352,6 +530,23 @@ __device__ void stage_tables(const WfDev& wf, GenShared& g, unsigned char* smem)
   g.sh = sh;
   g.pw = pw;
   g.C = wf.mo64;
+}
+
+template <int NE, int NC>
+__global__ void __launch_bounds__(128) k_eloc_md(WfDev wf, const double* __restrict__ walkers, int64_t W, int64_t ldw,
+                                                 bool kinetic, double* __restrict__ e_loc,
+                                                 double* __restrict__ log_psi) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  GenShared g;
+  stage_tables(wf, g, smem_raw);
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  double r[NE][3];
+  load_walker<NE>(walkers, ldw, w, wf.n_elec, r);
+  double e = 0.0, lp = 0.0;
+  eval_walker_md<NE, NC>(wf, g, r, kinetic, e, lp);
+  if (kinetic) e_loc[w] = e;
+  if (log_psi) log_psi[w] = lp;
 }
 
 template <int NE, int NO>
@@ -585,11 +780,24 @@ bool general_supported(const WfDev& wf) {
   return wf.n_det == 1 && wf.n_elec <= 8 && ns <= 4;
 }
 
+bool bf_multidet_supported(const WfDev& wf) {
+  const int ns = wf.n_up > wf.n_down ? wf.n_up : wf.n_down;
+  const int nc = wf.p_hi[0] > wf.p_hi[1] ? wf.p_hi[0] : wf.p_hi[1];
+  return wf.n_elec <= 8 && ns <= 4 && nc <= 8;
+}
+
 cudaError_t launch_eloc_general(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, bool kinetic,
                                 double* e_loc, double* log_psi, cudaStream_t st) {
   if (W == 0) return cudaSuccess;
   const size_t smem = gen_table_bytes(wf);
   const dim3 grid((unsigned)((W + 127) / 128));
+  if (wf.n_det > 1) {
+    if (!bf_multidet_supported(wf)) return cudaErrorInvalidValue;
+    if (wf.n_elec <= 2) k_eloc_md<2, 8><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
+    else if (wf.n_elec <= 4) k_eloc_md<4, 8><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
+    else k_eloc_md<8, 8><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
+    return cudaGetLastError();
+  }
   QMC_GEN_DISPATCH((k_eloc_general<NE, NO><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi)));
   return cudaGetLastError();
 }

@@ -183,6 +183,8 @@ cudaError_t launch_sum_counts(const int64_t* counts, int64_t W, double* out, cud
 
 // general single-determinant FP64 path (backflow, forces, parameter gradient)
 bool general_supported(const WfDev& wf);
+// backflow with several determinants: <= 8 electrons, <= 4 per spin, <= 8 orbital columns
+bool bf_multidet_supported(const WfDev& wf);
 int general_blocks(int64_t W);
 size_t grad_smem_bytes(const WfDev& wf, int n_param);
 cudaError_t launch_eloc_general(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, bool kinetic,

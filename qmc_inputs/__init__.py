@@ -305,7 +305,9 @@ def make_lih(bond: float = 3.015) -> Molecule:
     )
 
 
-def make_li2(bond: float = 5.05, backflow_w: float = 0.1, n_mo: int = 3) -> Molecule:
+def make_li2(bond: float = 5.05, backflow_w: float = 0.1, n_mo: int = 3, n_det: int = 1) -> Molecule:
+    """Li2 with backflow; n_det > 1 draws the ground state plus n_det - 1
+    excitations of SD(6, n_mo) (all orbitals active)."""
     rng = np.random.default_rng(SEED_EXPONENTS)
     bb = _BasisBuilder()
     _sto_dz_li_like(bb, 0, rng)
@@ -313,9 +315,14 @@ def make_li2(bond: float = 5.05, backflow_w: float = 0.1, n_mo: int = 3) -> Mole
     xyz = np.array([[0.0, 0.0, -bond / 2], [0.0, 0.0, bond / 2]])
     z = np.array([3.0, 3.0])
     mo = random_orthonormal(20, n_mo, np.random.default_rng(SEED_MO))
+    if n_det == 1:
+        dets = [(ground_exc(), ground_exc())]
+    else:
+        all_dets = sd_expansion(3, 3, n_mo)
+        dets = _select_dets(all_dets, n_det, np.random.default_rng(SEED_DETS)) if n_det < len(all_dets) else all_dets
     return Molecule(
-        name="li2", atom_xyz=xyz, atom_z=z, n_up=3, n_down=3, **bb.arrays(), mo_coeff=mo,
-        det_weight=np.ones(1), det_exc=_dets_array([(ground_exc(), ground_exc())]),
+        name="li2" if n_det == 1 else "li2_md", atom_xyz=xyz, atom_z=z, n_up=3, n_down=3, **bb.arrays(),
+        mo_coeff=mo, det_weight=_ci_weights(len(dets), np.random.default_rng(SEED_CI)), det_exc=_dets_array(dets),
         jastrow_b=1.0, backflow_w=backflow_w, electron_home=electron_homes(z, 3, 3),
     )
 

@@ -39,6 +39,38 @@ def test_li2_backflow_local_energy_parity(pkg):
     print("li2 backflow fp64", st)
 
 
+@pytest.mark.parametrize("n_det", [5, 20, 118])
+def test_multidet_backflow_local_energy_parity(pkg, n_det):
+    """Several determinants with backflow: excited determinants from tables of
+    the reference inverse per coordinate (Eqs. table, table_squared), against
+    the oracle's explicit per-determinant Eq. nabla_d."""
+    mol = qi.make_li2(n_mo=6, n_det=n_det)
+    r = qi.walkers(mol, 300, seed=42)
+    E_ref, lp_ref, sens = oracle_reference(mol, r)
+    wf = pkg.Wavefunction(mol, precision="fp64")
+    e, lp = wf.local_energy(_x(r))
+    torch.cuda.synchronize()
+    st = fp64_check(e.cpu().numpy(), E_ref, sens, min_within=0.98)
+    scale = np.maximum(1.0, np.abs(lp_ref))
+    assert np.all(np.abs(lp.cpu().numpy() - lp_ref) <= 128 * 2.0 ** -53 * sens * scale)
+    print(f"li2 backflow {n_det} dets fp64", st)
+
+
+def test_multidet_backflow_chain_matches_oracle(pkg):
+    mol = qi.make_li2(n_mo=6, n_det=20)
+    r0 = qi.walkers(mol, 64, seed=48)
+    r_ref, _, acc_ref = O.metropolis(O.Wavefunction(mol), torch.tensor(r0), 10, 0.1, seed=6)
+    wf = pkg.Wavefunction(mol)
+    x = _x(r0)
+    acc = torch.zeros(64, dtype=torch.int64, device="cuda")
+    wf.sample(x, n_steps=10, step=0.1, seed=6, n_accept=acc)
+    torch.cuda.synchronize()
+    same = acc.cpu().numpy() == acc_ref.numpy()
+    assert same.mean() >= 0.98
+    r_gpu = qi.from_soa(x.cpu().numpy(), 64, mol.n_elec)
+    assert np.abs(r_gpu - r_ref.numpy()).max(axis=(1, 2))[same].max() < 1e-9
+
+
 def test_backflow_rejected_outside_its_scope(pkg):
     from paper_2506_09743_gb300 import QmcError
 
@@ -48,6 +80,11 @@ def test_backflow_rejected_outside_its_scope(pkg):
     mol.backflow_w = 0.1
     with pytest.raises(QmcError):
         pkg.Wavefunction(mol, precision="fp64")
+    # gradients and forces are single-determinant only
+    wf = pkg.Wavefunction(qi.make_li2(n_mo=6, n_det=5), precision="fp64")
+    with pytest.raises(QmcError):
+        wf.energy_grad(_x(qi.walkers(qi.make_li2(), 16, seed=1)))
+    wf.close()
 
 
 def _oracle_energy_grad(mol, r):

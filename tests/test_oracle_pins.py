@@ -171,12 +171,14 @@ def test_nuclear_repulsion_closed_form():
 # kinetic energy: trace formulas against brute-force differentiation
 
 
-@pytest.mark.parametrize("name", ["h2", "lih", "co_small", "li2", "li2_multidet"])
+@pytest.mark.parametrize("name", ["h2", "lih", "co_small", "li2", "li2_multidet", "li2_sd20"])
 def test_local_energy_matches_autograd_laplacian(name):
     if name == "co_small":
         mol = qi.make_co(n_det=8)
     elif name == "li2_multidet":
         mol = _li2_multidet()
+    elif name == "li2_sd20":
+        mol = qi.make_li2(n_mo=6, n_det=20)
     else:
         mol = qi.make_molecule(name)
     wf = O.Wavefunction(mol)
