@@ -83,6 +83,11 @@ class Wavefunction:
         self.w0_par = float(mol.jastrow_w0_par)
         self.w0_anti = float(mol.jastrow_w0_anti)
         self.jastrow_b = torch.tensor(float(mol.jastrow_b), dtype=DT)
+        # many-body Jastrow (App. D); None when absent
+        jen = getattr(mol, "jastrow_en", None)
+        jeen = getattr(mol, "jastrow_een", None)
+        self.jastrow_en = None if jen is None else torch.tensor(np.asarray(jen, dtype=np.float64))
+        self.jastrow_een = None if jeen is None else torch.tensor(np.asarray(jeen, dtype=np.float64))
         self.backflow_w = torch.tensor(float(mol.backflow_w), dtype=DT)
         if requires_grad:
             for t in self.params().values():
@@ -289,7 +294,10 @@ def jastrow(wf, r):
     grad_i J = sum_j u'(r_ij) r_ij_vec / r_ij,  lap_i J = sum_j u'' + 2u'/r_ij.
     """
     W, N, _ = r.shape
+    manybody = wf.jastrow_en is not None or wf.jastrow_een is not None
     if N < 2:
+        if manybody:
+            return jastrow_manybody(wf, r)
         z = torch.zeros(W, dtype=DT)
         return z, torch.zeros(W, N, 3, dtype=DT), torch.zeros(W, N, dtype=DT)
     b = wf.jastrow_b
@@ -304,7 +312,85 @@ def jastrow(wf, r):
     J = 0.5 * u.sum((1, 2))
     gJ = ((u1 / dist)[..., None] * rij).sum(2)
     lJ = (u2 + 2.0 * u1 / dist).sum(2)
+    if manybody:
+        Jm, gm, lm = jastrow_manybody(wf, r)
+        J, gJ, lJ = J + Jm, gJ + gm, lJ + lm
     return J, gJ, lJ
+
+
+def _rational(a, b, x):
+    """f = a x / (1 + b x), f' = a / (1 + b x)^2, f'' = -2 a b / (1 + b x)^3."""
+    d = 1.0 + b * x
+    return a * x / d, a / d ** 2, -2.0 * a * b / d ** 3
+
+
+def jastrow_manybody(wf, r):
+    """Many-body Jastrow terms of App. D with their electron derivatives.
+
+    Electron-nucleus: K_en(r) = (w0 r + w1 r^2) / (1 + w2 r) summed over atoms
+    alpha and electrons i, with r = r_alpha_i;
+      K' = (w0 + 2 w1 r + w1 w2 r^2) / (1 + w2 r)^2,  K'' = 2 (w1 - w0 w2) / (1 + w2 r)^3.
+    Electron-electron-nucleus: K_een(x, y, z) = sum_mu c_mu f(a1, b1; x)
+    f(a2, b2; y) f(a3, b3; z), f(a, b; r) = a r / (1 + b r), with x = r_alpha_i,
+    y = r_alpha_j, z = r_ij, summed over atoms and ordered pairs i != j with
+    a factor 1/2 (the kernel symmetrised in i and j, so that J is symmetric
+    under electron exchange).  Per electron i the gradient and Laplacian
+    follow from the chain rule through x, y, z:
+      grad_i = sum K_x u_ai + K_z u_ij,
+      lap_i  = sum K_xx + 2 K_x / x + K_zz + 2 K_z / z + 2 K_xz (u_ai . u_ij)
+    (and the mirror terms for i in the second slot).  Returns J [W],
+    grad J [W, N, 3], lap_i J [W, N].
+    """
+    W, N, _ = r.shape
+    J = torch.zeros(W, dtype=DT)
+    g = torch.zeros(W, N, 3, dtype=DT)
+    lap = torch.zeros(W, N, dtype=DT)
+    n_atom = wf.atom_xyz.shape[0]
+    ria = r[:, :, None, :] - wf.atom_xyz[None, None, :, :]  # [W, N, A, 3]
+    dia = torch.sqrt((ria * ria).sum(-1))  # [W, N, A]
+    uia = ria / dia[..., None]
+    if wf.jastrow_en is not None:
+        w0, w1, w2 = wf.jastrow_en[0], wf.jastrow_en[1], wf.jastrow_en[2]
+        d = 1.0 + w2 * dia
+        K = (w0 * dia + w1 * dia * dia) / d
+        K1 = (w0 + 2.0 * w1 * dia + w1 * w2 * dia * dia) / d ** 2
+        K2 = 2.0 * (w1 - w0 * w2) / d ** 3
+        J = J + K.sum((1, 2))
+        g = g + (K1[..., None] * uia).sum(2)
+        lap = lap + (K2 + 2.0 * K1 / dia).sum(2)
+    if wf.jastrow_een is not None and N >= 2:
+        rij = r[:, :, None, :] - r[:, None, :, :]
+        dij = torch.sqrt((rij * rij).sum(-1) + torch.eye(N, dtype=DT))
+        uij = rij / dij[..., None]
+        for a in range(n_atom):
+            for i in range(N):
+                for j in range(N):
+                    if i == j:
+                        continue
+                    x, y, z = dia[:, i, a], dia[:, j, a], dij[:, i, j]
+                    K = Kx = Ky = Kz = Kxx = Kyy = Kzz = Kxz = Kyz = 0.0
+                    for c, a1, b1, a2, b2, a3, b3 in wf.jastrow_een:
+                        f1, f1p, f1pp = _rational(a1, b1, x)
+                        f2, f2p, f2pp = _rational(a2, b2, y)
+                        f3, f3p, f3pp = _rational(a3, b3, z)
+                        K = K + c * f1 * f2 * f3
+                        Kx = Kx + c * f1p * f2 * f3
+                        Ky = Ky + c * f1 * f2p * f3
+                        Kz = Kz + c * f1 * f2 * f3p
+                        Kxx = Kxx + c * f1pp * f2 * f3
+                        Kyy = Kyy + c * f1 * f2pp * f3
+                        Kzz = Kzz + c * f1 * f2 * f3pp
+                        Kxz = Kxz + c * f1p * f2 * f3p
+                        Kyz = Kyz + c * f1 * f2p * f3p
+                    ui, uj, u = uia[:, i, a], uia[:, j, a], uij[:, i, j]
+                    J = J + 0.5 * K
+                    g[:, i] = g[:, i] + 0.5 * (Kx[:, None] * ui + Kz[:, None] * u)
+                    g[:, j] = g[:, j] + 0.5 * (Ky[:, None] * uj - Kz[:, None] * u)
+                    lap[:, i] = lap[:, i] + 0.5 * (Kxx + 2.0 * Kx / x + Kzz + 2.0 * Kz / z
+                                                   + 2.0 * Kxz * (ui * u).sum(-1))
+                    lap[:, j] = lap[:, j] + 0.5 * (Kyy + 2.0 * Ky / y + Kzz + 2.0 * Kz / z
+                                                   - 2.0 * Kyz * (uj * u).sum(-1))
+    return J, g, lap
 
 
 # ---------------------------------------------------------------------------

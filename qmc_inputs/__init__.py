@@ -73,6 +73,11 @@ class Molecule:
     jastrow_w0_anti: float = 0.5
     jastrow_b: float = 1.0
     backflow_w: float = 0.0
+    # many-body Jastrow (App. D): electron-nucleus kernel (w0, w1, w2) and
+    # electron-electron-nucleus terms [n_terms, 7] = (c, a1, b1, a2, b2, a3, b3);
+    # None = absent
+    jastrow_en: np.ndarray | None = None
+    jastrow_een: np.ndarray | None = None
     # electron -> home atom used to draw initial walker positions
     electron_home: np.ndarray | None = None
 
@@ -376,6 +381,21 @@ MOLECULES = {"h2": make_h2, "lih": make_lih, "li2": make_li2, "co": make_co}
 
 # walker counts of the four workloads
 WORKLOAD_WALKERS = {"h2": 1024, "lih": 65536, "li2": 131072, "co": 262144}
+
+
+def with_manybody_jastrow(mol: Molecule, n_terms: int = 5, seed: int = 9, en: bool = True) -> Molecule:
+    """The molecule with seeded many-body Jastrow parameters (App. D: K_en and
+    n_terms electron-electron-nucleus terms).  w0 ~ U(-0.3, -0.1), w1 ~ U(0,
+    0.05), w2 ~ U(0.5, 1.5); c ~ N(0, 0.1), a ~ U(0.2, 1), b ~ U(0.5, 2)."""
+    rng = np.random.default_rng(seed)
+    jen = np.array([rng.uniform(-0.3, -0.1), rng.uniform(0.0, 0.05), rng.uniform(0.5, 1.5)]) if en else None
+    een = None
+    if n_terms > 0:
+        een = np.empty((n_terms, 7))
+        een[:, 0] = 0.1 * rng.standard_normal(n_terms)
+        een[:, 1::2] = rng.uniform(0.2, 1.0, size=(n_terms, 3))
+        een[:, 2::2] = rng.uniform(0.5, 2.0, size=(n_terms, 3))
+    return dataclasses.replace(mol, name=mol.name + "_mbj", jastrow_en=jen, jastrow_een=een)
 
 
 def make_molecule(name: str, **kw) -> Molecule:

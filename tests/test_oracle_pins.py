@@ -140,6 +140,39 @@ def test_hydrogen_atom_exact_1s():
     assert E.var().item() < 1e-26
 
 
+def test_hydrogen_with_electron_nucleus_kernel_closed_form():
+    """One electron in the exact 1s orbital times exp(K_en(r)): with
+    Psi = exp(K(r) - r), lap Psi / Psi = (K' - 1)^2 + K'' + 2 (K' - 1) / r, so
+    E_L = -1/2 [(K' - 1)^2 + K'' + 2 (K' - 1)/r] - 1/r, with K' and K'' of
+    K(r) = (w0 r + w1 r^2)/(1 + w2 r) differentiated by hand."""
+    import dataclasses
+
+    w0, w1, w2 = -0.2, 0.03, 0.8
+    mol = dataclasses.replace(qi.make_hydrogenic(1.0, 1.0), jastrow_en=np.array([w0, w1, w2]))
+    wf = O.Wavefunction(mol)
+    r = _walkers(mol, 64)
+    x = torch.sqrt((r[:, 0] ** 2).sum(-1))
+    d = 1 + w2 * x
+    K1 = (w0 + w1 * x * (2 + w2 * x)) / d ** 2
+    K2 = 2 * (w1 - w0 * w2) / d ** 3
+    ref = -0.5 * ((K1 - 1) ** 2 + K2 + 2 * (K1 - 1) / x) - 1 / x
+    assert _rel(O.local_energy(wf, r), ref) < 1e-12
+
+
+def test_electron_electron_nucleus_kernel_is_exchange_symmetric():
+    """The many-body terms are spin independent and symmetric under the
+    exchange of any two electrons (the kernel is summed over ordered pairs),
+    although each of its terms is not."""
+    mol = qi.with_manybody_jastrow(qi.make_lih(), en=False)
+    wf = O.Wavefunction(mol)
+    r = _walkers(mol, 8)
+    J0 = O.jastrow_manybody(wf, r)[0]
+    for i, j in ((0, 1), (0, 2), (1, 3)):
+        rs = r.clone()
+        rs[:, [i, j]] = r[:, [j, i]]
+        assert torch.allclose(O.jastrow_manybody(wf, rs)[0], J0, atol=1e-13, rtol=0)
+
+
 @pytest.mark.parametrize("zeta,Z", [(1.3, 1.0), (0.7, 2.0), (2.5, 3.0)])
 def test_hydrogenic_closed_form(zeta, Z):
     mol = qi.make_hydrogenic(zeta, Z)
@@ -171,10 +204,14 @@ def test_nuclear_repulsion_closed_form():
 # kinetic energy: trace formulas against brute-force differentiation
 
 
-@pytest.mark.parametrize("name", ["h2", "lih", "co_small", "li2", "li2_multidet", "li2_sd20"])
+@pytest.mark.parametrize("name", ["h2", "lih", "co_small", "li2", "li2_multidet", "li2_sd20", "lih_mbj", "co_mbj"])
 def test_local_energy_matches_autograd_laplacian(name):
     if name == "co_small":
         mol = qi.make_co(n_det=8)
+    elif name == "lih_mbj":
+        mol = qi.with_manybody_jastrow(qi.make_lih())
+    elif name == "co_mbj":
+        mol = qi.with_manybody_jastrow(qi.make_co(n_det=8))
     elif name == "li2_multidet":
         mol = _li2_multidet()
     elif name == "li2_sd20":
@@ -226,8 +263,10 @@ def test_backflow_jacobian_finite_difference():
             assert _rel(J2[:, :, :, k, e], (J1p - J1m) / (2 * h)) < 1e-6
 
 
-def test_jastrow_derivatives_finite_difference():
-    wf = O.Wavefunction(qi.make_lih())
+@pytest.mark.parametrize("manybody", [False, True])
+def test_jastrow_derivatives_finite_difference(manybody):
+    mol = qi.make_lih()
+    wf = O.Wavefunction(qi.with_manybody_jastrow(mol) if manybody else mol)
     r = _walkers(wf.mol, 8)
     J, gJ, lJ = O.jastrow(wf, r)
     h = 1e-5
@@ -307,7 +346,7 @@ def test_table_local_energy_matches_explicit():
 
 
 def test_antisymmetry_same_spin_swap():
-    for mol in (qi.make_lih(), qi.make_co(n_det=20), qi.make_li2()):
+    for mol in (qi.make_lih(), qi.make_co(n_det=20), qi.make_li2(), qi.with_manybody_jastrow(qi.make_lih())):
         wf = O.Wavefunction(mol)
         r = _walkers(mol, 8)
         rs = r.clone()
