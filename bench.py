@@ -241,6 +241,14 @@ def run_secondary(device, stream, barrier, flush):
                 out["li2_energy_grad_note"] = ("131,072 walkers: E_L, mean/variance, gradient of 83 parameters "
                                                "and forces on both nuclei, host-timed (synchronous call)")
             wf.close()
+    # CO with the many-body Jastrow of App. D (K_en + 5 K_een terms), mixed form
+    mol = qi.with_manybody_jastrow(qi.make_co())
+    W = qi.WORKLOAD_WALKERS["co"]
+    x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
+    wf = Wavefunction(mol, precision="mixed_tf32", device=device)
+    out["co_manybody_jastrow_mixed_tf32_walker_evals_per_s"] = rate(wf, x, W, steps=3)
+    wf.close()
+    del x
     # several determinants with backflow: Li2, SD(6e, 6o) = 118 determinants
     mol = qi.make_li2(n_mo=6, n_det=118)
     W = qi.WORKLOAD_WALKERS["li2"]

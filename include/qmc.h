@@ -246,6 +246,23 @@ qmc_status qmc_set_params(qmc_wf* wf, const double* params);
  * [4] backflow w, [5] = n_param.  offsets may be NULL. */
 qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[6]);
 
+/* Many-body Jastrow factor (App. D), added to the Pade electron-electron
+ * kernel in J (Eq. jastrow):
+ *   electron-nucleus        K_en(r) = (w0 r + w1 r^2) / (1 + w2 r), summed over
+ *                           atoms a and electrons i, r = |r_i - R_a|;
+ *   electron-electron-nucleus, n_een terms mu:
+ *     K_een = sum_mu c_mu f(a1, b1; r_ai) f(a2, b2; r_aj) f(a3, b3; r_ij),
+ *     f(a, b; r) = a r / (1 + b r), summed over atoms and ordered electron
+ *     pairs i != j with a factor 1/2 (J stays symmetric under exchange).
+ * Both are spin independent.  en: host [3] (w0, w1, w2) or NULL (no K_en);
+ * een: host [n_een][7] (c, a1, b1, a2, b2, a3, b3), n_een <= 8 (0 = none).
+ * Requires w2 >= 0 and b >= 0 (no pole at r >= 0): QMC_ERR_ARG otherwise.
+ * Covers qmc_local_energy* and qmc_sample in every precision form;
+ * QMC_ERR_UNSUPPORTED with backflow, and qmc_energy_grad / qmc_optimize
+ * refuse a wavefunction that has it (its parameters are not in the gradient
+ * layout).  Synchronous (rebuilds the device tables). */
+qmc_status qmc_set_manybody_jastrow(qmc_wf* wf, const double* en, int32_t n_een, const double* een);
+
 /* Determinant method of the local-energy and sampling calls.
  *  QMC_DET_TABLE     (default) excited determinants from tables of the
  *                    reference inverse: D_X / D_0 and the kinetic trace of

@@ -86,6 +86,18 @@ class Wavefunction:
                                      ctypes.byref(handle)))
         self._h = handle
         self._lib = lib
+        jen, jeen = getattr(mol, "jastrow_en", None), getattr(mol, "jastrow_een", None)
+        if jen is not None or jeen is not None:
+            self.set_manybody_jastrow(jen, jeen)
+
+    def set_manybody_jastrow(self, en=None, een=None):
+        """Electron-nucleus kernel (w0, w1, w2) and electron-electron-nucleus
+        terms [n, 7] = (c, a1, b1, a2, b2, a3, b3) of App. D; None = off."""
+        e = None if en is None else np.ascontiguousarray(en, dtype=np.float64).reshape(3)
+        t = None if een is None else np.ascontiguousarray(een, dtype=np.float64).reshape(-1, 7)
+        _lib.check(self._lib.qmc_set_manybody_jastrow(
+            self._h, None if e is None else _ptr(e, ctypes.c_double), 0 if t is None else t.shape[0],
+            None if t is None else _ptr(t, ctypes.c_double)))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

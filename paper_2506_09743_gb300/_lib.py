@@ -24,7 +24,7 @@ EXPORTED = (
     "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_energy_grad",
     "qmc_set_params", "qmc_server_create", "qmc_server_destroy", "qmc_server_add_wf", "qmc_server_submit",
     "qmc_server_progress", "qmc_server_results", "qmc_server_free_bytes", "qmc_server_clock",
-    "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method", "qmc_optimize", "qmc_force_batches",
+    "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method", "qmc_optimize", "qmc_force_batches", "qmc_set_manybody_jastrow",
     "qmc_last_error",
 )
 
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
     lib.qmc_set_timing.restype = c_int32
     lib.qmc_set_det_method.argtypes = [c_void_p, c_int32]
     lib.qmc_set_det_method.restype = c_int32
+    lib.qmc_set_manybody_jastrow.argtypes = [c_void_p, PD, c_int32, PD]
+    lib.qmc_set_manybody_jastrow.restype = c_int32
     lib.qmc_optimize.argtypes = [c_void_p, c_void_p, c_int64, c_int64, POINTER(OptConfig), c_void_p, c_void_p]
     lib.qmc_optimize.restype = c_int32
     lib.qmc_force_batches.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32, c_void_p, c_void_p,

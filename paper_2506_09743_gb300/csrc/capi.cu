@@ -199,6 +199,19 @@ qmc_status build_tables(qmc_wf* wf) {
   d.vnn = vnn_of(d);
   if (h.w != 0.0 && prec != QMC_FP64)
     return fail(QMC_ERR_UNSUPPORTED, "backflow wavefunctions run in the FP64 form only");
+  d.mb_en = h.jen.empty() ? 0 : 1;
+  d.n_een = (int)(h.jeen.size() / 7);
+  for (int k = 0; k < 3; ++k) {
+    d.jen[k] = d.mb_en ? h.jen[k] : 0.0;
+    d.jen_f[k] = (float)d.jen[k];
+  }
+  for (int t = 0; t < d.n_een; ++t)
+    for (int k = 0; k < 7; ++k) {
+      d.jeen[t][k] = h.jeen[7 * t + k];
+      d.jeen_f[t][k] = (float)d.jeen[t][k];
+    }
+  if (h.w != 0.0 && (d.mb_en || d.n_een))
+    return fail(QMC_ERR_UNSUPPORTED, "the many-body Jastrow is not combined with backflow");
 
   // ---- basis: shells, normalisation, angular factors
   std::vector<ShellDev> shells;
@@ -777,6 +790,8 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
   if (wf->precision != QMC_FP64) return fail(QMC_ERR_UNSUPPORTED, "energy gradients are computed in the FP64 form");
   if (!general_supported(wf->dev))
     return fail(QMC_ERR_UNSUPPORTED, "energy gradients need one determinant, <= 8 electrons, <= 4 per spin");
+  if (wf->dev.mb_en || wf->dev.n_een)
+    return fail(QMC_ERR_UNSUPPORTED, "energy gradients do not cover the many-body Jastrow");
   int64_t n_param = 0;
   qmc_param_layout(wf, &n_param, nullptr);
   if (grad && grad_smem_bytes(wf->dev, (int)n_param) > 227 * 1024)
@@ -825,6 +840,28 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
   cudaError_t e = cudaMemcpyAsync(e_stats, stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? QMC_OK : cuda_fail(e, "energy statistics");
+}
+
+qmc_status qmc_set_manybody_jastrow(qmc_wf* wf, const double* en, int32_t n_een, const double* een) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  if (n_een < 0 || n_een > kMaxEen || (n_een > 0 && !een)) return fail(QMC_ERR_ARG, "bad electron-electron-nucleus terms");
+  if (en && (!std::isfinite(en[0]) || !std::isfinite(en[1]) || !(en[2] >= 0.0) || !std::isfinite(en[2])))
+    return fail(QMC_ERR_ARG, "electron-nucleus kernel: finite w0, w1 and w2 >= 0 required");
+  for (int t = 0; t < n_een; ++t)
+    for (int k = 0; k < 7; ++k) {
+      const double v = een[7 * t + k];
+      if (!std::isfinite(v) || ((k == 2 || k == 4 || k == 6) && v < 0.0))
+        return fail(QMC_ERR_ARG, "electron-electron-nucleus terms: finite values and b >= 0 required");
+    }
+  std::lock_guard<std::mutex> lock(wf->mu);
+  HostSpec old = wf->spec;
+  wf->spec.jen.clear();
+  if (en) wf->spec.jen.assign(en, en + 3);
+  wf->spec.jeen.clear();
+  if (n_een > 0) wf->spec.jeen.assign(een, een + 7 * n_een);
+  qmc_status st = build_tables(wf);
+  if (st != QMC_OK) wf->spec = old;
+  return st;
 }
 
 qmc_status qmc_set_det_method(qmc_wf* wf, int32_t method) {

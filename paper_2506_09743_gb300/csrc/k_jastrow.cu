@@ -7,6 +7,16 @@
 //   V        = sum_{i<j} 1/r_ij - sum_{i,a} Z_a / r_ia + V_nn  (Eq. Hmol)
 // Each pair is visited once.
 //
+// Many-body Jastrow (App. D), compiled in only when the wavefunction has it:
+//   K_en(r)  = (w0 r + w1 r^2) / (1 + w2 r) per electron i and atom a, r = r_ai:
+//              K' = (w0 + 2 w1 r + w1 w2 r^2) / (1 + w2 r)^2,  K'' = 2 (w1 - w0 w2) / (1 + w2 r)^3
+//   K_een    = sum_mu c_mu f(a1, b1; x) f(a2, b2; y) f(a3, b3; z), f(a, b; r) = a r / (1 + b r),
+//              x = r_ai, y = r_aj, z = r_ij, summed over atoms and ordered pairs with 1/2,
+//              i.e. G(x, y, z) = (K_een(x, y, z) + K_een(y, x, z)) / 2 per unordered pair;
+//   grad_i += G_x u_ai + G_z u_ij,  grad_j += G_y u_aj - G_z u_ij,
+//   lap_i  += G_xx + 2 G_x / x + G_zz + 2 G_z / z + 2 G_xz (u_ai . u_ij),
+//   lap_j  += G_yy + 2 G_y / y + G_zz + 2 G_z / z - 2 G_yz (u_aj . u_ij).
+//
 // FP64 form: everything in double.  Other forms: positions are split into
 // float pairs (hi + lo, integer operations only), pair differences
 // (hi_i - hi_j) + (lo_i - lo_j) keep 2^-24 relative accuracy even for close
@@ -18,7 +28,112 @@
 
 namespace qmc {
 
-template <int NMAX>
+// f(a, b; r) = a r / (1 + b r) and its first two derivatives
+template <typename T>
+__device__ __forceinline__ void rational3(T a, T b, T r, T& f, T& f1, T& f2) {
+  const T id = T(1) / (T(1) + b * r);
+  f1 = a * id * id;
+  f = a * r * id;
+  f2 = T(-2) * b * f1 * id;
+}
+
+// Many-body Jastrow contributions (App. D) of one walker.  disp_en(i, a, v)
+// writes r_i - R_a, disp_ee(i, j, v) writes r_i - r_j, both in T; par_en
+// [3] and par_een [n_een][7] are the kernel parameters in T; J and lap are
+// accumulators with add(T); g [NMAX][3] the electron gradients.
+template <typename T, int NMAX, typename DispEn, typename DispEe, typename Acc>
+__device__ __forceinline__ void manybody_terms(const WfDev& wf, const T* par_en, const T (*par_een)[7], int n,
+                                               DispEn disp_en, DispEe disp_ee, Acc& J, Acc& lap, T (&g)[NMAX][3],
+                                               bool deriv) {
+  for (int a = 0; a < wf.n_atom; ++a) {
+    if (wf.mb_en) {
+      const T w0 = par_en[0], w1 = par_en[1], w2 = par_en[2];
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) {
+        if (i < n) {
+          T v[3];
+          disp_en(i, a, v);
+          const T r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+          const T ir = T(1) / sqrt(r2), r = r2 * ir;
+          const T id = T(1) / (T(1) + w2 * r);
+          J.add((w0 * r + w1 * r * r) * id);
+          if (deriv) {
+            const T k1 = (w0 + T(2) * w1 * r + w1 * w2 * r * r) * id * id;
+            const T k2 = T(2) * (w1 - w0 * w2) * id * id * id;
+            lap.add(k2 + T(2) * k1 * ir);
+            const T s = k1 * ir;
+            g[i][0] += s * v[0]; g[i][1] += s * v[1]; g[i][2] += s * v[2];
+          }
+        }
+      }
+    }
+    if (wf.n_een == 0) continue;
+    // runtime pair loop (the electron gradients go to local memory in this
+    // variant; fully unrolled triplet sums cost minutes of compile time)
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
+#pragma unroll 1
+      for (int j = i + 1; j < n; ++j) {
+        {
+          T vi[3], vj[3], vij[3];
+          disp_en(i, a, vi);
+          disp_en(j, a, vj);
+          disp_ee(i, j, vij);
+          const T x2 = vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2];
+          const T y2 = vj[0] * vj[0] + vj[1] * vj[1] + vj[2] * vj[2];
+          const T z2 = vij[0] * vij[0] + vij[1] * vij[1] + vij[2] * vij[2];
+          const T ix = T(1) / sqrt(x2), iy = T(1) / sqrt(y2), iz = T(1) / sqrt(z2);
+          const T x = x2 * ix, y = y2 * iy, z = z2 * iz;
+          T G = T(0), Gx = T(0), Gy = T(0), Gz = T(0), Gxx = T(0), Gyy = T(0), Gzz = T(0), Gxz = T(0), Gyz = T(0);
+          for (int t = 0; t < wf.n_een; ++t) {
+            const T c = T(0.5) * par_een[t][0];
+            T p1x, p1x1, p1x2, p2y, p2y1, p2y2, p1y, p1y1, p1y2, p2x, p2x1, p2x2, q, q1, q2;
+            rational3(par_een[t][1], par_een[t][2], x, p1x, p1x1, p1x2);
+            rational3(par_een[t][3], par_een[t][4], y, p2y, p2y1, p2y2);
+            rational3(par_een[t][1], par_een[t][2], y, p1y, p1y1, p1y2);
+            rational3(par_een[t][3], par_een[t][4], x, p2x, p2x1, p2x2);
+            rational3(par_een[t][5], par_een[t][6], z, q, q1, q2);
+            const T P = p1x * p2y + p1y * p2x;  // symmetrised in x and y
+            const T Px = p1x1 * p2y + p1y * p2x1, Py = p1x * p2y1 + p1y1 * p2x;
+            G += c * P * q;
+            if (deriv) {
+              Gx += c * Px * q;
+              Gy += c * Py * q;
+              Gz += c * P * q1;
+              Gxx += c * (p1x2 * p2y + p1y * p2x2) * q;
+              Gyy += c * (p1x * p2y2 + p1y2 * p2x) * q;
+              Gzz += c * P * q2;
+              Gxz += c * Px * q1;
+              Gyz += c * Py * q1;
+            }
+          }
+          J.add(G);
+          if (deriv) {
+            T ui[3], uj[3], u[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) { ui[d] = vi[d] * ix; uj[d] = vj[d] * iy; u[d] = vij[d] * iz; }
+            const T cij = ui[0] * u[0] + ui[1] * u[1] + ui[2] * u[2];
+            const T cji = uj[0] * u[0] + uj[1] * u[1] + uj[2] * u[2];
+            lap.add(Gxx + T(2) * Gx * ix + Gyy + T(2) * Gy * iy + T(2) * (Gzz + T(2) * Gz * iz) +
+                    T(2) * (Gxz * cij - Gyz * cji));
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              g[i][d] += Gx * ui[d] + Gz * u[d];
+              g[j][d] += Gy * uj[d] - Gz * u[d];
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+struct PlainD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+};
+
+template <int NMAX, bool MB>
 __global__ void __launch_bounds__(128) k_jastrow_f64(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                      int64_t ldw, double* __restrict__ gradJ,
                                                      double* __restrict__ jscal, int64_t ldm, bool deriv) {
@@ -69,6 +184,18 @@ __global__ void __launch_bounds__(128) k_jastrow_f64(WfDev wf, const double* __r
       }
     V -= wf.atom_z[a] * va;
   }
+  if (MB) {
+    PlainD Jm, lm;
+    auto disp_en = [&](int i, int a, double* v) {
+      for (int d = 0; d < 3; ++d) v[d] = r[i][d] - wf.atom_xyz[a][d];
+    };
+    auto disp_ee = [&](int i, int j, double* v) {
+      for (int d = 0; d < 3; ++d) v[d] = r[i][d] - r[j][d];
+    };
+    manybody_terms<double, NMAX>(wf, wf.jen, wf.jeen, n, disp_en, disp_ee, Jm, lm, g, deriv);
+    J += Jm.s;
+    lap += lm.s;
+  }
   double kin = lap;
   if (deriv) {
 #pragma unroll
@@ -97,7 +224,7 @@ struct KahanF {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-template <int NMAX>
+template <int NMAX, bool MB>
 __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                      int64_t ldw, float* __restrict__ gradJ,
                                                      double* __restrict__ jscal, int64_t ldm, float b, float w0p,
@@ -155,6 +282,19 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
         V.add(-zh / sqrtf(dx * dx + dy * dy + dz * dz));
       }
   }
+  if (MB) {
+    auto disp_en = [&](int i, int a, float* v) {
+      for (int d = 0; d < 3; ++d) {
+        float ah, al;
+        split_f64(wf.atom_xyz[a][d], ah, al);
+        v[d] = (rh[i][d] - ah) + (rl[i][d] - al);
+      }
+    };
+    auto disp_ee = [&](int i, int j, float* v) {
+      for (int d = 0; d < 3; ++d) v[d] = (rh[i][d] - rh[j][d]) + (rl[i][d] - rl[j][d]);
+    };
+    manybody_terms<float, NMAX>(wf, wf.jen_f, wf.jeen_f, n, disp_en, disp_ee, J, lap, g, deriv);
+  }
   if (deriv) {
 #pragma unroll
     for (int i = 0; i < NMAX; ++i)
@@ -175,21 +315,29 @@ cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int
   if (W == 0) return cudaSuccess;
   const dim3 block(128), grid((unsigned)((W + 127) / 128));
   const float b = (float)wf.jb, w0p = (float)wf.w0_par, w0a = (float)wf.w0_anti;
-#define QMC_JAS(NM)                                                                                          \
-  if (wf.n_elec <= NM) {                                                                                     \
-    if (prec == QMC_FP64)                                                                                    \
-      k_jastrow_f64<NM><<<grid, block, 0, st>>>(wf, walkers, W, ldw, static_cast<double*>(ws.gradJ), ws.jscal, \
-                                                ws.ldm, derivs);                                             \
-    else                                                                                                     \
-      k_jastrow_f32<NM><<<grid, block, 0, st>>>(wf, walkers, W, ldw, static_cast<float*>(ws.gradJ), ws.jscal,  \
-                                                ws.ldm, b, w0p, w0a, derivs);                                \
-    return cudaGetLastError();                                                                               \
+  const bool mb = wf.mb_en || wf.n_een > 0;
+#define QMC_JAS_MB(NM, MB)                                                                                       \
+  if (prec == QMC_FP64)                                                                                          \
+    k_jastrow_f64<NM, MB><<<grid, block, 0, st>>>(wf, walkers, W, ldw, static_cast<double*>(ws.gradJ), ws.jscal, \
+                                                  ws.ldm, derivs);                                               \
+  else                                                                                                           \
+    k_jastrow_f32<NM, MB><<<grid, block, 0, st>>>(wf, walkers, W, ldw, static_cast<float*>(ws.gradJ), ws.jscal,  \
+                                                  ws.ldm, b, w0p, w0a, derivs);
+#define QMC_JAS(NM)                     \
+  if (wf.n_elec <= NM) {                \
+    if (mb) {                           \
+      QMC_JAS_MB(NM, true)              \
+    } else {                            \
+      QMC_JAS_MB(NM, false)             \
+    }                                   \
+    return cudaGetLastError();          \
   }
   QMC_JAS(2)
   QMC_JAS(4)
   QMC_JAS(8)
   QMC_JAS(16)
 #undef QMC_JAS
+#undef QMC_JAS_MB
   return cudaErrorInvalidValue;
 }
 

@@ -24,6 +24,7 @@ namespace qmc {
 constexpr int kMaxShells = 128;
 constexpr int kMaxExc = 512;   // unique excitations per spin channel
 constexpr int kMaxDets = 4096;
+constexpr int kMaxEen = 8;       // electron-electron-nucleus Jastrow terms
 constexpr int kMaxShellAo = 16;  // AOs of one shell record (longer runs are split)
 constexpr int kTcPass = 32;      // AO columns per K-pass of the tensor-core AO stage
 constexpr int kMaxTcPass = 16;   // passes (QMC_MAX_AO columns, gaps of < kMaxShellAo per pass)
@@ -50,6 +51,13 @@ struct WfDev {
   int nh[2], nv[2];  // table extents: holes n_s - h_lo, virtuals p_hi - n_s
   int tab_elems;  // doubles of excitation tables per walker
   double w0_par, w0_anti, jb, bf_w, vnn;
+  // many-body Jastrow (App. D): electron-nucleus kernel (w0, w1, w2) when
+  // mb_en, and n_een electron-electron-nucleus terms (c, a1, b1, a2, b2, a3, b3)
+  int mb_en, n_een;
+  double jen[3];
+  double jeen[kMaxEen][7];
+  float jen_f[3];  // FP32 copies for the FP32 kernels
+  float jeen_f[kMaxEen][7];
   double atom_xyz[QMC_MAX_ATOMS][3];
   double atom_z[QMC_MAX_ATOMS];
   const ShellDev* shells;  // [n_shell]

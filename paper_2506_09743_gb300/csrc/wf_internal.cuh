@@ -38,6 +38,8 @@ struct HostSpec {
   std::vector<double> prim_exp, prim_coef, mo, det_w;
   std::vector<int> det_exc;
   double w0p = 0.25, w0a = 0.5, b = 1.0, w = 0.0;
+  std::vector<double> jen;   // [3] or empty: electron-nucleus Jastrow kernel
+  std::vector<double> jeen;  // [n][7]: electron-electron-nucleus terms
 };
 
 struct qmc_wf {

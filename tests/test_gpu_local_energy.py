@@ -140,6 +140,62 @@ def test_explicit_method_parity(pkg, precision, n_det):
         assert np.all(np.abs(E - Et) <= 2 * bound)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_tf32"])
+@pytest.mark.parametrize("name", ["lih", "co"])
+def test_manybody_jastrow_parity(pkg, name, precision):
+    """Electron-nucleus and electron-electron-nucleus Jastrow kernels (App. D)
+    in every precision form against the oracle."""
+    base = qi.make_lih() if name == "lih" else qi.make_co(n_det=20)
+    mol = qi.with_manybody_jastrow(base)
+    r = qi.walkers(mol, 300 if name == "lih" else 150, seed=25)
+    E_ref, lp_ref, sens = oracle_reference(mol, r)
+    E, lp = _run(pkg, mol, r, precision)
+    if precision == "fp64":
+        fp64_check(E, E_ref, sens, min_within=0.98)
+        scale = np.maximum(1.0, np.abs(lp_ref))
+        assert np.all(np.abs(lp - lp_ref) <= 128 * 2.0 ** -53 * sens * scale + 1e-13 * scale)
+    else:
+        mixed_check(E, E_ref, sens)
+    # the terms change the energy (the test is not vacuous)
+    E0, _, _ = oracle_reference(base, r)
+    assert np.abs(E_ref - E0).max() > 1e-3
+
+
+def test_manybody_jastrow_hydrogen_closed_form_on_gpu(pkg):
+    import dataclasses
+
+    w0, w1, w2 = -0.2, 0.03, 0.8
+    mol = dataclasses.replace(qi.make_hydrogenic(1.0, 1.0), jastrow_en=np.array([w0, w1, w2]))
+    r = qi.walkers(mol, 200, seed=26)
+    x = np.linalg.norm(r[:, 0], axis=-1)
+    d = 1 + w2 * x
+    K1 = (w0 + w1 * x * (2 + w2 * x)) / d ** 2
+    K2 = 2 * (w1 - w0 * w2) / d ** 3
+    ref = -0.5 * ((K1 - 1) ** 2 + K2 + 2 * (K1 - 1) / x) - 1 / x
+    E, _ = _run(pkg, mol, r, "fp64")
+    assert np.abs(E - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_manybody_jastrow_scope(pkg):
+    from paper_2506_09743_gb300 import QmcError
+
+    wf = pkg.Wavefunction(qi.with_manybody_jastrow(qi.make_lih()), precision="fp64")
+    x = torch.tensor(qi.to_soa(qi.walkers(qi.make_lih(), 16, seed=1)), device="cuda")
+    with pytest.raises(QmcError):
+        wf.energy_grad(x)
+    with pytest.raises(QmcError):
+        wf.set_manybody_jastrow([0.1, 0.0, -1.0], None)  # pole: w2 < 0
+    wf.set_manybody_jastrow(None, None)  # off again: the plain Pade energy
+    e, _ = wf.local_energy(x)
+    ref = pkg.Wavefunction(qi.make_lih(), precision="fp64")
+    e0, _ = ref.local_energy(x)
+    assert torch.equal(e, e0)
+    wf.close()
+    ref.close()
+    with pytest.raises(QmcError):
+        pkg.Wavefunction(qi.with_manybody_jastrow(qi.make_li2()), precision="fp64")
+
+
 def test_closed_forms_on_gpu(pkg):
     mol = qi.make_hydrogenic(1.0, 1.0)
     r = qi.walkers(mol, 333, seed=4)
