@@ -74,7 +74,7 @@ size_t workspace_bytes(const qmc_wf* wf, int64_t W) {
   b += align256(3 * N * ldm * ta);                     // gradJ
   b += align256(3 * ldm * sizeof(double));             // jscal
   const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
-  b += align256((size_t)N * 2 * mo_row_pad(wf->dev.n_mo, tc) * ldm * ta);  // MO channels
+  b += align256((size_t)N * 2 * mo_row_pad(wf->dev.n_mo, tc) * ldm * sizeof(double));  // MO channels (FP64)
   b += align256(3 * N * ldm * sizeof(double));         // proposals
   b += 2 * align256(ldm * sizeof(double));             // lp, lp_new
   b += align256(sizeof(int));                          // device error flag
@@ -91,7 +91,7 @@ Workspace carve(const qmc_wf* wf, void* base, int64_t W, int** err_flag) {
   ws.jscal = reinterpret_cast<double*>(p); p += align256(3 * ws.ldm * sizeof(double));
   const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
   ws.nmp = mo_row_pad(wf->dev.n_mo, tc);
-  ws.mo = p; p += align256((size_t)N * 2 * ws.nmp * ws.ldm * ta);
+  ws.mo = reinterpret_cast<double*>(p); p += align256((size_t)N * 2 * ws.nmp * ws.ldm * sizeof(double));
   ws.prop = reinterpret_cast<double*>(p); p += align256(3 * N * ws.ldm * sizeof(double));
   ws.lp = reinterpret_cast<double*>(p); p += align256(ws.ldm * sizeof(double));
   ws.lp_new = reinterpret_cast<double*>(p); p += align256(ws.ldm * sizeof(double));
@@ -389,7 +389,7 @@ qmc_status build_tables(qmc_wf* wf) {
   if (h.w != 0.0 && !general_supported(d) && !bf_multidet_supported(d))
     return fail(QMC_ERR_UNSUPPORTED,
                 "backflow needs <= 8 electrons, <= 4 per spin and (several determinants) <= 8 orbital columns");
-  if (det_smem_bytes(d, std::max(nup, ndn), det_team_size(d), true) > 227 * 1024)
+  if (det_smem_bytes(d, true) > 227 * 1024)
     return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
 
   // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
@@ -869,7 +869,7 @@ qmc_status qmc_set_det_method(qmc_wf* wf, int32_t method) {
   if (method != QMC_DET_TABLE && method != QMC_DET_EXPLICIT) return fail(QMC_ERR_ARG, "unknown determinant method");
   std::lock_guard<std::mutex> lock(wf->mu);
   if (method == QMC_DET_EXPLICIT &&
-      det_explicit_smem_bytes(wf->dev, true, (int)ta_size(wf->precision)) > 227 * 1024)
+      det_explicit_smem_bytes(wf->dev, true) > 227 * 1024)
     return fail(QMC_ERR_UNSUPPORTED, "explicit determinant stage exceeds shared memory");
   wf->det_method = method;
   return QMC_OK;

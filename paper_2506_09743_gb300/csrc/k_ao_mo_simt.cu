@@ -13,7 +13,7 @@ namespace qmc {
 template <typename T, int NMO, int NCH>
 __global__ void __launch_bounds__(128) k_ao_mo_simt(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                     int64_t ldw, const T* __restrict__ gradJ,
-                                                    T* __restrict__ mo_out, int64_t ldm) {
+                                                    double* __restrict__ mo_out, int64_t ldm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ShellDev* sh_s = reinterpret_cast<ShellDev*>(smem_raw);
   int* pow_s = reinterpret_cast<int*>(sh_s + wf.n_shell);
@@ -79,12 +79,12 @@ __global__ void __launch_bounds__(128) k_ao_mo_simt(WfDev wf, const double* __re
       }
     }
   }
-  // walker-major MO block: row (w, i, channel) of NMO entries
-  T* dst = mo_out + ((size_t)w * wf.n_elec + i) * NCH * NMO;
+  // walker-fastest FP64 MO layout [N][NCH][NMO][ldm] (FP32 results widened exactly)
+  double* dst = mo_out + (size_t)i * NCH * NMO * ldm + w;
 #pragma unroll
   for (int m = 0; m < NMO; ++m) {
-    dst[m] = acc0[m];
-    if (NCH == 2) dst[NMO + m] = acc1[m];
+    dst[(size_t)m * ldm] = widen(acc0[m]);
+    if (NCH == 2) dst[(size_t)(NMO + m) * ldm] = widen(acc1[m]);
   }
 }
 
@@ -93,7 +93,7 @@ static cudaError_t launch_t(const WfDev& wf, const double* walkers, int64_t W, i
                             int nch, cudaStream_t st) {
   const dim3 block(128), grid((unsigned)((W + 127) / 128), (unsigned)wf.n_elec);
   const T* gj = static_cast<const T*>(ws.gradJ);
-  T* mo = static_cast<T*>(ws.mo);
+  double* mo = ws.mo;
 #define QMC_AOMO(NM)                                                                                        \
   if (wf.n_mo <= NM) {                                                                                      \
     const size_t smem = round_up(sizeof(ShellDev) * wf.n_shell + sizeof(int) * wf.n_ao, 16) +              \

@@ -98,7 +98,7 @@ __host__ __device__ inline int tc_int_words(const WfDev& wf) { return (2 * wf.n_
 template <int NCH>
 __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                          int64_t ldw, const float* __restrict__ gradJ,
-                                                         float* __restrict__ mo_out, int64_t ldm,
+                                                         double* __restrict__ mo_out, int64_t ldm,
                                                          int* __restrict__ err_flag) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int kp = wf.k_pad;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
     const int ch = tid >> 7;
     if (ch < NCH && live)
       for (int m = 0; m < kNPad; ++m)
-        mo_out[(((size_t)w * wf.n_elec + i) * NCH + ch) * kNPad + m] = __int_as_float(0x7fc00000);
+        mo_out[((size_t)(i * NCH + ch) * kNPad + m) * ldm + w] = __longlong_as_double(0x7ff8000000000000ll);
   } else {
     // ---- epilogue: TMEM -> registers -> MO channels in HBM
     const int quad = warp & 3, ch = warp >> 2;
@@ -270,12 +270,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const int64_t wr = (int64_t)blockIdx.x * kRows + quad * 32 + (tid & 31);
-      if (wr < W) {  // walker-major MO block row (wr, i, ch): 16 floats, 64 B aligned
-        float4* dst = reinterpret_cast<float4*>(mo_out + (((size_t)wr * wf.n_elec + i) * NCH + ch) * kNPad);
+      if (wr < W) {  // walker-fastest MO layout: a warp stores 32 consecutive walkers per orbital
+        double* dst = mo_out + (size_t)(i * NCH + ch) * kNPad * ldm + wr;
 #pragma unroll
-        for (int m = 0; m < kNPad / 4; ++m)
-          dst[m] = make_float4(__uint_as_float(v[4 * m]), __uint_as_float(v[4 * m + 1]),
-                               __uint_as_float(v[4 * m + 2]), __uint_as_float(v[4 * m + 3]));
+        for (int m = 0; m < kNPad; ++m) dst[(size_t)m * ldm] = widen(__uint_as_float(v[m]));
       }
     }
   }
@@ -297,7 +295,7 @@ cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, in
   const dim3 grid((unsigned)((W + kRows - 1) / kRows), (unsigned)wf.n_elec);
   const size_t smem = tc_smem_bytes(wf, nch);
   const float* gj = static_cast<const float*>(ws.gradJ);
-  float* mo = static_cast<float*>(ws.mo);
+  double* mo = ws.mo;
   if (nch == 2) {
     cudaFuncSetAttribute(k_ao_mo_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_ao_mo_tc<2><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, mo, ws.ldm, err_flag);

@@ -13,8 +13,7 @@
 // All arithmetic in FP64.
 //
 // Decomposition: a team of 8 threads per walker (four walkers per warp); the
-// walker's MO block of one spin is staged in shared memory (input type,
-// widened on read), the team's threads take distinct excitations in turn,
+// walker's MO block of one spin is staged in shared memory, the team's threads take distinct excitations in turn,
 // each factorising its A_X in registers; (D_X, t_X) go to shared memory and
 // the determinant list is then split over the team.
 #include "qmc_internal.cuh"
@@ -24,8 +23,8 @@ namespace qmc {
 constexpr int kTS = 8;
 constexpr int kWPB = 8;  // walkers per CTA (64 threads)
 
-template <int NS, typename TA, bool KIN>
-__global__ void __launch_bounds__(kWPB * kTS) k_det_explicit(WfDev wf, int64_t W, const TA* __restrict__ mo, int nmp,
+template <int NS, bool KIN>
+__global__ void __launch_bounds__(kWPB * kTS) k_det_explicit(WfDev wf, int64_t W, const double* __restrict__ mo, int nmp,
                                                              const double* __restrict__ jscal, int64_t ldm,
                                                              int stride, double* __restrict__ e_loc,
                                                              double* __restrict__ log_psi) {
@@ -45,12 +44,12 @@ __global__ void __launch_bounds__(kWPB * kTS) k_det_explicit(WfDev wf, int64_t W
   const int team = threadIdx.x / kTS, q = threadIdx.x % kTS;
   const int64_t w = (int64_t)blockIdx.x * kWPB + team;
   const bool live = w < W;
-  const int nmo = wf.n_mo, N = wf.n_elec;
+  const int nmo = wf.n_mo;
   double* my = walk_s + (size_t)team * stride;
   // per-walker shared layout: results [2][nexc][2] (D_X, t_X) | stage [NCH][NS][nmo]
   double* res = my;
-  TA* stage = reinterpret_cast<TA*>(my + 4 * nexc);
-  const TA* blk = mo + (size_t)(live ? w : 0) * N * NCH * nmp;
+  double* stage = my + 4 * nexc;
+  const int64_t wc = live ? w : 0;
 
   for (int s = 0; s < 2; ++s) {
     const int n = s == 0 ? wf.n_up : wf.n_down;
@@ -61,12 +60,12 @@ __global__ void __launch_bounds__(kWPB * kTS) k_det_explicit(WfDev wf, int64_t W
       __syncwarp();
       continue;
     }
-    {
-      const TA* src = blk + (size_t)i0 * NCH * nmp;
-      const int total = n * NCH * nmp;
+    {  // MO layout [N][NCH][nmp][ldm], walker fastest
+      const int total = n * NCH * nmo;
       for (int k = q; k < total; k += kTS) {
-        const int m = k % nmp, rc = k / nmp, c = rc % NCH, r = rc / NCH;
-        if (m < nmo) stage[(c * NS + r) * nmo + m] = live ? src[k] : TA(r == m ? 1 : 0);
+        const int m = k % nmo, rc = k / nmo, c = rc % NCH, r = rc / NCH;
+        stage[(c * NS + r) * nmo + m] =
+            live ? mo[((int64_t)((i0 + r) * NCH + c) * nmp + m) * ldm + wc] : (r == m ? 1.0 : 0.0);
       }
     }
     __syncwarp();
@@ -82,7 +81,7 @@ __global__ void __launch_bounds__(kWPB * kTS) k_det_explicit(WfDev wf, int64_t W
       for (int r = 0; r < NS; ++r)
 #pragma unroll
         for (int c = 0; c < NS; ++c)
-          a[r][c] = (r < n && c < n) ? widen(stage[r * nmo + orb[c]]) : (r == c ? 1.0 : 0.0);
+          a[r][c] = (r < n && c < n) ? (stage[r * nmo + orb[c]]) : (r == c ? 1.0 : 0.0);
       // LU with partial pivoting, P A = L U (L unit lower, stored below the diagonal)
       int perm[NS];
 #pragma unroll
@@ -103,12 +102,12 @@ __global__ void __launch_bounds__(kWPB * kTS) k_det_explicit(WfDev wf, int64_t W
 #pragma unroll
             for (int c = 0; c < NS; ++c) {
               const double t = a[k][c];
-              a[k][c] = sw ? a[i][c] : a[k][c];
-              a[i][c] = sw ? t : a[i][c];
+              a[k][c] = dsel(sw, a[i][c], t);
+              a[i][c] = dsel(sw, t, a[i][c]);
             }
             const int tp = perm[k];
-            perm[k] = sw ? perm[i] : perm[k];
-            perm[i] = sw ? tp : perm[i];
+            perm[k] = isel(sw, perm[i], tp);
+            perm[i] = isel(sw, tp, perm[i]);
           }
           const double pv = a[k][k];
           det *= (p != k) ? -pv : pv;
@@ -133,7 +132,7 @@ __global__ void __launch_bounds__(kWPB * kTS) k_det_explicit(WfDev wf, int64_t W
           if (c < n) {
             double y[NS];
 #pragma unroll
-            for (int r = 0; r < NS; ++r) y[r] = r < n ? widen(stage[(NS + perm[r]) * nmo + orb[c]]) : 0.0;
+            for (int r = 0; r < NS; ++r) y[r] = r < n ? (stage[(NS + perm[r]) * nmo + orb[c]]) : 0.0;
 #pragma unroll
             for (int r = 0; r < NS; ++r)
 #pragma unroll
@@ -177,57 +176,50 @@ __global__ void __launch_bounds__(kWPB * kTS) k_det_explicit(WfDev wf, int64_t W
 
 namespace {
 
-int explicit_stride(const WfDev& wf, int NS, bool kin, int ta_bytes) {
+int explicit_stride(const WfDev& wf, int NS, bool kin) {
   const int nexc = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
   const int nch = kin ? 2 : 1;
-  int s = 4 * nexc + (nch * NS * wf.n_mo * ta_bytes + 7) / 8;
+  int s = 4 * nexc + nch * NS * wf.n_mo;
   return s | 1;  // odd: the teams' rows start on different banks
 }
 
-template <int NS, typename TA>
+template <int NS>
 cudaError_t launch_x(const WfDev& wf, int64_t W, const Workspace& ws, bool kin, double* e_loc, double* log_psi,
                      cudaStream_t st) {
-  const int stride = explicit_stride(wf, NS, kin, (int)sizeof(TA));
-  const size_t smem = det_explicit_smem_bytes(wf, kin, (int)sizeof(TA));
+  const int stride = explicit_stride(wf, NS, kin);
+  const size_t smem = det_explicit_smem_bytes(wf, kin);
   const dim3 grid((unsigned)((W + kWPB - 1) / kWPB));
-  const TA* mo = static_cast<const TA*>(ws.mo);
-  auto kern = kin ? k_det_explicit<NS, TA, true> : k_det_explicit<NS, TA, false>;
+  auto kern = kin ? k_det_explicit<NS, true> : k_det_explicit<NS, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<grid, kWPB * kTS, smem, st>>>(wf, W, mo, ws.nmp, ws.jscal, ws.ldm, stride, e_loc, log_psi);
+  kern<<<grid, kWPB * kTS, smem, st>>>(wf, W, ws.mo, ws.nmp, ws.jscal, ws.ldm, stride, e_loc, log_psi);
   return cudaGetLastError();
-}
-
-template <typename TA>
-cudaError_t launch_xt(const WfDev& wf, int64_t W, const Workspace& ws, bool kin, double* e_loc, double* log_psi,
-                      cudaStream_t st) {
-  const int ns = wf.n_up > wf.n_down ? wf.n_up : wf.n_down;
-  switch (ns) {
-    case 1: return launch_x<1, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-    case 2: return launch_x<2, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-    case 3: return launch_x<3, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-    case 4: return launch_x<4, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-    case 5: return launch_x<5, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-    case 6: return launch_x<6, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-    case 7: return launch_x<7, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-    case 8: return launch_x<8, TA>(wf, W, ws, kin, e_loc, log_psi, st);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 }  // namespace
 
-size_t det_explicit_smem_bytes(const WfDev& wf, bool kin, int ta_bytes) {
+size_t det_explicit_smem_bytes(const WfDev& wf, bool kin) {
   const int nexc = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
   const int ns = wf.n_up > wf.n_down ? wf.n_up : wf.n_down;
-  return sizeof(double) * ((size_t)kWPB * explicit_stride(wf, ns, kin, ta_bytes) + wf.n_det) +
+  return sizeof(double) * ((size_t)kWPB * explicit_stride(wf, ns, kin) + wf.n_det) +
          sizeof(int) * (10 * (size_t)nexc + 2 * (size_t)wf.n_det);
 }
 
 cudaError_t launch_det_explicit(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,
                                 double* e_loc, double* log_psi, cudaStream_t st) {
+  (void)prec;  // the MO channels are FP64 in every form
   if (W == 0) return cudaSuccess;
-  return prec == QMC_FP64 ? launch_xt<double>(wf, W, ws, kinetic, e_loc, log_psi, st)
-                          : launch_xt<float>(wf, W, ws, kinetic, e_loc, log_psi, st);
+  const int ns = wf.n_up > wf.n_down ? wf.n_up : wf.n_down;
+  switch (ns) {
+    case 1: return launch_x<1>(wf, W, ws, kinetic, e_loc, log_psi, st);
+    case 2: return launch_x<2>(wf, W, ws, kinetic, e_loc, log_psi, st);
+    case 3: return launch_x<3>(wf, W, ws, kinetic, e_loc, log_psi, st);
+    case 4: return launch_x<4>(wf, W, ws, kinetic, e_loc, log_psi, st);
+    case 5: return launch_x<5>(wf, W, ws, kinetic, e_loc, log_psi, st);
+    case 6: return launch_x<6>(wf, W, ws, kinetic, e_loc, log_psi, st);
+    case 7: return launch_x<7>(wf, W, ws, kinetic, e_loc, log_psi, st);
+    case 8: return launch_x<8>(wf, W, ws, kinetic, e_loc, log_psi, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace qmc

@@ -4,14 +4,17 @@
 //   walkers        double [3N][ldw]            caller-owned, coordinate-major
 //   grad J         TA     [3N][ldm]            Jastrow gradient per electron
 //   jastrow scal.  double [3][ldm]             J, sum_i(lap_i J + |grad_i J|^2), V
-//   MO channels    TA     [W][N][NCH][nmp]     walker-major blocks; channel 0 =
+//   MO channels    double [N][NCH][nmp][ldm]   walker fastest; channel 0 =
 //                                              Phi_{i,m}, channel 1 =
 //                                              (lap + 2 grad J . grad) Phi_{i,m};
 //                                              orbitals padded to nmp (8/16/32)
-// with TA = double (FP64 form) or float (other forms).  Coordinate-major
-// arrays are read by thread-per-walker kernels (consecutive threads,
-// consecutive walkers); each walker's MO block is one contiguous chunk, read
-// whole by the determinant team of that walker.
+// with TA = double (FP64 form) or float (other forms).  The MO channels are
+// stored in FP64 in every form (FP32 results widened exactly): the
+// determinant stage, bound by the FP64 pipe, then reads its operands
+// without conversion.  Every array is
+// walker fastest: the kernels map consecutive threads (or consecutive
+// tensor-memory rows) to consecutive walkers, so each warp-wide load or
+// store of one element touches one contiguous span.
 #pragma once
 
 #include <cstdint>
@@ -94,7 +97,7 @@ struct Workspace {
   int nmp;         // padded orbital count of an MO row
   void* gradJ;     // TA [3N][ldm]
   double* jscal;   // [3][ldm]
-  void* mo;        // TA [W][N][NCH][nmp]
+  double* mo;      // [N][NCH][nmp][ldm]
   double* prop;    // [3N][ldm] proposed positions (sampling)
   double* lp;      // [ldm] current log|Psi| (sampling)
   double* lp_new;  // [ldm] proposed log|Psi| (sampling)
@@ -141,6 +144,25 @@ __device__ __forceinline__ double widen(float f) {
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
+// Bitwise select c ? x : y, opaque to the optimiser.  Register arrays that
+// are permuted by runtime pivot indices stay in registers (a plain select
+// chain over a row index may be turned into an indexed access, which moves
+// the whole array to local memory).
+__device__ __forceinline__ double dsel(bool c, double x, double y) {
+  double r;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\tselp.b64 %0, %2, %3, q;\n\t}"
+      : "=d"(r)
+      : "r"((int)c), "d"(x), "d"(y));
+  return r;
+}
+__device__ __forceinline__ int isel(bool c, int x, int y) {
+  int r;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\tselp.b32 %0, %2, %3, q;\n\t}"
+      : "=r"(r)
+      : "r"((int)c), "r"(x), "r"(y));
+  return r;
+}
+
 // |x| as an ordered integer key (the IEEE bit pattern with the sign cleared
 // orders like |x| for finite x), so pivot search needs no FP64 compare.
 __device__ __forceinline__ long long abs_key(double x) {
@@ -176,9 +198,8 @@ __device__ __forceinline__ double team_sum(double v) {
 }
 #endif
 
-int det_team_size(const WfDev& wf);
 size_t tc_smem_bytes(const WfDev& wf, int nch);
-size_t det_smem_bytes(const WfDev& wf, int NS, int TS, bool kin, int ta_bytes = 8);
+size_t det_smem_bytes(const WfDev& wf, bool kin);
 
 // initial walker positions for the serving loop: home nucleus per electron
 struct InitSpec {
@@ -214,7 +235,7 @@ cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, in
 cudaError_t launch_det(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,
                        double* e_loc, double* log_psi, cudaStream_t st);
 // explicit per-excitation determinants (the baseline of the table method)
-size_t det_explicit_smem_bytes(const WfDev& wf, bool kin, int ta_bytes);
+size_t det_explicit_smem_bytes(const WfDev& wf, bool kin);
 cudaError_t launch_det_explicit(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,
                                 double* e_loc, double* log_psi, cudaStream_t st);
 cudaError_t launch_propose(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
