@@ -191,6 +191,9 @@ qmc_status build_tables(qmc_wf* wf) {
   d.w0_par = h.w0p;
   d.w0_anti = h.w0a;
   d.jb = h.b;
+  d.w0p_f = (float)h.w0p;
+  d.w0a_f = (float)h.w0a;
+  d.jb_f = (float)h.b;
   d.bf_w = h.w;
   for (int a = 0; a < na; ++a) {
     for (int k = 0; k < 3; ++k) d.atom_xyz[a][k] = h.xyz[3 * a + k];

@@ -54,6 +54,7 @@ struct WfDev {
   int nh[2], nv[2];  // table extents: holes n_s - h_lo, virtuals p_hi - n_s
   int tab_elems;  // doubles of excitation tables per walker
   double w0_par, w0_anti, jb, bf_w, vnn;
+  float w0p_f, w0a_f, jb_f;  // FP32 copies for the FP32 kernels
   // many-body Jastrow (App. D): electron-nucleus kernel (w0, w1, w2) when
   // mb_en, and n_een electron-electron-nucleus terms (c, a1, b1, a2, b2, a3, b3)
   int mb_en, n_een;
