@@ -1,7 +1,8 @@
 // AO evaluation fused with the AO->MO contraction on the 5th-generation
 // tensor cores (tcgen05, sm_103a).  Mixed forms only.
 //
-// CTA = 512 threads, 128 walkers x one electron (MMA M = 128 rows).  The AO
+// Persistent CTAs (two per SM) walk over tiles of 128 walkers x one electron
+// (MMA M = 128 rows) with the tables staged once; 512 threads.  The AO
 // columns are packed on the host into K-passes of 32 columns (a shell never
 // straddles two passes; unused columns are zero).  For each pass the four
 // thread parts of a row evaluate the pass's shells (dealt to the parts by
@@ -26,6 +27,8 @@
 //
 // Every wait on an mbarrier is bounded (about one second), after which the
 // kernel raises an error flag and writes NaN instead of hanging.
+#include <algorithm>
+
 #include "ao_eval.cuh"
 
 namespace qmc {
@@ -137,127 +140,144 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
   const uint32_t tmem = *tmem_slot;
 
   const int row = tid & (kRows - 1), part = tid / kRows;
-  const int64_t w = (int64_t)blockIdx.x * kRows + row;
-  const int i = blockIdx.y;
-  const bool live = w < W;
-  double rx = 0.0, ry = 0.0, rz = 0.0;
-  float gjx = 0.f, gjy = 0.f, gjz = 0.f;
-  if (live) {
-    rx = walkers[(int64_t)(3 * i) * ldw + w];
-    ry = walkers[(int64_t)(3 * i + 1) * ldw + w];
-    rz = walkers[(int64_t)(3 * i + 2) * ldw + w];
-    if (NCH == 2) {
-      gjx = gradJ[(int64_t)(3 * i) * ldm + w];
-      gjy = gradJ[(int64_t)(3 * i + 1) * ldm + w];
-      gjz = gradJ[(int64_t)(3 * i + 2) * ldm + w];
-    }
-  }
-  auto put = [&](int ch, int k, float v) {  // k: column within the pass
-    const size_t off = (size_t)(row / 8) * (kPass / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4 + (k % 4);
-    const uint32_t hi = tf32_rna(v);
-    const float lo = v - __uint_as_float(hi);
-    A[(size_t)(ch * 2 + 0) * tile_words + off] = hi;
-    A[(size_t)(ch * 2 + 1) * tile_words + off] = tf32_rna(lo);
-  };
   const uint32_t lbo = 128, sbo_a = (uint32_t)(kPass / 4) * 128, sbo_b = (uint32_t)(kp / 4) * 128;
-  bool ok = true;
-  for (int pass = 0; pass < wf.n_pass; ++pass) {
-    if (pass > 0) {
-      // the previous pass's MMAs must have read the A buffer before it is overwritten
-      ok = ok && mbar_wait_bounded(smem_u32(mbar), (uint32_t)((pass - 1) & 1));
+  const int64_t n_wblk = (W + kRows - 1) / kRows;
+  const int64_t n_tiles = n_wblk * wf.n_elec;
+  uint32_t commits = 0;  // mbarrier phases completed so far (each pass commits once)
+  // persistent CTA: the tables stay in shared memory and the tensor memory
+  // stays allocated while the CTA walks over (walker block, electron) tiles
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int i = (int)(tile % wf.n_elec);
+    const int64_t wb = tile / wf.n_elec;
+    const int64_t w = wb * kRows + row;
+    const bool live = w < W;
+    double rx = 0.0, ry = 0.0, rz = 0.0;
+    float gjx = 0.f, gjy = 0.f, gjz = 0.f;
+    if (live) {
+      rx = walkers[(int64_t)(3 * i) * ldw + w];
+      ry = walkers[(int64_t)(3 * i + 1) * ldw + w];
+      rz = walkers[(int64_t)(3 * i + 2) * ldw + w];
+      if (NCH == 2) {
+        gjx = gradJ[(int64_t)(3 * i) * ldm + w];
+        gjy = gradJ[(int64_t)(3 * i + 1) * ldm + w];
+        gjz = gradJ[(int64_t)(3 * i + 2) * ldm + w];
+      }
     }
-    // unused columns of the pass are zero (disjoint from the shells' columns)
-    for (int k = wf.pass_cols[pass] + part; k < kPass; k += kParts)
-      for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
-    const int s_begin = wf.part_off[pass][part], s_end = wf.part_off[pass][part + 1];
-    int cur_atom = -1, pow_atom = -1;
-    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, rho = 0.f, irho = 0.f, G = 0.f;
-    float px[5], py[5], pz[5];
-    // value channel P f and kinetic channel
-    //   (lap + 2 grad J . grad)(P f) = f lap P + P (f2 + 2 (l+1) g1 + 2 g1 gJ.d) + 2 f gJ.grad P
-    auto emit = [&](int col, float v, float kin) {
-      put(0, col, live ? v : 0.f);
-      if (NCH == 2) put(1, col, live ? kin : 0.f);
+    auto put = [&](int ch, int k, float v) {  // k: column within the pass
+      const size_t off = (size_t)(row / 8) * (kPass / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4 + (k % 4);
+      const uint32_t hi = tf32_rna(v);
+      const float lo = v - __uint_as_float(hi);
+      A[(size_t)(ch * 2 + 0) * tile_words + off] = hi;
+      A[(size_t)(ch * 2 + 1) * tile_words + off] = tf32_rna(lo);
     };
-    for (int q = s_begin; q < s_end; ++q) {
-      const int ent = list_s[q];
-      const ShellDev& sh = sh_s[ent & 0xff];
-      const int c0 = (ent >> 8) & 0xff, type = ent >> 16;
-      if (sh.atom != cur_atom) {
-        cur_atom = sh.atom;
-        displacement(rx, ry, rz, wf.atom_xyz[cur_atom], dx, dy, dz);
-        r2 = dx * dx + dy * dy + dz * dz;
-        irho = rsqrtf(r2);
-        rho = r2 * irho;
-        G = gjx * dx + gjy * dy + gjz * dz;
+    bool ok = true;
+    for (int pass = 0; pass < wf.n_pass; ++pass) {
+      if (pass > 0) {
+        // the previous pass's MMAs must have read the A buffer before it is overwritten
+        ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1) && ok;
       }
-      float f, g1 = 0.f, f2 = 0.f;
-      shell_radial(sh, r2, rho, irho, f, g1, f2, NCH == 2);
-      const float RL = f2 + float(2 * (sh.l + 1)) * g1 + 2.f * g1 * G;
-      const float tf = 2.f * f;
-      if (type == 1) {
-        emit(c0, f, RL);
-      } else if (type == 2) {
-        emit(c0 + 0, dx * f, dx * RL + tf * gjx);
-        emit(c0 + 1, dy * f, dy * RL + tf * gjy);
-        emit(c0 + 2, dz * f, dz * RL + tf * gjz);
-      } else if (type == 3) {
-        const float fx = f * dx, fy = f * dy, fz = f * dz;
-        const float Rx = RL * dx, Ry = RL * dy, Rz = RL * dz;
-        emit(c0 + 0, fx * dx, tf + Rx * dx + 2.f * tf * gjx * dx);
-        emit(c0 + 1, fx * dy, Rx * dy + tf * (gjx * dy + gjy * dx));
-        emit(c0 + 2, fx * dz, Rx * dz + tf * (gjx * dz + gjz * dx));
-        emit(c0 + 3, fy * dy, tf + Ry * dy + 2.f * tf * gjy * dy);
-        emit(c0 + 4, fy * dz, Ry * dz + tf * (gjy * dz + gjz * dy));
-        emit(c0 + 5, fz * dz, tf + Rz * dz + 2.f * tf * gjz * dz);
-      } else {
-        if (pow_atom != cur_atom) {
-          pow_atom = cur_atom;
-          pow_table(dx, px); pow_table(dy, py); pow_table(dz, pz);
+      // unused columns of the pass are zero (disjoint from the shells' columns)
+      for (int k = wf.pass_cols[pass] + part; k < kPass; k += kParts)
+        for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
+      const int s_begin = wf.part_off[pass][part], s_end = wf.part_off[pass][part + 1];
+      int cur_atom = -1, pow_atom = -1;
+      float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, rho = 0.f, irho = 0.f, G = 0.f;
+      float px[5], py[5], pz[5];
+      // value channel P f and kinetic channel
+      //   (lap + 2 grad J . grad)(P f) = f lap P + P (f2 + 2 (l+1) g1 + 2 g1 gJ.d) + 2 f gJ.grad P
+      auto emit = [&](int col, float v, float kin) {
+        put(0, col, live ? v : 0.f);
+        if (NCH == 2) put(1, col, live ? kin : 0.f);
+      };
+      for (int q = s_begin; q < s_end; ++q) {
+        const int ent = list_s[q];
+        const ShellDev& sh = sh_s[ent & 0xff];
+        const int c0 = (ent >> 8) & 0xff, type = ent >> 16;
+        if (sh.atom != cur_atom) {
+          cur_atom = sh.atom;
+          displacement(rx, ry, rz, wf.atom_xyz[cur_atom], dx, dy, dz);
+          r2 = dx * dx + dy * dy + dz * dz;
+          irho = rsqrtf(r2);
+          rho = r2 * irho;
+          G = gjx * dx + gjy * dy + gjz * dz;
         }
-        for (int k = 0; k < sh.n_ao; ++k) {
-          const int b = sh.ao_first + k;
-          const int col = col_s[b] - pass * kPass;
-          float P, Px, Py, Pz, lapP;
-          angular(pow_s[b], px, py, pz, P, Px, Py, Pz, lapP, NCH == 2);
-          emit(col, P * f, f * lapP + P * RL + tf * (gjx * Px + gjy * Py + gjz * Pz));
+        float f, g1 = 0.f, f2 = 0.f;
+        shell_radial(sh, r2, rho, irho, f, g1, f2, NCH == 2);
+        const float RL = f2 + float(2 * (sh.l + 1)) * g1 + 2.f * g1 * G;
+        const float tf = 2.f * f;
+        if (type == 1) {
+          emit(c0, f, RL);
+        } else if (type == 2) {
+          emit(c0 + 0, dx * f, dx * RL + tf * gjx);
+          emit(c0 + 1, dy * f, dy * RL + tf * gjy);
+          emit(c0 + 2, dz * f, dz * RL + tf * gjz);
+        } else if (type == 3) {
+          const float fx = f * dx, fy = f * dy, fz = f * dz;
+          const float Rx = RL * dx, Ry = RL * dy, Rz = RL * dz;
+          emit(c0 + 0, fx * dx, tf + Rx * dx + 2.f * tf * gjx * dx);
+          emit(c0 + 1, fx * dy, Rx * dy + tf * (gjx * dy + gjy * dx));
+          emit(c0 + 2, fx * dz, Rx * dz + tf * (gjx * dz + gjz * dx));
+          emit(c0 + 3, fy * dy, tf + Ry * dy + 2.f * tf * gjy * dy);
+          emit(c0 + 4, fy * dz, Ry * dz + tf * (gjy * dz + gjz * dy));
+          emit(c0 + 5, fz * dz, tf + Rz * dz + 2.f * tf * gjz * dz);
+        } else {
+          if (pow_atom != cur_atom) {
+            pow_atom = cur_atom;
+            pow_table(dx, px); pow_table(dy, py); pow_table(dz, pz);
+          }
+          for (int k = 0; k < sh.n_ao; ++k) {
+            const int b = sh.ao_first + k;
+            const int col = col_s[b] - pass * kPass;
+            float P, Px, Py, Pz, lapP;
+            angular(pow_s[b], px, py, pz, P, Px, Py, Pz, lapP, NCH == 2);
+            emit(col, P * f, f * lapP + P * RL + tf * (gjx * Px + gjy * Py + gjz * Pz));
+          }
         }
       }
+      // generic-proxy shared stores -> visible to the tensor core (async proxy);
+      // every thread learns whether all the waits of this CTA succeeded
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      ok = __syncthreads_and(ok) != 0;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) break;
+      if (tid == 0) {
+        const uint32_t b_hi = smem_u32(B), b_lo = smem_u32(B + kNPad * kp);
+        for (int ch = 0; ch < NCH; ++ch) {
+          const uint32_t a_hi = smem_u32(A + (size_t)(ch * 2) * tile_words);
+          const uint32_t a_lo = smem_u32(A + (size_t)(ch * 2 + 1) * tile_words);
+          const uint32_t d = tmem + (uint32_t)(ch * kNPad);
+          for (int ks = 0; ks < kPass / 8; ++ks) {
+            const uint32_t aoff = (uint32_t)ks * 256;                            // two core matrices along K
+            const uint32_t boff = (uint32_t)(pass * (kPass / 4) + 2 * ks) * 128;  // same columns of B
+            const uint32_t acc = (pass > 0 || ks > 0) ? 1u : 0u;
+            mma_tf32(d, smem_desc(a_hi + aoff, lbo, sbo_a), smem_desc(b_hi + boff, lbo, sbo_b), acc);
+            mma_tf32(d, smem_desc(a_hi + aoff, lbo, sbo_a), smem_desc(b_lo + boff, lbo, sbo_b), 1u);
+            mma_tf32(d, smem_desc(a_lo + aoff, lbo, sbo_a), smem_desc(b_hi + boff, lbo, sbo_b), 1u);
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(mbar))
+                     : "memory");
+      }
+      ++commits;
     }
-    // generic-proxy shared stores -> visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    if (ok) ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1);
+    ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
-      const uint32_t b_hi = smem_u32(B), b_lo = smem_u32(B + kNPad * kp);
-      for (int ch = 0; ch < NCH; ++ch) {
-        const uint32_t a_hi = smem_u32(A + (size_t)(ch * 2) * tile_words);
-        const uint32_t a_lo = smem_u32(A + (size_t)(ch * 2 + 1) * tile_words);
-        const uint32_t d = tmem + (uint32_t)(ch * kNPad);
-        for (int ks = 0; ks < kPass / 8; ++ks) {
-          const uint32_t aoff = (uint32_t)ks * 256;                            // two core matrices along K
-          const uint32_t boff = (uint32_t)(pass * (kPass / 4) + 2 * ks) * 128;  // same columns of B
-          const uint32_t acc = (pass > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(d, smem_desc(a_hi + aoff, lbo, sbo_a), smem_desc(b_hi + boff, lbo, sbo_b), acc);
-          mma_tf32(d, smem_desc(a_hi + aoff, lbo, sbo_a), smem_desc(b_lo + boff, lbo, sbo_b), 1u);
-          mma_tf32(d, smem_desc(a_lo + aoff, lbo, sbo_a), smem_desc(b_hi + boff, lbo, sbo_b), 1u);
-        }
+    if (!ok) {
+      // an MMA did not complete in time: poison this CTA's remaining outputs
+      // (this tile and the tiles it would have taken) and stop
+      if (tid == 0) atomicExch(err_flag, 1);
+      const int ch = tid >> 7;
+      for (int64_t t = tile; t < n_tiles; t += gridDim.x) {
+        const int ti = (int)(t % wf.n_elec);
+        const int64_t tw = (t / wf.n_elec) * kRows + row;
+        if (ch < NCH && tw < W)
+          for (int m = 0; m < kNPad; ++m)
+            mo_out[((size_t)(ti * NCH + ch) * kNPad + m) * ldm + tw] = __longlong_as_double(0x7ff8000000000000ll);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(mbar))
-                   : "memory");
+      break;
     }
-  }
-  ok = ok && mbar_wait_bounded(smem_u32(mbar), (uint32_t)((wf.n_pass - 1) & 1));
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok) {
-    // the accumulators are not trustworthy: poison this tile's outputs
-    if (tid == 0) atomicExch(err_flag, 1);
-    const int ch = tid >> 7;
-    if (ch < NCH && live)
-      for (int m = 0; m < kNPad; ++m)
-        mo_out[((size_t)(i * NCH + ch) * kNPad + m) * ldm + w] = __longlong_as_double(0x7ff8000000000000ll);
-  } else {
     // ---- epilogue: TMEM -> registers -> MO channels in HBM
     const int quad = warp & 3, ch = warp >> 2;
     if (ch < NCH) {
@@ -269,15 +289,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
             "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int64_t wr = (int64_t)blockIdx.x * kRows + quad * 32 + (tid & 31);
+      const int64_t wr = wb * kRows + quad * 32 + (tid & 31);
       if (wr < W) {  // walker-fastest MO layout: a warp stores 32 consecutive walkers per orbital
         double* dst = mo_out + (size_t)(i * NCH + ch) * kNPad * ldm + wr;
 #pragma unroll
         for (int m = 0; m < kNPad; ++m) dst[(size_t)m * ldm] = widen(__uint_as_float(v[m]));
       }
     }
+    // the next tile's first MMA overwrites the accumulators: the loads above
+    // are complete (wait::ld) before the barrier that precedes it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
@@ -292,7 +314,13 @@ cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, in
                             const Workspace& ws, int nch, int* err_flag, cudaStream_t st) {
   if (W == 0) return cudaSuccess;
   if (prec != QMC_MIXED_TF32) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)((W + kRows - 1) / kRows), (unsigned)wf.n_elec);
+  // persistent grid: two CTAs per SM (the occupancy the kernel is built
+  // for), never more CTAs than tiles
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t n_tiles = ((W + kRows - 1) / kRows) * wf.n_elec;
+  const dim3 grid((unsigned)std::min<int64_t>(n_tiles, 2 * (int64_t)std::max(n_sm, 1)));
   const size_t smem = tc_smem_bytes(wf, nch);
   const float* gj = static_cast<const float*>(ws.gradJ);
   double* mo = ws.mo;
