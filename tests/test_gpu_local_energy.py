@@ -252,12 +252,15 @@ def test_caller_workspace_and_too_small_workspace(pkg):
     assert "workspace" in str(ei.value)
 
 
-def test_host_entry_point_matches_device(pkg):
+@pytest.mark.parametrize("W", [500, 70001])
+def test_host_entry_point_matches_device(pkg, W):
+    """The host-buffer entry point gives the device call's results bit for
+    bit."""
     mol = qi.make_co(n_det=30)
-    r = qi.walkers(mol, 500, seed=9)
+    r = qi.walkers(mol, W, seed=9)
     wf = pkg.Wavefunction(mol, precision="mixed_tf32")
     soa = np.ascontiguousarray(qi.to_soa(r))
-    e_h, lp_h = wf.local_energy_host(soa, log_psi=np.empty(500))
+    e_h, lp_h = wf.local_energy_host(soa, log_psi=np.empty(W))
     e_d, lp_d = wf.local_energy(torch.tensor(soa, device="cuda"))
     torch.cuda.synchronize()
     assert np.array_equal(e_h, e_d.cpu().numpy()) and np.array_equal(lp_h, lp_d.cpu().numpy())
