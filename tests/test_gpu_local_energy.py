@@ -252,6 +252,39 @@ def test_caller_workspace_and_too_small_workspace(pkg):
     assert "workspace" in str(ei.value)
 
 
+@pytest.mark.parametrize("precision", ["mixed_tf32", "fp32", "fp64"])
+def test_set_params_rebuilds_every_table(pkg, precision):
+    """New exponents, MO coefficients, CI weights and Jastrow b installed with
+    qmc_set_params give the energies of a wavefunction built from them (the
+    tensor-core operand, shell tables and excitation weights are rebuilt)."""
+    import dataclasses
+
+    mol = qi.make_co(n_det=20)
+    r = qi.walkers(mol, 257, seed=27)
+    wf = pkg.Wavefunction(mol, precision=precision)
+    n, off = wf.param_layout()
+    rng = np.random.default_rng(3)
+    p = np.concatenate([mol.prim_exp, mol.mo_coeff.reshape(-1), mol.det_weight, [mol.jastrow_b, 0.0]])
+    assert p.shape[0] == n
+    p2 = p.copy()
+    p2[off[0]:off[1]] *= rng.uniform(0.9, 1.1, off[1] - off[0])
+    p2[off[1]:off[2]] += 0.01 * rng.standard_normal(off[2] - off[1])
+    p2[off[2]:off[3]] *= rng.uniform(0.8, 1.2, off[3] - off[2])
+    p2[off[3]] = 0.8
+    wf.set_params(p2)
+    x = torch.tensor(qi.to_soa(r), device="cuda")
+    e1, lp1 = wf.local_energy(x)
+    mol2 = dataclasses.replace(mol, prim_exp=p2[off[0]:off[1]].copy(),
+                               mo_coeff=p2[off[1]:off[2]].reshape(mol.mo_coeff.shape).copy(),
+                               det_weight=p2[off[2]:off[3]].copy(), jastrow_b=0.8)
+    fresh = pkg.Wavefunction(mol2, precision=precision)
+    e2, lp2 = fresh.local_energy(x)
+    torch.cuda.synchronize()
+    assert torch.equal(e1, e2) and torch.equal(lp1, lp2)
+    wf.close()
+    fresh.close()
+
+
 @pytest.mark.parametrize("W", [500, 70001])
 def test_host_entry_point_matches_device(pkg, W):
     """The host-buffer entry point gives the device call's results bit for
