@@ -144,15 +144,37 @@ __global__ void __launch_bounds__(2 * kWalkersPerBlock)
       for (int r = 0; r < NS; ++r)
         if (m < n && r < n) tr0 = fma(a[m][r], ld(1, r, m), tr0);
   }
+  // virtual columns Phi_p and B_p are loaded one column ahead (software
+  // pipelining: their global-load latency overlaps the previous column's FMAs)
+  double nphi[NS], nbp[NS];
+#pragma unroll
+  for (int r = 0; r < NS; ++r) {
+    nphi[r] = (r < n && nv > 0) ? ld(0, r, n) : 0.0;
+    nbp[r] = (KIN && r < n && nv > 0) ? ld(1, r, n) : 0.0;
+  }
   for (int pv = 0; pv < nv; ++pv) {
     const int p = n + pv;
+    double cphi[NS], cbp[NS];
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      cphi[r] = nphi[r];
+      cbp[r] = nbp[r];
+    }
+    if (pv + 1 < nv) {
+#pragma unroll
+      for (int r = 0; r < NS; ++r)
+        if (r < n) {
+          nphi[r] = ld(0, r, p + 1);
+          if (KIN) nbp[r] = ld(1, r, p + 1);
+        }
+    }
     double t[NS];
 #pragma unroll
     for (int m = 0; m < NS; ++m) t[m] = 0.0;
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
       if (r < n) {
-        const double phi = ld(0, r, p);
+        const double phi = cphi[r];
 #pragma unroll
         for (int m = 0; m < NS; ++m) t[m] = fma(a[m][r], phi, t[m]);
       }
@@ -166,7 +188,7 @@ __global__ void __launch_bounds__(2 * kWalkersPerBlock)
       for (int r = 0; r < NS; ++r) {
         double acc = 0.0;
         if (r < n) {
-          acc = ld(1, r, p);
+          acc = cbp[r];
 #pragma unroll
           for (int m = 0; m < NS; ++m)
             if (m < n) acc = fma(-ld(1, r, m), t[m], acc);
