@@ -138,11 +138,16 @@ __global__ void __launch_bounds__(2 * kWalkersPerBlock)
   // ---- 2. tr0 and the excitation tables
   double tr0 = 0.0;
   if (KIN) {
+    double part[NS];  // independent partial sums (no serial FMA chain)
 #pragma unroll
-    for (int m = 0; m < NS; ++m)
+    for (int m = 0; m < NS; ++m) {
+      part[m] = 0.0;
 #pragma unroll
       for (int r = 0; r < NS; ++r)
-        if (m < n && r < n) tr0 = fma(a[m][r], ld(1, r, m), tr0);
+        if (m < n && r < n) part[m] = fma(a[m][r], ld(1, r, m), part[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < NS; ++m) tr0 += part[m];
   }
   // virtual columns Phi_p and B_p are loaded one column ahead (software
   // pipelining: their global-load latency overlaps the previous column's FMAs)
