@@ -389,6 +389,21 @@ qmc_status build_tables(qmc_wf* wf) {
     d.nv[s] = p_hi - ns;
   }
   d.tab_elems = 2 * (d.nh[0] * d.nv[0] + d.nh[1] * d.nv[1]);
+  // per determinant and spin: the table offsets (h_a - h_lo) nv + (p_b - n_s)
+  // of its k x k block packed into one word (8 bits each; nh nv <= 8 x 24)
+  // and its rank, so the determinant stage reads one record per determinant
+  std::vector<int> det_tab(4 * (size_t)ndet);
+  for (int n = 0; n < ndet; ++n)
+    for (int s = 0; s < 2; ++s) {
+      const int ns = s == 0 ? nup : ndn, hl = d.h_lo[s], nv = d.nv[s];
+      const int* e = &exc[(s * kMaxExc + det_idx[2 * n + s]) * 5];
+      auto q = [&](int hh, int pp) { return (hh - hl) * nv + (pp - ns); };
+      int packed = 0;
+      if (e[0] >= 1) packed = q(e[1], e[3]);
+      if (e[0] == 2) packed |= (q(e[1], e[4]) << 8) | (q(e[2], e[3]) << 16) | (q(e[2], e[4]) << 24);
+      det_tab[4 * n + 2 * s] = packed;
+      det_tab[4 * n + 2 * s + 1] = e[0];
+    }
   if (h.w != 0.0 && !general_supported(d) && !bf_multidet_supported(d))
     return fail(QMC_ERR_UNSUPPORTED,
                 "backflow needs <= 8 electrons, <= 4 per spin and (several determinants) <= 8 orbital columns");
@@ -425,7 +440,7 @@ qmc_status build_tables(qmc_wf* wf) {
       {det_w_sorted.data(), sizeof(double) * ndet},      {tc_hi.data(), sizeof(uint32_t) * tc_hi.size()},
       {tc_lo.data(), sizeof(uint32_t) * tc_lo.size()},  {ang.data(), sizeof(double) * nao},
       {h.prim_start.data(), sizeof(int) * (nao + 1)}, {ao_col.data(), sizeof(int) * nao},
-      {tc_shells.data(), sizeof(int) * tc_shells.size()}};
+      {tc_shells.data(), sizeof(int) * tc_shells.size()}, {det_tab.data(), sizeof(int) * det_tab.size()}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
   void* blob = nullptr;
@@ -460,6 +475,7 @@ qmc_status build_tables(qmc_wf* wf) {
   d.ao_prim = reinterpret_cast<const int*>(ptr[10]);
   d.ao_col = reinterpret_cast<const int*>(ptr[11]);
   d.tc_shells = reinterpret_cast<const int*>(ptr[12]);
+  d.det_tab = reinterpret_cast<const int4*>(ptr[13]);
   // the previous tables may still be read by work in flight on any stream
   if (wf->blob) {
     cudaDeviceSynchronize();

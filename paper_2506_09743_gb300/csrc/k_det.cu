@@ -51,15 +51,13 @@ __global__ void __launch_bounds__(2 * kWalkersPerBlock)
           int stride, double* __restrict__ e_loc, double* __restrict__ log_psi) {
   constexpr int NCH = KIN ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nexc = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
   double* tab_all = reinterpret_cast<double*>(smem_raw);       // [kWalkersPerBlock][stride]
   double* dw_s = tab_all + (size_t)kWalkersPerBlock * stride;  // [n_det]
-  int* exc_s = reinterpret_cast<int*>(dw_s + wf.n_det);        // [2][nexc][5]
-  int* didx_s = exc_s + 10 * nexc;                             // [n_det][2]
-  for (int s = 0; s < 2; ++s)
-    for (int k = threadIdx.x; k < wf.n_exc[s] * 5; k += blockDim.x) exc_s[s * nexc * 5 + k] = wf.exc[s * kMaxExc * 5 + k];
-  for (int k = threadIdx.x; k < wf.n_det * 2; k += blockDim.x) didx_s[k] = wf.det_idx[k];
-  for (int k = threadIdx.x; k < wf.n_det; k += blockDim.x) dw_s[k] = wf.det_w[k];
+  int4* dt_s = reinterpret_cast<int4*>(dw_s + ((wf.n_det + 1) & ~1));  // [n_det] determinant records
+  for (int k = threadIdx.x; k < wf.n_det; k += blockDim.x) {
+    dw_s[k] = wf.det_w[k];
+    dt_s[k] = wf.det_tab[k];
+  }
   __syncthreads();
 
   const int wl = threadIdx.x >> 1, s = threadIdx.x & 1;
@@ -219,31 +217,26 @@ __global__ void __launch_bounds__(2 * kWalkersPerBlock)
   // ---- 3. determinant expansion: thread s takes determinants d = s, s + 2, ...
   double sum_r = 0.0, sum_k = 0.0;
   for (int d = s; d < wf.n_det; d += 2) {
+    const int4 rec = dt_s[d];
     double R[2], K[2];
-    int off = 0;
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
-      const int nsp = sp == 0 ? wf.n_up : wf.n_down;
-      const int hls = wf.h_lo[sp], nhs = wf.nh[sp], nvs = wf.nv[sp];
-      const int* e = exc_s + (sp * nexc + didx_s[2 * d + sp]) * 5;
-      const int rank = e[0];
+      const int packed = sp == 0 ? rec.x : rec.z, rank = sp == 0 ? rec.y : rec.w;
+      const int off = sp == 0 ? 0 : NCH * wf.nh[0] * wf.nv[0];
       const double* tv = tab + off;
-      const double* tk = tab + off + nhs * nvs;
+      const double* tk = tab + off + wf.nh[sp] * wf.nv[sp];
+      const int q00 = packed & 0xff, q01 = (packed >> 8) & 0xff, q10 = (packed >> 16) & 0xff, q11 = packed >> 24;
       if (rank == 0) {
         R[sp] = 1.0;
         K[sp] = 0.0;
       } else if (rank == 1) {
-        const int qq = (e[1] - hls) * nvs + (e[3] - nsp);
-        R[sp] = tv[qq];
-        K[sp] = KIN ? tk[qq] : 0.0;
+        R[sp] = tv[q00];
+        K[sp] = KIN ? tk[q00] : 0.0;
       } else {
-        const int q00 = (e[1] - hls) * nvs + (e[3] - nsp), q01 = (e[1] - hls) * nvs + (e[4] - nsp);
-        const int q10 = (e[2] - hls) * nvs + (e[3] - nsp), q11 = (e[2] - hls) * nvs + (e[4] - nsp);
         const double s00 = tv[q00], s01 = tv[q01], s10 = tv[q10], s11 = tv[q11];
         R[sp] = fma(s00, s11, -s01 * s10);
         K[sp] = KIN ? fma(s11, tk[q00], fma(-s01, tk[q10], fma(-s10, tk[q01], s00 * tk[q11]))) : 0.0;
       }
-      off += NCH * nhs * nvs;
     }
     const double dw = dw_s[d];
     const double dr1 = dw * R[1];
@@ -284,9 +277,8 @@ cudaError_t launch_ns(const WfDev& wf, int64_t W, const Workspace& ws, bool kin,
 }  // namespace
 
 size_t det_smem_bytes(const WfDev& wf, bool kin) {
-  const int nexc = wf.n_exc[0] > wf.n_exc[1] ? wf.n_exc[0] : wf.n_exc[1];
-  return sizeof(double) * ((size_t)kWalkersPerBlock * table_stride(wf, kin) + wf.n_det) +
-         sizeof(int) * (10 * (size_t)nexc + 2 * (size_t)wf.n_det);
+  return sizeof(double) * ((size_t)kWalkersPerBlock * table_stride(wf, kin) + ((wf.n_det + 1) & ~1)) +
+         sizeof(int4) * (size_t)wf.n_det;
 }
 
 cudaError_t launch_det(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic, double* e_loc,

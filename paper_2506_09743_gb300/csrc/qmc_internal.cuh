@@ -71,6 +71,10 @@ struct WfDev {
   const int* exc;          // [2][kMaxExc][5] rank, h1, h2, p1, p2
   const int* det_idx;      // [n_det][2] excitation index per spin
   const double* det_w;     // [n_det]
+  // [n_det] {packed offsets up, rank up, packed offsets down, rank down}:
+  // table offsets (h_a - h_lo) nv + (p_b - n_s) of the k x k block, 8 bits
+  // each in the order (h1 p1), (h1 p2), (h2 p1), (h2 p2)
+  const int4* det_tab;
   // tensor-core B operand: MO^T split into high and low parts, K-major
   // core-matrix layout [n_mo_pad=16][k_pad], 32-bit words
   const uint32_t* mo_tc_hi;
