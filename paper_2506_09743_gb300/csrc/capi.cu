@@ -215,6 +215,8 @@ qmc_status build_tables(qmc_wf* wf) {
     }
   if (h.w != 0.0 && (d.mb_en || d.n_een))
     return fail(QMC_ERR_UNSUPPORTED, "the many-body Jastrow is not combined with backflow");
+  if (d.n_een && een_shared_bytes(d, prec == QMC_FP64) > 227 * 1024)
+    return fail(QMC_ERR_UNSUPPORTED, "electron-electron-nucleus Jastrow tables exceed shared memory");
 
   // ---- basis: shells, normalisation, angular factors
   std::vector<ShellDev> shells;

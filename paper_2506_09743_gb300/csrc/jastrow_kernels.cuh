@@ -26,107 +26,262 @@
 // sums are widened.
 #pragma once
 
+#include <type_traits>
+
 #include "qmc_internal.cuh"
 
 namespace qmc {
 
+// 1 / d: IEEE division in FP64; the correctly rounded reciprocal in FP32
+// (one reciprocal instead of a division per kernel evaluation)
+__device__ __forceinline__ double recip_t(double d) { return 1.0 / d; }
+__device__ __forceinline__ float recip_t(float d) { return __frcp_rn(d); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
 // f(a, b; r) = a r / (1 + b r) and its first two derivatives
 template <typename T>
 __device__ __forceinline__ void rational3(T a, T b, T r, T& f, T& f1, T& f2) {
-  const T id = T(1) / (T(1) + b * r);
+  const T id = recip_t(T(1) + b * r);
   f1 = a * id * id;
   f = a * r * id;
   f2 = T(-2) * b * f1 * id;
 }
 
-// Many-body Jastrow contributions (App. D) of one walker.  disp_en(i, a, v)
-// writes r_i - R_a, disp_ee(i, j, v) writes r_i - r_j, both in T; par_en
-// [3] and par_een [n_een][7] are the kernel parameters in T; J and lap are
-// accumulators with add(T); g [NMAX][3] the electron gradients.
-template <typename T, int NMAX, typename DispEn, typename DispEe, typename Acc>
-__device__ __forceinline__ void manybody_terms(const WfDev& wf, const T* par_en, const T (*par_een)[7], int n,
-                                               DispEn disp_en, DispEe disp_ee, Acc& J, Acc& lap, T (&g)[NMAX][3],
-                                               bool deriv) {
+// Electron-nucleus Jastrow kernel (App. D) of one walker.  disp_en(i, a, v)
+// writes r_i - R_a in T; par_en [3] are (w0, w1, w2) in T; J and lap are
+// accumulators with add(T); g [NMAX][3] the electron gradients.  (The
+// electron-electron-nucleus terms run in k_jastrow_een, after this stage.)
+template <typename T, int NMAX, typename DispEn, typename Acc>
+__device__ __forceinline__ void en_terms(const WfDev& wf, const T* par_en, int n, DispEn disp_en, Acc& J, Acc& lap,
+                                         T (&g)[NMAX][3], bool deriv) {
+  if (!wf.mb_en) return;
+  const T w0 = par_en[0], w1 = par_en[1], w2 = par_en[2];
   for (int a = 0; a < wf.n_atom; ++a) {
-    if (wf.mb_en) {
-      const T w0 = par_en[0], w1 = par_en[1], w2 = par_en[2];
 #pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        if (i < n) {
-          T v[3];
-          disp_en(i, a, v);
-          const T r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-          const T ir = T(1) / sqrt(r2), r = r2 * ir;
-          const T id = T(1) / (T(1) + w2 * r);
-          J.add((w0 * r + w1 * r * r) * id);
-          if (deriv) {
-            const T k1 = (w0 + T(2) * w1 * r + w1 * w2 * r * r) * id * id;
-            const T k2 = T(2) * (w1 - w0 * w2) * id * id * id;
-            lap.add(k2 + T(2) * k1 * ir);
-            const T s = k1 * ir;
-            g[i][0] += s * v[0]; g[i][1] += s * v[1]; g[i][2] += s * v[2];
-          }
+    for (int i = 0; i < NMAX; ++i) {
+      if (i < n) {
+        T v[3];
+        disp_en(i, a, v);
+        const T r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const T ir = T(1) / sqrt(r2), r = r2 * ir;
+        const T id = T(1) / (T(1) + w2 * r);
+        J.add((w0 * r + w1 * r * r) * id);
+        if (deriv) {
+          const T k1 = (w0 + T(2) * w1 * r + w1 * w2 * r * r) * id * id;
+          const T k2 = T(2) * (w1 - w0 * w2) * id * id * id;
+          lap.add(k2 + T(2) * k1 * ir);
+          const T s = k1 * ir;
+          g[i][0] += s * v[0]; g[i][1] += s * v[1]; g[i][2] += s * v[2];
         }
       }
     }
-    if (wf.n_een == 0) continue;
-    // runtime pair loop (the electron gradients go to local memory in this
-    // variant; fully unrolled triplet sums cost minutes of compile time)
-#pragma unroll 1
-    for (int i = 0; i < n; ++i) {
-#pragma unroll 1
-      for (int j = i + 1; j < n; ++j) {
-        {
-          T vi[3], vj[3], vij[3];
-          disp_en(i, a, vi);
-          disp_en(j, a, vj);
-          disp_ee(i, j, vij);
-          const T x2 = vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2];
-          const T y2 = vj[0] * vj[0] + vj[1] * vj[1] + vj[2] * vj[2];
-          const T z2 = vij[0] * vij[0] + vij[1] * vij[1] + vij[2] * vij[2];
-          const T ix = T(1) / sqrt(x2), iy = T(1) / sqrt(y2), iz = T(1) / sqrt(z2);
-          const T x = x2 * ix, y = y2 * iy, z = z2 * iz;
-          T G = T(0), Gx = T(0), Gy = T(0), Gz = T(0), Gxx = T(0), Gyy = T(0), Gzz = T(0), Gxz = T(0), Gyz = T(0);
-          for (int t = 0; t < wf.n_een; ++t) {
-            const T c = T(0.5) * par_een[t][0];
-            T p1x, p1x1, p1x2, p2y, p2y1, p2y2, p1y, p1y1, p1y2, p2x, p2x1, p2x2, q, q1, q2;
-            rational3(par_een[t][1], par_een[t][2], x, p1x, p1x1, p1x2);
-            rational3(par_een[t][3], par_een[t][4], y, p2y, p2y1, p2y2);
-            rational3(par_een[t][1], par_een[t][2], y, p1y, p1y1, p1y2);
-            rational3(par_een[t][3], par_een[t][4], x, p2x, p2x1, p2x2);
-            rational3(par_een[t][5], par_een[t][6], z, q, q1, q2);
-            const T P = p1x * p2y + p1y * p2x;  // symmetrised in x and y
-            const T Px = p1x1 * p2y + p1y * p2x1, Py = p1x * p2y1 + p1y1 * p2x;
-            G += c * P * q;
-            if (deriv) {
-              Gx += c * Px * q;
-              Gy += c * Py * q;
-              Gz += c * P * q1;
-              Gxx += c * (p1x2 * p2y + p1y * p2x2) * q;
-              Gyy += c * (p1x * p2y2 + p1y2 * p2x) * q;
-              Gzz += c * P * q2;
-              Gxz += c * Px * q1;
-              Gyz += c * Py * q1;
-            }
-          }
-          J.add(G);
-          if (deriv) {
-            T ui[3], uj[3], u[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) { ui[d] = vi[d] * ix; uj[d] = vj[d] * iy; u[d] = vij[d] * iz; }
-            const T cij = ui[0] * u[0] + ui[1] * u[1] + ui[2] * u[2];
-            const T cji = uj[0] * u[0] + uj[1] * u[1] + uj[2] * u[2];
-            lap.add(Gxx + T(2) * Gx * ix + Gyy + T(2) * Gy * iy + T(2) * (Gzz + T(2) * Gz * iz) +
-                    T(2) * (Gxz * cij - Gyz * cji));
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              g[i][d] += Gx * ui[d] + Gz * u[d];
-              g[j][d] += Gy * uj[d] - Gz * u[d];
-            }
-          }
-        }
+  }
+}
+
+// Electron positions as kept in shared memory by k_jastrow_een: plain in
+// FP64, float pairs hi + lo (integer splitting only) in FP32.
+struct EenPosD {
+  double x[3];
+};
+struct EenPosF {
+  float h[3], l[3];
+};
+__device__ __forceinline__ EenPosD een_pos(const double* r, double) { return EenPosD{{r[0], r[1], r[2]}}; }
+__device__ __forceinline__ EenPosF een_pos(const double* r, float) {
+  EenPosF p;
+  for (int d = 0; d < 3; ++d) split_f64(r[d], p.h[d], p.l[d]);
+  return p;
+}
+__device__ __forceinline__ void een_diff(const EenPosD& a, const EenPosD& b, double* v) {
+  for (int d = 0; d < 3; ++d) v[d] = a.x[d] - b.x[d];
+}
+__device__ __forceinline__ void een_diff(const EenPosF& a, const EenPosF& b, float* v) {
+  for (int d = 0; d < 3; ++d) v[d] = (a.h[d] - b.h[d]) + (a.l[d] - b.l[d]);
+}
+
+// Electron-electron-nucleus Jastrow terms (App. D), added to the outputs of
+// the Jastrow stage.  Sixteen lanes per walker (N <= 16), kEenWalkers walkers
+// per block.
+//  1. lane e tabulates, for its electron and every atom a, the distance x =
+//     r_ae, its unit vector u_ae and, per term, f(a1, b1; x) and f(a2, b2; x)
+//     with their first two derivatives (f(a, b; r) = a r / (1 + b r));
+//  2. the unordered pairs (i < j) are dealt to the lanes; per pair the lane
+//     forms z = r_ij and the terms' f(a3, b3; z) once, and per atom the
+//     symmetrised kernel
+//       G(x, y, z) = (K_een(x, y, z) + K_een(y, x, z)) / 2,  x = r_ai, y = r_aj,
+//     from the tables, with both electrons' derivatives:
+//       grad_i += G_x u_ai + G_z u_ij,   grad_j += G_y u_aj - G_z u_ij,
+//       lap_i  += G_xx + 2 G_x / x + G_zz + 2 G_z / z + 2 G_xz (u_ai . u_ij),
+//       lap_j  += G_yy + 2 G_y / y + G_zz + 2 G_z / z - 2 G_yz (u_aj . u_ij),
+//       J      += G;
+//  3. lane e gathers its electron's pair terms in a fixed pair order
+//     (deterministic sums).  The electron's total gradient is grad J (Pade and
+//     electron-nucleus parts, already written) plus this part, so kinJ gains
+//     lap_e + 2 g0 . g + |g|^2; the lane sums of a walker are reduced by
+//     shuffles in a fixed order and added by one lane.
+constexpr int kEenWalkers = 4;
+constexpr int kEenMaxPairs = 120;  // 16 x 15 / 2
+
+// shared-memory layout of k_jastrow_een (dynamic part), in elements of T
+struct EenLayout {
+  int per_ea;    // values per (electron, atom): x, 1/x, u (3), then 6 per term
+  int per_walk;  // per walker: n x n_atom x per_ea
+  int pair_walk; // per walker: the pairs' two-sided terms, n (n - 1) / 2 x 8
+  __host__ __device__ EenLayout(int n, int n_atom, int n_een)
+      : per_ea(5 + 6 * n_een), per_walk(n * n_atom * per_ea), pair_walk(n * (n - 1) / 2 * 8) {}
+};
+template <typename T>
+size_t een_smem_bytes(const WfDev& wf) {
+  const EenLayout L(wf.n_elec, wf.n_atom, wf.n_een);
+  return sizeof(T) * (size_t)kEenWalkers * (L.per_walk + L.pair_walk);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(16 * kEenWalkers) k_jastrow_een(WfDev wf, const double* __restrict__ walkers,
+                                                                  int64_t W, int64_t ldw, T* __restrict__ gradJ,
+                                                                  double* __restrict__ jscal, int64_t ldm, bool deriv) {
+  using Pos = decltype(een_pos((const double*)nullptr, T(0)));
+  __shared__ Pos pos_s[kEenWalkers][16];
+  __shared__ Pos atom_s[QMC_MAX_ATOMS];
+  __shared__ T par_s[kMaxEen][7];
+  __shared__ unsigned char pair_i[kEenMaxPairs], pair_j[kEenMaxPairs], pair_of[16][16];
+  extern __shared__ __align__(16) unsigned char een_raw[];
+  const int n = wf.n_elec, na = wf.n_atom, nt = wf.n_een;
+  const EenLayout L(n, na, nt);
+  T* tab_all = reinterpret_cast<T*>(een_raw);                         // [kEenWalkers][per_walk]
+  T* contrib_all = tab_all + (size_t)kEenWalkers * L.per_walk;        // [kEenWalkers][pairs][2][4]
+  const T* par_src = std::is_same<T, double>::value ? reinterpret_cast<const T*>(&wf.jeen[0][0])
+                                                     : reinterpret_cast<const T*>(&wf.jeen_f[0][0]);
+  const int grp = threadIdx.x >> 4, lane = threadIdx.x & 15;
+  const int n_pairs = n * (n - 1) / 2;
+  const int64_t w = (int64_t)blockIdx.x * kEenWalkers + grp;
+  const bool wl = w < W;
+  T* tab = tab_all + (size_t)grp * L.per_walk;
+  T* contrib = contrib_all + (size_t)grp * L.pair_walk;
+  if (wl && lane < n) {
+    double r[3];
+    for (int d = 0; d < 3; ++d) r[d] = walkers[(int64_t)(3 * lane + d) * ldw + w];
+    pos_s[grp][lane] = een_pos(r, T(0));
+  }
+  if (threadIdx.x < na) atom_s[threadIdx.x] = een_pos(wf.atom_xyz[threadIdx.x], T(0));
+  for (int k = threadIdx.x; k < nt * 7; k += blockDim.x) par_s[k / 7][k % 7] = par_src[k];
+  if (threadIdx.x < n) {  // pair numbering: (0,1), (0,2), ..., (1,2), ...
+    const int i = threadIdx.x;
+    for (int j = i + 1; j < n; ++j) {
+      const int k = i * n - i * (i + 1) / 2 + (j - i - 1);
+      pair_i[k] = (unsigned char)i;
+      pair_j[k] = (unsigned char)j;
+      pair_of[i][j] = pair_of[j][i] = (unsigned char)k;
+    }
+  }
+  __syncthreads();
+  // ---- 1. electron-atom tables
+  if (wl && lane < n) {
+    const Pos pe = pos_s[grp][lane];
+    for (int a = 0; a < na; ++a) {
+      T v[3];
+      een_diff(pe, atom_s[a], v);
+      const T x2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+      const T ix = rsqrt_t(x2), x = x2 * ix;
+      T* e = tab + (lane * na + a) * L.per_ea;
+      e[0] = x;
+      e[1] = ix;
+      for (int d = 0; d < 3; ++d) e[2 + d] = v[d] * ix;
+      for (int t = 0; t < nt; ++t) {
+        rational3(par_s[t][1], par_s[t][2], x, e[5 + 6 * t], e[6 + 6 * t], e[7 + 6 * t]);
+        rational3(par_s[t][3], par_s[t][4], x, e[8 + 6 * t], e[9 + 6 * t], e[10 + 6 * t]);
       }
     }
+  }
+  __syncthreads();
+  // ---- 2. pairs
+  T jv = T(0);
+  if (wl) {
+    for (int k = lane; k < n_pairs; k += 16) {
+      const int i = pair_i[k], j = pair_j[k];
+      T vij[3];
+      een_diff(pos_s[grp][i], pos_s[grp][j], vij);
+      const T z2 = vij[0] * vij[0] + vij[1] * vij[1] + vij[2] * vij[2];
+      const T iz = rsqrt_t(z2), z = z2 * iz;
+      T u[3];
+      for (int d = 0; d < 3; ++d) u[d] = vij[d] * iz;
+      T ci[4] = {T(0), T(0), T(0), T(0)}, cj[4] = {T(0), T(0), T(0), T(0)};
+      T qz[kMaxEen][3];  // f(a3, b3; z) and its derivatives, per term
+#pragma unroll
+      for (int t = 0; t < kMaxEen; ++t)
+        if (t < nt) rational3(par_s[t][5], par_s[t][6], z, qz[t][0], qz[t][1], qz[t][2]);
+      for (int a = 0; a < na; ++a) {
+        const T* ei = tab + (i * na + a) * L.per_ea;
+        const T* ej = tab + (j * na + a) * L.per_ea;
+        T G = T(0), Gx = T(0), Gy = T(0), Gz = T(0), Gxx = T(0), Gyy = T(0), Gzz = T(0), Gxz = T(0), Gyz = T(0);
+#pragma unroll
+        for (int t = 0; t < kMaxEen; ++t) {
+          if (t >= nt) break;
+          const T q = qz[t][0], q1 = qz[t][1], q2 = qz[t][2];
+          const T c = T(0.5) * par_s[t][0];
+          const T* fi = ei + 5 + 6 * t;  // f1(x), f1', f1'', f2(x), f2', f2''
+          const T* fj = ej + 5 + 6 * t;  // the same at y
+          const T P = fi[0] * fj[3] + fj[0] * fi[3];  // symmetrised in x and y
+          const T Px = fi[1] * fj[3] + fj[0] * fi[4], Py = fi[0] * fj[4] + fj[1] * fi[3];
+          G += c * P * q;
+          if (deriv) {
+            Gx += c * Px * q;
+            Gy += c * Py * q;
+            Gz += c * P * q1;
+            Gxx += c * (fi[2] * fj[3] + fj[0] * fi[5]) * q;
+            Gyy += c * (fi[0] * fj[5] + fj[2] * fi[3]) * q;
+            Gzz += c * P * q2;
+            Gxz += c * Px * q1;
+            Gyz += c * Py * q1;
+          }
+        }
+        jv += G;
+        if (deriv) {
+          const T ix = ei[1], iy = ej[1];
+          const T cij = ei[2] * u[0] + ei[3] * u[1] + ei[4] * u[2];
+          const T cji = ej[2] * u[0] + ej[3] * u[1] + ej[4] * u[2];
+          for (int d = 0; d < 3; ++d) {
+            ci[d] += Gx * ei[2 + d] + Gz * u[d];
+            cj[d] += Gy * ej[2 + d] - Gz * u[d];
+          }
+          ci[3] += Gxx + T(2) * Gx * ix + Gzz + T(2) * Gz * iz + T(2) * Gxz * cij;
+          cj[3] += Gyy + T(2) * Gy * iy + Gzz + T(2) * Gz * iz - T(2) * Gyz * cji;
+        }
+      }
+      if (deriv)
+        for (int q = 0; q < 4; ++q) {
+          contrib[k * 8 + q] = ci[q];
+          contrib[k * 8 + 4 + q] = cj[q];
+        }
+    }
+  }
+  __syncthreads();
+  // ---- 3. per-electron gather
+  T corr = T(0);
+  if (deriv && wl && lane < n) {
+    const int e = lane;
+    T g[4] = {T(0), T(0), T(0), T(0)};
+    for (int o = 0; o < n; ++o) {
+      if (o == e) continue;
+      const int k = pair_of[e][o], side = e < o ? 0 : 4;
+      for (int q = 0; q < 4; ++q) g[q] += contrib[k * 8 + side + q];
+    }
+    T* g0p = gradJ + (int64_t)(3 * e) * ldm + w;
+    const T g0x = g0p[0], g0y = g0p[ldm], g0z = g0p[2 * ldm];
+    g0p[0] = g0x + g[0];
+    g0p[ldm] = g0y + g[1];
+    g0p[2 * ldm] = g0z + g[2];
+    corr = g[3] + T(2) * (g0x * g[0] + g0y * g[1] + g0z * g[2]) + (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    jv += __shfl_xor_sync(0xffffffffu, jv, o);
+    corr += __shfl_xor_sync(0xffffffffu, corr, o);
+  }
+  if (lane == 0 && wl) {
+    jscal[w] += widen(jv);
+    if (deriv) jscal[ldm + w] += widen(corr);
   }
 }
 
@@ -191,10 +346,7 @@ __global__ void __launch_bounds__(128) k_jastrow_f64(WfDev wf, const double* __r
     auto disp_en = [&](int i, int a, double* v) {
       for (int d = 0; d < 3; ++d) v[d] = r[i][d] - wf.atom_xyz[a][d];
     };
-    auto disp_ee = [&](int i, int j, double* v) {
-      for (int d = 0; d < 3; ++d) v[d] = r[i][d] - r[j][d];
-    };
-    manybody_terms<double, NMAX>(wf, wf.jen, wf.jeen, n, disp_en, disp_ee, Jm, lm, g, deriv);
+    en_terms<double, NMAX>(wf, wf.jen, n, disp_en, Jm, lm, g, deriv);
     J += Jm.s;
     lap += lm.s;
   }
@@ -292,10 +444,7 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
         v[d] = (rh[i][d] - ah) + (rl[i][d] - al);
       }
     };
-    auto disp_ee = [&](int i, int j, float* v) {
-      for (int d = 0; d < 3; ++d) v[d] = (rh[i][d] - rh[j][d]) + (rl[i][d] - rl[j][d]);
-    };
-    manybody_terms<float, NMAX>(wf, wf.jen_f, wf.jeen_f, n, disp_en, disp_ee, J, lap, g, deriv);
+    en_terms<float, NMAX>(wf, wf.jen_f, n, disp_en, J, lap, g, deriv);
   }
   if (deriv) {
 #pragma unroll

@@ -231,6 +231,8 @@ cudaError_t launch_grad(const WfDev& wf, const double* walkers, int64_t W, int64
                         double* grad, cudaStream_t st);
 
 // kernel launchers (return cudaError_t of the launch)
+// dynamic shared memory of the electron-electron-nucleus Jastrow kernel
+size_t een_shared_bytes(const WfDev& wf, bool fp64);
 cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
                            const Workspace& ws, bool derivs, cudaStream_t st);
 cudaError_t launch_ao_mo_simt(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
