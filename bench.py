@@ -39,7 +39,7 @@ WORKLOAD = "CO 14e- 58 GTO 14 MO 100 det, 262144 walkers"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)
 # DRAM bytes (read + write) per walker of the mixed-form k_det launch, from an ncu capture of that
 # kernel on 131,072 CO walkers (242.8 MB); set to None whenever the kernel changes.
-DET_TRAFFIC_BYTES_PER_WALKER = 422.433024e6 / 131072  # ncu dram read+write of k_det (131,072 walkers)
+DET_TRAFFIC_BYTES_PER_WALKER = (414.390016e6 + 5.340672e6) / 131072  # ncu dram read+write of k_det (131,072 walkers)
 
 
 def det_stage_flops(mol) -> float:
@@ -348,6 +348,9 @@ def main():
                     help="requests of the Poisson serving run (0 = skip the serving measurement)")
     ap.add_argument("--no-serving-fp64", action="store_true", help="serve the mix in the mixed form only")
     ap.add_argument("--no-det-sweep", action="store_true", help="skip the explicit-versus-table sweep")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the other molecules' measurements")
+    ap.add_argument("--manybody-jastrow", action="store_true",
+                    help="time CO with the many-body Jastrow of App. D (K_en + 5 K_een terms) instead")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -380,7 +383,7 @@ def main():
     def max_over_ranks(v: float) -> float:
         return reduce_max(v, dist)
 
-    mol = qi.make_co()
+    mol = qi.with_manybody_jastrow(qi.make_co()) if args.manybody_jastrow else qi.make_co()
     W = args.walkers
     r = qi.walkers(mol, W, seed=rank_walker_seed(rank))
     soa = np.ascontiguousarray(qi.to_soa(r))
@@ -459,7 +462,7 @@ def main():
     mh_steps_per_s = world * W * n_mh / (max_over_ranks(a.elapsed_time(b)) / 1e3)
     del xs
 
-    secondary = run_secondary(local, stream, barrier, flush) if world == 1 else None
+    secondary = run_secondary(local, stream, barrier, flush) if world == 1 and not args.no_secondary else None
     det_sweep = run_det_sweep(local, stream, barrier, flush) if world == 1 and not args.no_det_sweep else None
 
     serving_out = None
@@ -480,7 +483,9 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 AO / tf32x3 MMA / f64 det", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "walkers_per_gpu": W, "precision": "mixed_tf32",
+        "config": {"workload": (WORKLOAD.replace("262144 walkers", f"{W} walkers")
+                                + (" + many-body Jastrow (K_en, 5 K_een terms)" if args.manybody_jastrow else "")),
+                   "walkers_per_gpu": W, "precision": "mixed_tf32",
                    "l2": "flushed (256 MB write) between timed steps, outside the timed events",
                    "parallelism": f"walker shards x{world}, no data-path collective"},
         "fp64_plain": {"value": value_fp64, "ms_per_step": tot_fp64 / k64,
@@ -493,7 +498,8 @@ def main():
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(soa.nbytes),
                 "d2h_bytes_per_step": int(2 * 8 * W), "api": "qmc_local_energy_host (pinned host buffers)"},
-        "gpu_launches": 3 * args.steps,
+        # per E_L: Jastrow (+ e-e-n kernel with the many-body Jastrow), AO->MO, determinants
+        "gpu_launches": (4 if args.manybody_jastrow else 3) * args.steps,
         "clocks": clocks,
         "p99_request_latency_ms": None if serving_out is None else serving_out["mixed"]["p99_ms"],
         "metropolis_walker_steps_per_s": mh_steps_per_s,

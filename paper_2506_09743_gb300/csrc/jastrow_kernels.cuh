@@ -126,10 +126,16 @@ constexpr int kEenMaxPairs = 120;  // 16 x 15 / 2
 // shared-memory layout of k_jastrow_een (dynamic part), in elements of T
 struct EenLayout {
   int per_ea;    // values per (electron, atom): x, 1/x, u (3), then 6 per term
-  int per_walk;  // per walker: n x n_atom x per_ea
-  int pair_walk; // per walker: the pairs' two-sided terms, n (n - 1) / 2 x 8
+  int per_walk;  // per walker: n x n_atom x per_ea, made odd so that the two
+                 // walkers of a warp read opposite bank parities
+  int np_pad;    // pair stride of the two-sided pair terms, = 2 (mod 4): the
+                 // two walkers of a warp write opposite halves of the banks
+  int pair_walk; // per walker: 8 x np_pad (value-major [8][np_pad])
   __host__ __device__ EenLayout(int n, int n_atom, int n_een)
-      : per_ea(5 + 6 * n_een), per_walk(n * n_atom * per_ea), pair_walk(n * (n - 1) / 2 * 8) {}
+      : per_ea(5 + 6 * n_een),
+        per_walk((n * n_atom * per_ea) | 1),
+        np_pad(((n * (n - 1) / 2 + 1) / 4) * 4 + 2),
+        pair_walk(8 * np_pad) {}
 };
 template <typename T>
 size_t een_smem_bytes(const WfDev& wf) {
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(16 * kEenWalkers) k_jastrow_een(WfDev wf, cons
   const int n = wf.n_elec, na = wf.n_atom, nt = wf.n_een;
   const EenLayout L(n, na, nt);
   T* tab_all = reinterpret_cast<T*>(een_raw);                         // [kEenWalkers][per_walk]
-  T* contrib_all = tab_all + (size_t)kEenWalkers * L.per_walk;        // [kEenWalkers][pairs][2][4]
+  T* contrib_all = tab_all + (size_t)kEenWalkers * L.per_walk;        // [kEenWalkers][2][4][np_pad]
   const T* par_src = std::is_same<T, double>::value ? reinterpret_cast<const T*>(&wf.jeen[0][0])
                                                      : reinterpret_cast<const T*>(&wf.jeen_f[0][0]);
   const int grp = threadIdx.x >> 4, lane = threadIdx.x & 15;
@@ -251,8 +257,8 @@ __global__ void __launch_bounds__(16 * kEenWalkers) k_jastrow_een(WfDev wf, cons
       }
       if (deriv)
         for (int q = 0; q < 4; ++q) {
-          contrib[k * 8 + q] = ci[q];
-          contrib[k * 8 + 4 + q] = cj[q];
+          contrib[q * L.np_pad + k] = ci[q];
+          contrib[(4 + q) * L.np_pad + k] = cj[q];
         }
     }
   }
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(16 * kEenWalkers) k_jastrow_een(WfDev wf, cons
     for (int o = 0; o < n; ++o) {
       if (o == e) continue;
       const int k = pair_of[e][o], side = e < o ? 0 : 4;
-      for (int q = 0; q < 4; ++q) g[q] += contrib[k * 8 + side + q];
+      for (int q = 0; q < 4; ++q) g[q] += contrib[(side + q) * L.np_pad + k];
     }
     T* g0p = gradJ + (int64_t)(3 * e) * ldm + w;
     const T g0x = g0p[0], g0y = g0p[ldm], g0z = g0p[2 * ldm];
