@@ -123,20 +123,45 @@ __device__ __forceinline__ void een_diff(const EenPosF& a, const EenPosF& b, flo
 constexpr int kEenWalkers = 4;
 constexpr int kEenMaxPairs = 120;  // 16 x 15 / 2
 
-// shared-memory layout of k_jastrow_een (dynamic part), in elements of T
+// shared-memory layout of k_jastrow_een (dynamic part), in elements of T.
+// The tables are read as two-element vectors; their electron stride is 2
+// (mod 4) elements, so that the 16 lanes of a walker reading 16 different
+// electrons hit distinct banks.
 struct EenLayout {
-  int per_ea;    // values per (electron, atom): x, 1/x, u (3), then 6 per term
-  int per_walk;  // per walker: n x n_atom x per_ea, made odd so that the two
-                 // walkers of a warp read opposite bank parities
+  int per_ea;    // values per (electron, atom): x, 1/x, u (3), a pad, then 6 per term
+  int per_e;     // per electron: n_atom x per_ea, rounded up to 2 (mod 4)
+  int per_walk;  // per walker: n x per_e
   int np_pad;    // pair stride of the two-sided pair terms, = 2 (mod 4): the
                  // two walkers of a warp write opposite halves of the banks
   int pair_walk; // per walker: 8 x np_pad (value-major [8][np_pad])
   __host__ __device__ EenLayout(int n, int n_atom, int n_een)
-      : per_ea(5 + 6 * n_een),
-        per_walk((n * n_atom * per_ea) | 1),
+      : per_ea(6 + 6 * n_een),
+        per_e(n_atom * per_ea + ((n_atom * per_ea) % 4 == 0 ? 2 : 0)),
+        per_walk(n * per_e),
         np_pad(((n * (n - 1) / 2 + 1) / 4) * 4 + 2),
         pair_walk(8 * np_pad) {}
 };
+
+// 2 K consecutive table values as K two-element vector loads (p is aligned to
+// two elements)
+template <int K>
+__device__ __forceinline__ void ld_vec2(const float* p, float* v) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float2 q = reinterpret_cast<const float2*>(p)[k];
+    v[2 * k] = q.x;
+    v[2 * k + 1] = q.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void ld_vec2(const double* p, double* v) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double2 q = reinterpret_cast<const double2*>(p)[k];
+    v[2 * k] = q.x;
+    v[2 * k + 1] = q.y;
+  }
+}
 template <typename T>
 size_t een_smem_bytes(const WfDev& wf) {
   const EenLayout L(wf.n_elec, wf.n_atom, wf.n_een);
@@ -190,13 +215,14 @@ __global__ void __launch_bounds__(16 * kEenWalkers) k_jastrow_een(WfDev wf, cons
       een_diff(pe, atom_s[a], v);
       const T x2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
       const T ix = rsqrt_t(x2), x = x2 * ix;
-      T* e = tab + (lane * na + a) * L.per_ea;
+      T* e = tab + lane * L.per_e + a * L.per_ea;
       e[0] = x;
       e[1] = ix;
       for (int d = 0; d < 3; ++d) e[2 + d] = v[d] * ix;
+      e[5] = T(0);
       for (int t = 0; t < nt; ++t) {
-        rational3(par_s[t][1], par_s[t][2], x, e[5 + 6 * t], e[6 + 6 * t], e[7 + 6 * t]);
-        rational3(par_s[t][3], par_s[t][4], x, e[8 + 6 * t], e[9 + 6 * t], e[10 + 6 * t]);
+        rational3(par_s[t][1], par_s[t][2], x, e[6 + 6 * t], e[7 + 6 * t], e[8 + 6 * t]);
+        rational3(par_s[t][3], par_s[t][4], x, e[9 + 6 * t], e[10 + 6 * t], e[11 + 6 * t]);
       }
     }
   }
@@ -213,43 +239,52 @@ __global__ void __launch_bounds__(16 * kEenWalkers) k_jastrow_een(WfDev wf, cons
       T u[3];
       for (int d = 0; d < 3; ++d) u[d] = vij[d] * iz;
       T ci[4] = {T(0), T(0), T(0), T(0)}, cj[4] = {T(0), T(0), T(0), T(0)};
-      T qz[kMaxEen][3];  // f(a3, b3; z) and its derivatives, per term
+      T qz[kMaxEen][3];  // c / 2 times f(a3, b3; z) and its derivatives, per term
 #pragma unroll
       for (int t = 0; t < kMaxEen; ++t)
-        if (t < nt) rational3(par_s[t][5], par_s[t][6], z, qz[t][0], qz[t][1], qz[t][2]);
+        if (t < nt) {
+          rational3(par_s[t][5], par_s[t][6], z, qz[t][0], qz[t][1], qz[t][2]);
+          const T c = T(0.5) * par_s[t][0];
+          qz[t][0] *= c;
+          qz[t][1] *= c;
+          qz[t][2] *= c;
+        }
       for (int a = 0; a < na; ++a) {
-        const T* ei = tab + (i * na + a) * L.per_ea;
-        const T* ej = tab + (j * na + a) * L.per_ea;
+        const T* ei = tab + i * L.per_e + a * L.per_ea;
+        const T* ej = tab + j * L.per_e + a * L.per_ea;
         T G = T(0), Gx = T(0), Gy = T(0), Gz = T(0), Gxx = T(0), Gyy = T(0), Gzz = T(0), Gxz = T(0), Gyz = T(0);
 #pragma unroll
         for (int t = 0; t < kMaxEen; ++t) {
           if (t >= nt) break;
           const T q = qz[t][0], q1 = qz[t][1], q2 = qz[t][2];
-          const T c = T(0.5) * par_s[t][0];
-          const T* fi = ei + 5 + 6 * t;  // f1(x), f1', f1'', f2(x), f2', f2''
-          const T* fj = ej + 5 + 6 * t;  // the same at y
+          T fi[6], fj[6];  // f1(x), f1', f1'', f2(x), f2', f2''; the same at y
+          ld_vec2<3>(ei + 6 + 6 * t, fi);
+          ld_vec2<3>(ej + 6 + 6 * t, fj);
           const T P = fi[0] * fj[3] + fj[0] * fi[3];  // symmetrised in x and y
           const T Px = fi[1] * fj[3] + fj[0] * fi[4], Py = fi[0] * fj[4] + fj[1] * fi[3];
-          G += c * P * q;
+          G += P * q;
           if (deriv) {
-            Gx += c * Px * q;
-            Gy += c * Py * q;
-            Gz += c * P * q1;
-            Gxx += c * (fi[2] * fj[3] + fj[0] * fi[5]) * q;
-            Gyy += c * (fi[0] * fj[5] + fj[2] * fi[3]) * q;
-            Gzz += c * P * q2;
-            Gxz += c * Px * q1;
-            Gyz += c * Py * q1;
+            Gx += Px * q;
+            Gy += Py * q;
+            Gz += P * q1;
+            Gxx += (fi[2] * fj[3] + fj[0] * fi[5]) * q;
+            Gyy += (fi[0] * fj[5] + fj[2] * fi[3]) * q;
+            Gzz += P * q2;
+            Gxz += Px * q1;
+            Gyz += Py * q1;
           }
         }
         jv += G;
         if (deriv) {
-          const T ix = ei[1], iy = ej[1];
-          const T cij = ei[2] * u[0] + ei[3] * u[1] + ei[4] * u[2];
-          const T cji = ej[2] * u[0] + ej[3] * u[1] + ej[4] * u[2];
+          T hi[6], hj[6];  // x, 1/x, u (3), pad
+          ld_vec2<3>(ei, hi);
+          ld_vec2<3>(ej, hj);
+          const T ix = hi[1], iy = hj[1];
+          const T cij = hi[2] * u[0] + hi[3] * u[1] + hi[4] * u[2];
+          const T cji = hj[2] * u[0] + hj[3] * u[1] + hj[4] * u[2];
           for (int d = 0; d < 3; ++d) {
-            ci[d] += Gx * ei[2 + d] + Gz * u[d];
-            cj[d] += Gy * ej[2 + d] - Gz * u[d];
+            ci[d] += Gx * hi[2 + d] + Gz * u[d];
+            cj[d] += Gy * hj[2 + d] - Gz * u[d];
           }
           ci[3] += Gxx + T(2) * Gx * ix + Gzz + T(2) * Gz * iz + T(2) * Gxz * cij;
           cj[3] += Gyy + T(2) * Gy * iy + Gzz + T(2) * Gz * iz - T(2) * Gyz * cji;
