@@ -162,10 +162,15 @@ qmc_status qmc_local_energy(qmc_wf* wf, const double* walkers, int64_t n_walkers
                             double* e_loc, double* log_psi, void* workspace, size_t workspace_bytes,
                             void* stream);
 
-/* As qmc_local_energy with HOST buffers: copies the walkers to library-owned
- * device memory, evaluates, and copies e_loc (and log_psi if not NULL) back;
- * returns after the results are on the host.  walkers: host [3N][n_walkers]
- * (ldw = n_walkers); host buffers should be pinned for full speed. */
+/* As qmc_local_energy with HOST buffers: evaluates into library-owned device
+ * memory and copies e_loc (and log_psi if not NULL) back; returns after the
+ * results are on the host.  walkers: host [3N][n_walkers] (ldw = n_walkers).
+ * Page-locked walkers mapped into the wavefunction's device (as
+ * cudaHostAlloc / torch pin_memory give them) are read by the first kernel
+ * directly and copied to device memory on the way; other host memory is
+ * uploaded with one copy before it (backflow wavefunctions always take the
+ * copy).  Results are identical either way.  Host buffers should be pinned
+ * for full speed. */
 qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_walkers,
                                  double* e_loc, double* log_psi, void* stream);
 
@@ -258,9 +263,13 @@ qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[
  * een: host [n_een][7] (c, a1, b1, a2, b2, a3, b3), n_een <= 8 (0 = none).
  * Requires w2 >= 0 and b >= 0 (no pole at r >= 0): QMC_ERR_ARG otherwise.
  * Covers qmc_local_energy* and qmc_sample in every precision form;
- * QMC_ERR_UNSUPPORTED with backflow, and qmc_energy_grad / qmc_optimize
- * refuse a wavefunction that has it (its parameters are not in the gradient
- * layout).  Synchronous (rebuilds the device tables). */
+ * QMC_ERR_UNSUPPORTED with backflow, or when the electron-electron-nucleus
+ * tables (per walker: n_elec x n_atom x (6 + 6 n_een) values plus
+ * 8 x n_elec (n_elec - 1) / 2 pair terms, four walkers per block) exceed the
+ * 227 KB of shared memory of a block; qmc_energy_grad / qmc_optimize refuse a
+ * wavefunction that has it (its parameters are not in the gradient layout).
+ * On error the previous Jastrow stays.  Synchronous (rebuilds the device
+ * tables). */
 qmc_status qmc_set_manybody_jastrow(qmc_wf* wf, const double* en, int32_t n_een, const double* een);
 
 /* Determinant method of the local-energy and sampling calls.

@@ -600,8 +600,14 @@ static void mark(qmc_wf* wf, int k, cudaStream_t st) {
 // measured slower on CO: a determinant block sharing an SM keeps half of its
 // warps and loses more FP64 throughput than the overlap gains.)  Backflow
 // wavefunctions run the general FP64 kernel.
+//
+// mapped: null, or walkers [3N][ldw] in mapped host memory.  Then `stage` is a
+// device buffer of the same shape: the Jastrow kernel reads the positions
+// over the host link once and writes them there, and the later stages read
+// the device copy (the upload overlaps the Jastrow stage's arithmetic).
 static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
-                            int* err_flag, bool kinetic, double* e_loc, double* log_psi, cudaStream_t st) {
+                            int* err_flag, bool kinetic, double* e_loc, double* log_psi, cudaStream_t st,
+                            const double* mapped = nullptr, double* stage = nullptr) {
   const WfDev& d = wf->dev;
   if (d.bf_w != 0.0) {  // backflow: one general kernel (Jastrow, orbitals, Eq. nabla_d, E_L)
     mark(wf, 0, st);
@@ -619,8 +625,11 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   }
   const Workspace& v = ws;
   mark(wf, 0, st);
-  qmc_status s = launch_status(launch_jastrow(d, wf->precision, walkers, W, ldw, v, kinetic, st), "jastrow");
+  qmc_status s = launch_status(
+      launch_jastrow(d, wf->precision, mapped ? mapped : walkers, W, ldw, mapped ? stage : nullptr, v, kinetic, st),
+      "jastrow");
   if (s) return s;
+  if (mapped) walkers = stage;
   mark(wf, 1, st);
   mark(wf, 2, st);
   s = launch_status(tc ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag, st)
@@ -666,31 +675,48 @@ qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_wa
   const int64_t W = n_walkers;
   const size_t in_bytes = sizeof(double) * 3 * wf->dev.n_elec * W;
   const size_t need = align256(in_bytes) + 2 * align256(sizeof(double) * W);
-  double *d_in, *d_e, *d_lp;
-  {
-    std::lock_guard<std::mutex> lock(wf->mu);
-    DeviceGuard guard(wf->device);
-    if (wf->stage_bytes < need) {
-      if (wf->stage) cudaFree(wf->stage);
-      wf->stage = nullptr;
-      wf->stage_bytes = 0;
-      cudaError_t e = cudaMalloc(&wf->stage, need);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(QMC_ERR_OOM, std::string("staging allocation: ") + cudaGetErrorString(e));
-      }
-      wf->stage_bytes = need;
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  if (wf->stage_bytes < need) {
+    if (wf->stage) cudaFree(wf->stage);
+    wf->stage = nullptr;
+    wf->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&wf->stage, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QMC_ERR_OOM, std::string("staging allocation: ") + cudaGetErrorString(e));
     }
-    char* p = reinterpret_cast<char*>(wf->stage);
-    d_in = reinterpret_cast<double*>(p);
-    d_e = reinterpret_cast<double*>(p + align256(in_bytes));
-    d_lp = reinterpret_cast<double*>(p + align256(in_bytes) + align256(sizeof(double) * W));
+    wf->stage_bytes = need;
+  }
+  char* p = reinterpret_cast<char*>(wf->stage);
+  double* d_in = reinterpret_cast<double*>(p);
+  double* d_e = reinterpret_cast<double*>(p + align256(in_bytes));
+  double* d_lp = reinterpret_cast<double*>(p + align256(in_bytes) + align256(sizeof(double) * W));
+  // Page-locked host walkers that the runtime maps into this device's address
+  // space are read by the first kernel directly (one pass over the host link,
+  // overlapped with its arithmetic); any other host memory is uploaded first.
+  // Backflow wavefunctions run one general kernel and always take the upload.
+  const double* mapped = nullptr;
+  if (wf->dev.bf_w == 0.0) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, walkers) == cudaSuccess) {
+      if (pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr && pa.device == wf->device)
+        mapped = static_cast<const double*>(pa.devicePointer);
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (!mapped) {
     cudaError_t e = cudaMemcpyAsync(d_in, walkers, in_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "walker upload");
   }
-  qmc_status s = qmc_local_energy(wf, d_in, W, W, d_e, log_psi ? d_lp : nullptr, nullptr, 0, stream);
+  void* base;
+  qmc_status s = get_workspace(wf, W, nullptr, 0, &base);
   if (s) return s;
-  DeviceGuard guard(wf->device);
+  int* err_flag;
+  Workspace ws = carve(wf, base, W, &err_flag);
+  s = eval_path(wf, d_in, W, W, ws, err_flag, true, d_e, log_psi ? d_lp : nullptr, st, mapped, d_in);
+  if (s) return s;
   cudaError_t e = cudaMemcpyAsync(e_loc, d_e, sizeof(double) * W, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && log_psi) e = cudaMemcpyAsync(log_psi, d_lp, sizeof(double) * W, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -333,8 +333,9 @@ struct PlainD {
 
 template <int NMAX, bool MB>
 __global__ void __launch_bounds__(128) k_jastrow_f64(WfDev wf, const double* __restrict__ walkers, int64_t W,
-                                                     int64_t ldw, double* __restrict__ gradJ,
-                                                     double* __restrict__ jscal, int64_t ldm, bool deriv) {
+                                                     int64_t ldw, double* __restrict__ copy,
+                                                     double* __restrict__ gradJ, double* __restrict__ jscal,
+                                                     int64_t ldm, bool deriv) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= W) return;
   const int n = wf.n_elec;
@@ -344,6 +345,7 @@ __global__ void __launch_bounds__(128) k_jastrow_f64(WfDev wf, const double* __r
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       r[i][d] = (i < n) ? walkers[(int64_t)(3 * i + d) * ldw + w] : 0.0;
+      if (copy && i < n) copy[(int64_t)(3 * i + d) * ldw + w] = r[i][d];
       g[i][d] = 0.0;
     }
   double J = 0.0, lap = 0.0, V = wf.vnn;
@@ -421,9 +423,9 @@ struct KahanF {
 
 template <int NMAX, bool MB>
 __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __restrict__ walkers, int64_t W,
-                                                     int64_t ldw, float* __restrict__ gradJ,
-                                                     double* __restrict__ jscal, int64_t ldm, float b, float w0p,
-                                                     float w0a, bool deriv) {
+                                                     int64_t ldw, double* __restrict__ copy,
+                                                     float* __restrict__ gradJ, double* __restrict__ jscal,
+                                                     int64_t ldm, float b, float w0p, float w0a, bool deriv) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= W) return;
   const int n = wf.n_elec;
@@ -432,8 +434,14 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
   for (int i = 0; i < NMAX; ++i)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      if (i < n) split_f64(walkers[(int64_t)(3 * i + d) * ldw + w], rh[i][d], rl[i][d]);
-      else { rh[i][d] = 0.f; rl[i][d] = 0.f; }
+      if (i < n) {
+        const double v = walkers[(int64_t)(3 * i + d) * ldw + w];
+        if (copy) copy[(int64_t)(3 * i + d) * ldw + w] = v;
+        split_f64(v, rh[i][d], rl[i][d]);
+      } else {
+        rh[i][d] = 0.f;
+        rl[i][d] = 0.f;
+      }
       g[i][d] = 0.f;
     }
   KahanF J, V, lap;
@@ -502,17 +510,20 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
   jscal[2 * ldm + w] = V.value() + wf.vnn;
 }
 
-// Launch one kernel instance; NM is the electron-count bracket.
+// Launch one kernel instance; NM is the electron-count bracket.  If copy is
+// not null the kernel also writes the positions it reads there (same layout):
+// walkers may then be mapped host memory, read once over the host link, and
+// the later stages read the device copy.
 template <int NM, bool MB>
 cudaError_t launch_jastrow_nm(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
-                              const Workspace& ws, bool derivs, cudaStream_t st) {
+                              double* copy, const Workspace& ws, bool derivs, cudaStream_t st) {
   const dim3 block(128), grid((unsigned)((W + 127) / 128));
   if (prec == QMC_FP64)
-    k_jastrow_f64<NM, MB><<<grid, block, 0, st>>>(wf, walkers, W, ldw, static_cast<double*>(ws.gradJ), ws.jscal,
-                                                  ws.ldm, derivs);
+    k_jastrow_f64<NM, MB><<<grid, block, 0, st>>>(wf, walkers, W, ldw, copy, static_cast<double*>(ws.gradJ),
+                                                  ws.jscal, ws.ldm, derivs);
   else
-    k_jastrow_f32<NM, MB><<<grid, block, 0, st>>>(wf, walkers, W, ldw, static_cast<float*>(ws.gradJ), ws.jscal,
-                                                  ws.ldm, wf.jb_f, wf.w0p_f, wf.w0a_f, derivs);
+    k_jastrow_f32<NM, MB><<<grid, block, 0, st>>>(wf, walkers, W, ldw, copy, static_cast<float*>(ws.gradJ),
+                                                  ws.jscal, ws.ldm, wf.jb_f, wf.w0p_f, wf.w0a_f, derivs);
   return cudaGetLastError();
 }
 

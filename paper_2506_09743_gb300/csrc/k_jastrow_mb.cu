@@ -9,16 +9,18 @@ size_t een_shared_bytes(const WfDev& wf, bool fp64) {
 }
 
 cudaError_t launch_jastrow_mb(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
-                              const Workspace& ws, bool derivs, cudaStream_t st) {
+                              double* copy, const Workspace& ws, bool derivs, cudaStream_t st) {
   const int n = wf.n_elec;
   cudaError_t e;
-  if (n <= 2) e = launch_jastrow_nm<2, true>(wf, prec, walkers, W, ldw, ws, derivs, st);
-  else if (n <= 4) e = launch_jastrow_nm<4, true>(wf, prec, walkers, W, ldw, ws, derivs, st);
-  else if (n <= 8) e = launch_jastrow_nm<8, true>(wf, prec, walkers, W, ldw, ws, derivs, st);
-  else if (n <= 16) e = launch_jastrow_nm<16, true>(wf, prec, walkers, W, ldw, ws, derivs, st);
+  if (n <= 2) e = launch_jastrow_nm<2, true>(wf, prec, walkers, W, ldw, copy, ws, derivs, st);
+  else if (n <= 4) e = launch_jastrow_nm<4, true>(wf, prec, walkers, W, ldw, copy, ws, derivs, st);
+  else if (n <= 8) e = launch_jastrow_nm<8, true>(wf, prec, walkers, W, ldw, copy, ws, derivs, st);
+  else if (n <= 16) e = launch_jastrow_nm<16, true>(wf, prec, walkers, W, ldw, copy, ws, derivs, st);
   else return cudaErrorInvalidValue;
   if (e != cudaSuccess || wf.n_een == 0) return e;
-  // electron-electron-nucleus terms: 16 lanes per walker, kEenWalkers walkers per block
+  // electron-electron-nucleus terms: 16 lanes per walker, kEenWalkers walkers
+  // per block; they read the device copy when the first kernel made one
+  if (copy) walkers = copy;
   const unsigned grid = (unsigned)((W + kEenWalkers - 1) / kEenWalkers);
   if (prec == QMC_FP64) {
     const size_t smem = een_smem_bytes<double>(wf);

@@ -233,7 +233,9 @@ cudaError_t launch_grad(const WfDev& wf, const double* walkers, int64_t W, int64
 // kernel launchers (return cudaError_t of the launch)
 // dynamic shared memory of the electron-electron-nucleus Jastrow kernel
 size_t een_shared_bytes(const WfDev& wf, bool fp64);
-cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
+// copy: null, or a device buffer [3N][ldw] that receives the positions read
+// from walkers (which may then be mapped host memory; later stages read copy)
+cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw, double* copy,
                            const Workspace& ws, bool derivs, cudaStream_t st);
 cudaError_t launch_ao_mo_simt(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
                               const Workspace& ws, int nch, cudaStream_t st);

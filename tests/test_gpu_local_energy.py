@@ -196,6 +196,40 @@ def test_manybody_jastrow_scope(pkg):
         pkg.Wavefunction(qi.with_manybody_jastrow(qi.make_li2()), precision="fp64")
 
 
+def _h_chain(n_atom, n_terms):
+    """Linear H chain, one 1s STO per atom, n_atom electrons, with the
+    many-body Jastrow of n_terms e-e-n terms."""
+    bb = qi._BasisBuilder()
+    for a in range(n_atom):
+        bb.add(a, qi.STO, 0, 0, 0, 0, [1.1], [1.0])
+    xyz = np.zeros((n_atom, 3))
+    xyz[:, 2] = 1.6 * (np.arange(n_atom) - (n_atom - 1) / 2)
+    z = np.ones(n_atom)
+    nu = n_atom // 2
+    mo = qi.random_orthonormal(n_atom, nu, np.random.default_rng(3))
+    mol = qi.Molecule(name=f"h{n_atom}", atom_xyz=xyz, atom_z=z, n_up=nu, n_down=n_atom - nu, **bb.arrays(),
+                      mo_coeff=mo, det_weight=np.ones(1),
+                      det_exc=qi._dets_array([(qi.ground_exc(), qi.ground_exc())]),
+                      electron_home=qi.electron_homes(z, nu, n_atom - nu))
+    return qi.with_manybody_jastrow(mol, n_terms=n_terms)
+
+
+def test_manybody_een_shared_memory_limit(pkg):
+    """The e-e-n tables of 12 electrons x 12 atoms x 8 terms need 266 KB per
+    block in FP64 (refused) and 133 KB in FP32 (accepted)."""
+    from paper_2506_09743_gb300 import QmcError
+
+    mol = _h_chain(12, 8)
+    with pytest.raises(QmcError):
+        pkg.Wavefunction(mol, precision="fp64")
+    wf = pkg.Wavefunction(mol, precision="mixed_tf32")
+    r = qi.walkers(mol, 300, seed=6)
+    e, _ = wf.local_energy(torch.tensor(qi.to_soa(r), device="cuda"))
+    wf.close()
+    E_ref, _, sens = oracle_reference(mol, r)
+    mixed_check(e.cpu().numpy(), E_ref, sens)
+
+
 def test_closed_forms_on_gpu(pkg):
     mol = qi.make_hydrogenic(1.0, 1.0)
     r = qi.walkers(mol, 333, seed=4)
@@ -285,18 +319,50 @@ def test_set_params_rebuilds_every_table(pkg, precision):
     fresh.close()
 
 
-@pytest.mark.parametrize("W", [500, 70001])
-def test_host_entry_point_matches_device(pkg, W):
+def _host_buffers(soa, W, pinned):
+    """(walkers, e_loc, log_psi) host arrays, page-locked or pageable."""
+    if not pinned:
+        return soa, np.empty(W), np.empty(W)
+    bufs = [torch.from_numpy(soa).pin_memory(), torch.empty(W, dtype=torch.float64).pin_memory(),
+            torch.empty(W, dtype=torch.float64).pin_memory()]
+    return tuple(b.numpy() for b in bufs)
+
+
+@pytest.mark.parametrize("W,pinned", [(500, False), (70001, False), (500, True), (70001, True)])
+def test_host_entry_point_matches_device(pkg, W, pinned):
     """The host-buffer entry point gives the device call's results bit for
-    bit."""
+    bit, from pageable host memory (uploaded before the first kernel) and
+    from page-locked memory (read by the first kernel over the host link)."""
     mol = qi.make_co(n_det=30)
     r = qi.walkers(mol, W, seed=9)
     wf = pkg.Wavefunction(mol, precision="mixed_tf32")
     soa = np.ascontiguousarray(qi.to_soa(r))
-    e_h, lp_h = wf.local_energy_host(soa, log_psi=np.empty(W))
+    x_h, e_h, lp_h = _host_buffers(soa, W, pinned)
+    wf.local_energy_host(x_h, e_loc=e_h, log_psi=lp_h)
     e_d, lp_d = wf.local_energy(torch.tensor(soa, device="cuda"))
     torch.cuda.synchronize()
     assert np.array_equal(e_h, e_d.cpu().numpy()) and np.array_equal(lp_h, lp_d.cpu().numpy())
+    wf.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tf32"])
+def test_host_entry_point_pinned_manybody(pkg, precision):
+    """Page-locked host walkers with the many-body Jastrow (its second kernel
+    reads the device copy the first one wrote), both precision forms."""
+    mol = qi.with_manybody_jastrow(qi.make_lih())
+    W = 4099
+    r = qi.walkers(mol, W, seed=12)
+    wf = pkg.Wavefunction(mol, precision=precision)
+    soa = np.ascontiguousarray(qi.to_soa(r))
+    x_h, e_h, lp_h = _host_buffers(soa, W, True)
+    for _ in range(2):  # the second call reuses the staging buffer
+        wf.local_energy_host(x_h, e_loc=e_h, log_psi=lp_h)
+        e_d, lp_d = wf.local_energy(torch.tensor(soa, device="cuda"))
+        torch.cuda.synchronize()
+        assert np.array_equal(e_h, e_d.cpu().numpy()) and np.array_equal(lp_h, lp_d.cpu().numpy())
+        soa = np.ascontiguousarray(soa[:, ::-1])
+        x_h[...] = soa
+    wf.close()
 
 
 def test_full_size_co_sampled_parity(pkg):
