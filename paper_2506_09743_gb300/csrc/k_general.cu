@@ -262,7 +262,141 @@ __device__ void backflow_positions(const double (&r)[NE][3], const Pairs<NE>& P,
     }
 }
 
+// Orbital values alone at one position: the value part of mo_channels, in
+// the same order of operations.
+template <int NO>
+__device__ __forceinline__ void mo_values(const WfDev& wf, const GenShared& g, const double (&p)[3], int n_occ, double (&phi)[NO]) {
+#pragma unroll
+  for (int m = 0; m < NO; ++m) phi[m] = 0.0;
+  for (int s = 0; s < wf.n_shell; ++s) {
+    const ShellDev& sh = g.sh[s];
+    const double dx = p[0] - wf.atom_xyz[sh.atom][0], dy = p[1] - wf.atom_xyz[sh.atom][1],
+                 dz = p[2] - wf.atom_xyz[sh.atom][2];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double rho = sqrt(r2);
+    double f, g1, f2;
+    radial(sh, r2, rho, f, g1, f2);
+    for (int k = 0; k < sh.n_ao; ++k) {
+      const int b = sh.ao_first + k;
+      const int pw = g.pw[b];
+      const double val = mono(dx, dy, dz, pw & 15, (pw >> 4) & 15, (pw >> 8) & 15) * f;
+      const double* Cb = g.C + (size_t)b * wf.n_mo;
+#pragma unroll
+      for (int m = 0; m < NO; ++m)
+        if (m < n_occ) phi[m] += Cb[m] * val;
+    }
+  }
+}
+
+// Determinant alone: the pivots of small_inverse's elimination (partial
+// pivoting, scaled pivot row), restricted to the rows and columns that later
+// pivots depend on.  Fully unrolled with opaque selects for the row
+// exchanges, so the matrix stays in registers.
+template <int NO>
+__device__ __forceinline__ double det_pivots(double (&a)[NO][NO], int n) {
+  double det = 1.0;
+#pragma unroll
+  for (int k = 0; k < NO; ++k) {
+    if (k < n) {
+      int p = k;
+      double best = fabs(a[k][k]);
+#pragma unroll
+      for (int i = k + 1; i < NO; ++i)
+        if (i < n && fabs(a[i][k]) > best) { best = fabs(a[i][k]); p = i; }
+      if (p != k) det = -det;
+#pragma unroll
+      for (int i = k + 1; i < NO; ++i) {
+        const bool sw = i == p;
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          const double t = a[k][j];
+          a[k][j] = dsel(sw, a[i][j], t);
+          a[i][j] = dsel(sw, t, a[i][j]);
+        }
+      }
+      const double pv = a[k][k];
+      det = det * pv;
+      const double inv = 1.0 / pv;
+#pragma unroll
+      for (int j = k + 1; j < NO; ++j) a[k][j] = a[k][j] * inv;
+#pragma unroll
+      for (int i = k + 1; i < NO; ++i) {
+        if (i < n) {
+          const double f = a[i][k];
+#pragma unroll
+          for (int j = k + 1; j < NO; ++j) a[i][j] -= f * a[k][j];
+        }
+      }
+    }
+  }
+  return det;
+}
+
 }  // namespace
+
+// log|Psi| alone of a single-determinant walker (the Metropolis value path):
+// Pade J, backflow positions, orbital values and the two determinants --
+// eval_walker's value part without its derivative channels.  Loops over the
+// electron-count bracket are unrolled (guards on the actual counts) so that
+// every array stays in registers; the pair terms are visited in eval_walker's
+// order.
+template <int NE, int NO>
+__device__ __forceinline__ double logpsi_walker(const WfDev& wf, const GenShared& g, const double (&r)[NE][3]) {
+  const int N = wf.n_elec, nu = wf.n_up, nd = wf.n_down;
+  const double w = wf.bf_w;
+  double J = 0.0, rt[NE][3];
+#pragma unroll
+  for (int i = 0; i < NE; ++i)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) rt[i][d] = r[i][d];
+#pragma unroll
+  for (int i = 0; i < NE; ++i)
+#pragma unroll
+    for (int j = i + 1; j < NE; ++j)
+      if (j < N) {
+        const double dx = r[i][0] - r[j][0], dy = r[i][1] - r[j][1], dz = r[i][2] - r[j][2];
+        const double iv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz), dist = 1.0 / iv;
+        const double w0 = ((i < nu) == (j < nu)) ? wf.w0_par : wf.w0_anti;
+        const double rd = 1.0 / (1.0 + wf.jb * dist);
+        J += w0 * dist * rd;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          rt[i][d] += w * iv * (r[i][d] - r[j][d]);
+          rt[j][d] += w * iv * (r[j][d] - r[i][d]);
+        }
+      }
+  const int n_occ = nu > nd ? nu : nd;
+  double phi[NE][NO];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    if (q < N) mo_values<NO>(wf, g, rt[q], n_occ, phi[q]);
+    else
+#pragma unroll
+      for (int m = 0; m < NO; ++m) phi[q][m] = 0.0;
+  }
+  double logdet = log(fabs(wf.det_w[0]));
+  double a[NO][NO];
+  if (nu > 0) {  // spin up: electrons 0 .. nu-1
+#pragma unroll
+    for (int e = 0; e < NO; ++e)
+#pragma unroll
+      for (int m = 0; m < NO; ++m) a[e][m] = phi[e < NE ? e : 0][m];
+    logdet += log_abs(det_pivots<NO>(a, nu));
+  }
+  if (nd > 0) {  // spin down: electrons nu .. nu+nd-1 (rows picked by selects)
+#pragma unroll
+    for (int e = 0; e < NO; ++e)
+#pragma unroll
+      for (int m = 0; m < NO; ++m) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < NE; ++q) v = dsel(q == nu + e, phi[q][m], v);
+        a[e][m] = v;
+      }
+    logdet += log_abs(det_pivots<NO>(a, nd));
+  }
+  return J + logdet;
+}
 
 // Local energy and log|Psi| of one walker.  T = double, or Dual<K> with the
 // nuclear coordinates R seeded for forces.  NE >= n_elec, NO >= occupied
@@ -566,6 +700,20 @@ __global__ void __launch_bounds__(128) k_eloc_general(WfDev wf, const double* __
   if (log_psi) log_psi[w] = lp;
 }
 
+template <int NE, int NO>
+__global__ void __launch_bounds__(128) k_logpsi_general(const __grid_constant__ WfDev wf,
+                                                        const double* __restrict__ walkers, int64_t W,
+                                                        int64_t ldw, double* __restrict__ log_psi) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  GenShared g;
+  stage_tables(wf, g, smem_raw);
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  double r[NE][3];
+  load_walker<NE>(walkers, ldw, w, wf.n_elec, r);
+  log_psi[w] = logpsi_walker<NE, NO>(wf, g, r);
+}
+
 // Forces, Eq. force: per walker the tangents of E_L and log|Psi| along the
 // three coordinates of nucleus `atom` (forward mode), combined as
 //   f = -(d E_L + (E_L - E_v) 2 d log|Psi|) / M
@@ -796,6 +944,10 @@ cudaError_t launch_eloc_general(const WfDev& wf, const double* walkers, int64_t 
     if (wf.n_elec <= 2) k_eloc_md<2, 8><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
     else if (wf.n_elec <= 4) k_eloc_md<4, 8><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
     else k_eloc_md<8, 8><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
+    return cudaGetLastError();
+  }
+  if (!kinetic && log_psi) {  // value path: log|Psi| alone
+    QMC_GEN_DISPATCH((k_logpsi_general<NE, NO><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, log_psi)));
     return cudaGetLastError();
   }
   QMC_GEN_DISPATCH((k_eloc_general<NE, NO><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi)));
