@@ -344,7 +344,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--walkers", type=int, default=qi.WORKLOAD_WALKERS["co"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=160,
+    ap.add_argument("--serving-requests", type=int, default=320,
                     help="requests of the Poisson serving run (0 = skip the serving measurement)")
     ap.add_argument("--no-serving-fp64", action="store_true", help="serve the mix in the mixed form only")
     ap.add_argument("--no-det-sweep", action="store_true", help="skip the explicit-versus-table sweep")

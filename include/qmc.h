@@ -352,10 +352,16 @@ qmc_status qmc_last_stage_ms(qmc_wf* wf, float* ms, int32_t n);
  * geometry): its walkers are uploaded or drawn on the device, n_steps
  * Metropolis steps are run (App. B), then the local energies (Eq. Hmol) and
  * their mean and variance, the Monte Carlo estimate of Sec. 1.  Requests are
- * queued on submission and admitted, in arrival order, as soon as one of
- * max_in_flight stream slots is free and the request's device memory
- * (walkers, scratch) fits in the server's arena of hbm_budget_bytes; admitted
- * requests run concurrently on their own streams.  The arena is allocated
+ * queued on submission and admitted as soon as one of max_in_flight stream
+ * slots is free and the request's device memory (walkers, scratch) fits in
+ * the server's arena of hbm_budget_bytes; admitted requests run concurrently
+ * on their own streams.  Admission policy (qmc_server_set_policy): requests
+ * of at least big_walkers walkers ("large") are admitted in arrival order
+ * with at most max_big of them in flight, on low-priority streams; the other
+ * requests are admitted in arrival order, may pass a large request that is
+ * waiting for its turn, and run on high-priority streams.  Memory is
+ * first-come for all: a request that does not fit stops admission until
+ * memory is released.  The arena is allocated
  * once at creation: admission allocates nothing.  A result depends only on
  * the request, not on the other requests in flight.  Single host thread:
  * call the server functions from one thread. */
@@ -405,6 +411,11 @@ qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n
 
 /* Move up to `capacity` finished results into out (oldest first). */
 qmc_status qmc_server_results(qmc_server* srv, qmc_result* out, int32_t capacity, int32_t* n_out);
+
+/* Admission policy (see above): big_walkers = 0 treats every request alike
+ * (plain arrival order); max_big_in_flight >= 1.  Defaults: 65536 and 2.
+ * Applies to the admissions that follow. */
+qmc_status qmc_server_set_policy(qmc_server* srv, int64_t big_walkers, int32_t max_big_in_flight);
 
 /* Bytes of the arena currently free. */
 size_t qmc_server_free_bytes(const qmc_server* srv);

@@ -23,7 +23,7 @@ EXPORTED = (
     "qmc_create_wf", "qmc_destroy_wf", "qmc_set_geometry", "qmc_workspace_size", "qmc_local_energy",
     "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_energy_grad",
     "qmc_set_params", "qmc_server_create", "qmc_server_destroy", "qmc_server_add_wf", "qmc_server_submit",
-    "qmc_server_progress", "qmc_server_results", "qmc_server_free_bytes", "qmc_server_clock",
+    "qmc_server_progress", "qmc_server_results", "qmc_server_set_policy", "qmc_server_free_bytes", "qmc_server_clock",
     "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method", "qmc_optimize", "qmc_force_batches", "qmc_set_manybody_jastrow",
     "qmc_last_error",
 )
@@ -141,6 +141,8 @@ def load(path: str = LIB_PATH):
     lib.qmc_server_progress.restype = c_int32
     lib.qmc_server_results.argtypes = [c_void_p, POINTER(Result), c_int32, POINTER(c_int32)]
     lib.qmc_server_results.restype = c_int32
+    lib.qmc_server_set_policy.argtypes = [c_void_p, c_int64, c_int32]
+    lib.qmc_server_set_policy.restype = c_int32
     lib.qmc_server_free_bytes.argtypes = [c_void_p]
     lib.qmc_server_free_bytes.restype = c_size_t
     lib.qmc_server_clock.argtypes = []

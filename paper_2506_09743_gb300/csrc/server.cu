@@ -89,7 +89,10 @@ struct Pending {
 };
 
 struct Slot {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // the stream of the current request (one of the two below)
+  cudaStream_t lo = nullptr;      // lowest priority: large requests
+  cudaStream_t hi = nullptr;      // highest priority: the others
+  bool big = false;               // the current request is a large one
   cudaEvent_t done = nullptr;
   bool busy = false;
   Pending job{};
@@ -102,6 +105,8 @@ struct Slot {
 
 struct qmc_server {
   int device = 0;
+  int64_t big_walkers = 65536;  // requests with at least this many walkers are large
+  int32_t max_big = 2;          // large requests in flight at once
   void* arena_base = nullptr;
   Arena arena;
   std::vector<qmc_wf*> wfs;
@@ -193,8 +198,12 @@ qmc_status qmc_server_create(int32_t device, size_t hbm_budget_bytes, int32_t ma
   }
   srv->arena.reset(hbm_budget_bytes);
   srv->slots.resize(max_in_flight);
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
   for (auto& sl : srv->slots) {
-    e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    e = cudaStreamCreateWithPriority(&sl.lo, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.hi, cudaStreamNonBlocking, greatest);
+    sl.stream = sl.hi;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&sl.host, sizeof(double) * 4);
     if (e != cudaSuccess) {
@@ -211,9 +220,11 @@ void qmc_server_destroy(qmc_server* srv) {
   {
     DeviceGuard guard(srv->device);
     for (auto& sl : srv->slots) {
-      if (sl.stream) cudaStreamSynchronize(sl.stream);
+      for (cudaStream_t q : {sl.lo, sl.hi})
+        if (q) cudaStreamSynchronize(q);
       if (sl.done) cudaEventDestroy(sl.done);
-      if (sl.stream) cudaStreamDestroy(sl.stream);
+      for (cudaStream_t q : {sl.lo, sl.hi})
+        if (q) cudaStreamDestroy(q);
       if (sl.host) cudaFreeHost(sl.host);
     }
     if (srv->arena_base) cudaFree(srv->arena_base);
@@ -272,14 +283,27 @@ qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n
     srv->arena.release(sl.off, sl.bytes);
     sl.busy = false;
   }
-  // admit queued requests in arrival order while a slot and memory are free
+  // Admit queued requests in arrival order while a slot and memory are free.
+  // Large requests (>= big_walkers walkers) keep their arrival order among
+  // themselves and at most max_big of them run at once, on low-priority
+  // streams; smaller requests may pass a large one that has to wait, and run
+  // on high-priority streams, so their kernels fill the device between the
+  // large requests' blocks instead of queueing behind them.  Memory stays
+  // first-come: a request that does not fit stops the admission.
   qmc_status status = QMC_OK;
-  while (!srv->queue.empty()) {
+  int n_big = 0;
+  for (auto& sl : srv->slots) n_big += (sl.busy && sl.big) ? 1 : 0;
+  for (auto it = srv->queue.begin(); it != srv->queue.end();) {
+    const bool big = srv->big_walkers > 0 && it->req.n_walkers >= srv->big_walkers;
+    if (big && n_big >= srv->max_big) {
+      ++it;
+      continue;
+    }
     Slot* free_slot = nullptr;
     for (auto& sl : srv->slots)
       if (!sl.busy) { free_slot = &sl; break; }
     if (!free_slot) break;
-    Pending& head = srv->queue.front();
+    Pending& head = *it;
     const size_t need = request_bytes(srv->wfs[head.req.wf_id], head.req.n_walkers);
     size_t off;
     if (!srv->arena.alloc(need, &off)) break;
@@ -289,7 +313,10 @@ qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n
     sl.bytes = need;
     sl.busy = true;
     sl.t_admit = now_s();
-    srv->queue.pop_front();
+    sl.big = big;
+    sl.stream = big ? sl.lo : sl.hi;
+    n_big += big ? 1 : 0;
+    it = srv->queue.erase(it);
     const qmc_status s = launch_job(srv, sl);
     if (s != QMC_OK) {
       // report the request as failed and keep serving the others
@@ -305,6 +332,7 @@ qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n
       srv->results.push_back(res);
       srv->arena.release(sl.off, sl.bytes);
       sl.busy = false;
+      n_big -= big ? 1 : 0;
       status = s;
     }
   }
@@ -323,6 +351,13 @@ qmc_status qmc_server_results(qmc_server* srv, qmc_result* out, int32_t capacity
   for (int32_t k = 0; k < n; ++k) out[k] = srv->results[k];
   srv->results.erase(srv->results.begin(), srv->results.begin() + n);
   *n_out = n;
+  return QMC_OK;
+}
+
+qmc_status qmc_server_set_policy(qmc_server* srv, int64_t big_walkers, int32_t max_big_in_flight) {
+  if (!srv || big_walkers < 0 || max_big_in_flight < 1) return sfail(QMC_ERR_ARG, "bad policy arguments");
+  srv->big_walkers = big_walkers;
+  srv->max_big = max_big_in_flight;
   return QMC_OK;
 }
 

@@ -13,11 +13,15 @@ from . import Wavefunction, _lib, library
 
 
 class Server:
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 32 << 30, max_in_flight: int = 8):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 32 << 30, max_in_flight: int = 8,
+                 big_walkers: int = 65536, max_big_in_flight: int = 2):
+        """big_walkers / max_big_in_flight: the admission policy of
+        qmc_server_set_policy (big_walkers = 0: plain arrival order)."""
         lib = library()
         h = ctypes.c_void_p()
         _lib.check_server(lib.qmc_server_create(device, int(hbm_budget_bytes), int(max_in_flight), ctypes.byref(h)))
         self._h, self._lib = h, lib
+        _lib.check_server(lib.qmc_server_set_policy(h, int(big_walkers), int(max_big_in_flight)))
         self._wfs = []  # keep wavefunctions alive
         self._hold = {}  # host walker buffers of requests in flight
         self.budget = int(hbm_budget_bytes)
@@ -66,6 +70,9 @@ class Server:
             self._hold.pop(int(r.ticket), None)
             out.append({f: getattr(r, f) for f, _ in _lib.Result._fields_})
         return out
+
+    def set_policy(self, big_walkers: int, max_big_in_flight: int):
+        _lib.check_server(self._lib.qmc_server_set_policy(self._h, int(big_walkers), int(max_big_in_flight)))
 
     def free_bytes(self) -> int:
         return int(self._lib.qmc_server_free_bytes(self._h))

@@ -28,10 +28,10 @@ def mix(pkg):
     return wfs
 
 
-def _server(mix, budget, slots):
+def _server(mix, budget, slots, **policy):
     from paper_2506_09743_gb300 import serving
 
-    srv = serving.Server(hbm_budget_bytes=budget, max_in_flight=slots)
+    srv = serving.Server(hbm_budget_bytes=budget, max_in_flight=slots, **policy)
     ids = {k: srv.add(wf) for k, wf in mix.items()}
     return srv, ids
 
@@ -116,4 +116,37 @@ def test_poisson_stream_reports_latency(mix):
     st = serving.summarize(done, 10)
     assert st["requests"] == 24 and st["failed"] == 0
     assert 0 < st["p50_ms"] <= st["p99_ms"]
+    srv.close()
+
+
+def test_large_requests_keep_order_and_limit(mix):
+    """Policy: at most max_big large requests in flight, in arrival order among
+    themselves; a small request submitted behind a waiting large one is
+    admitted before it; every result matches the same request run alone."""
+    srv, ids = _server(mix, 16 << 30, 8, big_walkers=40000, max_big_in_flight=1)
+    key = ids[("lih", 1)]
+    big = [srv.submit(key, 65536, 20, 0.1, 500 + k) for k in range(3)]
+    small = srv.submit(ids[("h2", 1)], 4096, 20, 0.1, 9)
+    res = {r["ticket"]: r for r in srv.drain()}
+    assert all(r["status"] == 0 for r in res.values())
+    spans = sorted((res[t]["t_admit"], res[t]["t_done"]) for t in big)
+    assert [res[t]["t_admit"] for t in big] == sorted(res[t]["t_admit"] for t in big)
+    for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
+        assert a1 >= d0  # never two large requests at once
+    assert res[small]["t_admit"] < res[big[1]]["t_admit"]
+    srv.set_policy(0, 1)  # plain arrival order: the same results
+    again = srv.submit(key, 65536, 20, 0.1, 501)
+    r2 = srv.drain()[0]
+    assert r2["e_mean"] == res[big[1]]["e_mean"] and r2["e_var"] == res[big[1]]["e_var"]
+    srv.close()
+
+
+def test_policy_arguments_are_checked(mix):
+    from paper_2506_09743_gb300 import QmcError
+
+    srv, _ = _server(mix, 1 << 30, 2)
+    with pytest.raises(QmcError):
+        srv.set_policy(-1, 2)
+    with pytest.raises(QmcError):
+        srv.set_policy(1000, 0)
     srv.close()
