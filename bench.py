@@ -170,24 +170,29 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(n_requests: int, with_fp64: bool, device: int):
+def run_serving(n_requests: int, with_fp64: bool, device: int, n_requests_fp64: int = 400,
+                n_capacity: int = 400):
     """Serving mix (H2, LiH, Li2, CO at 20 bond lengths each; 50 Metropolis
     steps + E_L mean/variance per request; walkers uniform on 4k..256k):
-    a closed-loop run measures the capacity (requests/s with everything
-    queued at once), then Poisson arrivals at 80% of it give the latencies."""
+    a closed-loop run of n_capacity requests measures the capacity (requests/s
+    with everything queued at once) and warms the server up, then Poisson
+    arrivals at 80% of it give the latencies (n_requests in the mixed form,
+    n_requests_fp64 in the slower FP64 form)."""
     from paper_2506_09743_gb300 import serving
 
     out = {"n_steps": 50, "walker_choices": [4096, 16384, 65536, 262144], "molecules": ["h2", "lih", "li2", "co"],
-           "note": "Li2 (backflow) requests run in the FP64 form in both mixes"}
+           "note": "Li2 (backflow) requests run in the FP64 form in both mixes",
+           "policy": "large (>= 65,536 walkers) requests ordered, at most 2 in flight, low stream priority"}
     forms = ["mixed_tf32"] + (["fp64"] if with_fp64 else [])
     for form in forms:
+        n = n_requests if form == "mixed_tf32" else min(n_requests, n_requests_fp64)
         wfs = serving.build_mix(form, device=device)
         srv = serving.Server(device=device, hbm_budget_bytes=48 << 30, max_in_flight=8)
         ids = {k: srv.add(wf) for k, wf in wfs.items()}
-        cap_reqs = qi.serving_requests(n_requests, rate_hz=0.0, seed=101)
+        cap_reqs = qi.serving_requests(min(n, n_capacity), rate_hz=0.0, seed=101)
         cap = serving.summarize(serving.run_stream(srv, ids, cap_reqs, n_steps=50, step=0.05), 50)
         rate = 0.8 * cap["requests_per_s"]
-        reqs = qi.serving_requests(n_requests, rate_hz=rate, seed=102)
+        reqs = qi.serving_requests(n, rate_hz=rate, seed=102)
         st = serving.summarize(serving.run_stream(srv, ids, reqs, n_steps=50, step=0.05, rate_hz=rate), 50)
         st["capacity_requests_per_s"] = cap["requests_per_s"]
         st["arrival_rate_hz"] = rate
@@ -344,8 +349,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--walkers", type=int, default=qi.WORKLOAD_WALKERS["co"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=320,
-                    help="requests of the Poisson serving run (0 = skip the serving measurement)")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests of the Poisson serving run, mixed form (the FP64 form serves at most 400; 0 = skip)")
     ap.add_argument("--no-serving-fp64", action="store_true", help="serve the mix in the mixed form only")
     ap.add_argument("--no-det-sweep", action="store_true", help="skip the explicit-versus-table sweep")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other molecules' measurements")
