@@ -77,6 +77,7 @@ size_t workspace_bytes(const qmc_wf* wf, int64_t W) {
   b += align256((size_t)N * 2 * mo_row_pad(wf->dev.n_mo, tc) * ldm * sizeof(double));  // MO channels (FP64)
   b += align256(3 * N * ldm * sizeof(double));         // proposals
   b += 2 * align256(ldm * sizeof(double));             // lp, lp_new
+  b += align256(sizeof(uint64_t));                     // step counter
   b += align256(sizeof(int));                          // device error flag
   return b;
 }
@@ -95,6 +96,7 @@ Workspace carve(const qmc_wf* wf, void* base, int64_t W, int** err_flag) {
   ws.prop = reinterpret_cast<double*>(p); p += align256(3 * N * ws.ldm * sizeof(double));
   ws.lp = reinterpret_cast<double*>(p); p += align256(ws.ldm * sizeof(double));
   ws.lp_new = reinterpret_cast<double*>(p); p += align256(ws.ldm * sizeof(double));
+  ws.ctr = reinterpret_cast<uint64_t*>(p); p += align256(sizeof(uint64_t));
   *err_flag = reinterpret_cast<int*>(p);
   return ws;
 }
@@ -551,6 +553,7 @@ void qmc_destroy_wf(qmc_wf* wf) {
     if (wf->gws) cudaFree(wf->gws);
     for (auto& e : wf->tev)
       if (e) cudaEventDestroy(e);
+    if (wf->cap_stream) cudaStreamDestroy(wf->cap_stream);
   }
   delete wf;
 }
@@ -723,6 +726,59 @@ qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_wa
   return e == cudaSuccess ? QMC_OK : cuda_fail(e, "result download");
 }
 
+// Metropolis steps as a CUDA graph: one step (proposal, value path on the
+// proposals, acceptance, step-counter advance) is captured once on the
+// wavefunction's capture stream and replayed n_steps times on st, so a
+// launch-bound chain (small walker counts) pays one graph launch per step
+// instead of five to seven kernel launches.  The step index comes from a
+// device counter (zeroed first), so every replay draws its own Philox
+// numbers and the chain is the one the plain loop gives.  *done = false with
+// QMC_OK when capture is not possible here (the caller then runs the loop).
+static constexpr int kGraphMinSteps = 4;
+
+static qmc_status sample_graph(qmc_wf* wf, double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                               int* err_flag, int32_t n_steps, double step, uint64_t seed, uint64_t first_walker,
+                               uint64_t step_offset, int64_t* n_accept, cudaStream_t st, bool* done) {
+  *done = false;
+  if (!wf->cap_stream && cudaStreamCreateWithFlags(&wf->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_OK;
+  }
+  cudaStream_t cs = wf->cap_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_OK;
+  }
+  Workspace wp = ws;
+  qmc_status s = launch_status(
+      launch_propose(wf->dev, walkers, W, ldw, ws, step, seed, first_walker, step_offset, ws.ctr, cs), "propose");
+  if (!s) s = eval_path(wf, ws.prop, W, ws.ldm, wp, err_flag, false, nullptr, ws.lp_new, cs);
+  if (!s)
+    s = launch_status(
+        launch_accept(wf->dev, walkers, W, ldw, ws, seed, first_walker, step_offset, ws.ctr, n_accept, cs), "accept");
+  if (!s) s = launch_status(launch_step_advance(ws.ctr, cs), "step counter");
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (s || e != cudaSuccess || !graph) {  // not capturable here: the plain loop runs instead
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return QMC_OK;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_OK;
+  }
+  e = cudaMemsetAsync(ws.ctr, 0, sizeof(uint64_t), st);
+  for (int t = 0; e == cudaSuccess && t < n_steps; ++t) e = cudaGraphLaunch(exec, st);
+  cudaGraphExecDestroy(exec);  // freed once the launched replays complete
+  if (e != cudaSuccess) return cuda_fail(e, "step graph launch");
+  *done = true;
+  return QMC_OK;
+}
+
 qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_steps, double step,
                       uint64_t seed, uint64_t first_walker, uint64_t step_offset, double* log_psi,
                       int64_t* n_accept, void* workspace, size_t workspace_bytes_, void* stream) {
@@ -742,15 +798,21 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
   s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, false, nullptr, ws.lp, st);
   if (s) return s;
   Workspace wp = ws;  // value path on the proposals: walkers = prop, ldw = ldm
-  for (int t = 0; t < n_steps; ++t) {
+  bool done = false;
+  if (n_steps >= kGraphMinSteps && !wf->timing) {
+    s = sample_graph(wf, walkers, n_walkers, ldw, ws, err_flag, n_steps, step, seed, first_walker, step_offset,
+                     n_accept, st, &done);
+    if (s) return s;
+  }
+  for (int t = 0; !done && t < n_steps; ++t) {
     const uint64_t g = step_offset + (uint64_t)t;
-    s = launch_status(launch_propose(wf->dev, walkers, n_walkers, ldw, ws, step, seed, first_walker, g, st),
+    s = launch_status(launch_propose(wf->dev, walkers, n_walkers, ldw, ws, step, seed, first_walker, g, nullptr, st),
                       "propose");
     if (s) return s;
     s = eval_path(wf, ws.prop, n_walkers, ws.ldm, wp, err_flag, false, nullptr, ws.lp_new, st);
     if (s) return s;
-    s = launch_status(launch_accept(wf->dev, walkers, n_walkers, ldw, ws, seed, first_walker, g, n_accept, st),
-                      "accept");
+    s = launch_status(
+        launch_accept(wf->dev, walkers, n_walkers, ldw, ws, seed, first_walker, g, nullptr, n_accept, st), "accept");
     if (s) return s;
   }
   if (log_psi) {

@@ -454,10 +454,10 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
         const float dy = (rh[i][1] - rh[j][1]) + (rl[i][1] - rl[j][1]);
         const float dz = (rh[i][2] - rh[j][2]) + (rl[i][2] - rl[j][2]);
         const float d2 = dx * dx + dy * dy + dz * dz;
-        const float inv = 1.0f / sqrtf(d2);
-        const float dist = d2 * inv;
+        const float inv = rsqrtf(d2);  // hardware reciprocal square root and reciprocal:
+        const float dist = d2 * inv;    // a few ulp, far inside the FP32 pair-term budget
         const float w0 = ((i < wf.n_up) == (j < wf.n_up)) ? w0p : w0a;
-        const float rden = 1.0f / (1.0f + b * dist);
+        const float rden = __frcp_rn(1.0f + b * dist);
         const float u1 = w0 * rden * rden;
         J.add(w0 * dist * rden);
         V.add(inv);
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
         const float dx = (rh[i][0] - ah[0]) + (rl[i][0] - al[0]);
         const float dy = (rh[i][1] - ah[1]) + (rl[i][1] - al[1]);
         const float dz = (rh[i][2] - ah[2]) + (rl[i][2] - al[2]);
-        V.add(-zh / sqrtf(dx * dx + dy * dy + dz * dz));
+        V.add(-zh * rsqrtf(dx * dx + dy * dy + dz * dz));
       }
   }
   if (MB) {

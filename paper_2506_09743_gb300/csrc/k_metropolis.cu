@@ -6,7 +6,9 @@
 // Block j gives Gaussians 4j..4j+3 by Box-Muller on the word pairs
 // (x0, x1), (x2, x3) with u(x) = (x + 0.5) 2^-32; block ceil(3N/4) word 0 is
 // the acceptance uniform.  Both kernels regenerate their numbers from the
-// counter, so nothing random is stored between them.
+// counter, so nothing random is stored between them.  The step index is
+// gstep plus, when gctr is not null, a device counter: a CUDA graph of one
+// step is then replayed with the counter advanced by a one-thread kernel.
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -28,9 +30,11 @@ __device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 0
 
 __global__ void __launch_bounds__(128) k_propose(int n3, const double* __restrict__ walkers, int64_t W, int64_t ldw,
                                                  double* __restrict__ prop, int64_t ldm, double step, uint64_t seed,
-                                                 uint64_t first_walker, uint64_t gstep) {
+                                                 uint64_t first_walker, uint64_t gstep,
+                                                 const unsigned long long* __restrict__ gctr) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= W) return;
+  if (gctr) gstep += *gctr;
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const uint32_t wi = (uint32_t)(first_walker + (uint64_t)w);
   const double two_pi = 6.283185307179586;
@@ -54,9 +58,11 @@ __global__ void __launch_bounds__(128) k_accept(int n3, double* __restrict__ wal
                                                 const double* __restrict__ prop, int64_t ldm,
                                                 double* __restrict__ lp, const double* __restrict__ lp_new,
                                                 uint64_t seed, uint64_t first_walker, uint64_t gstep,
+                                                const unsigned long long* __restrict__ gctr,
                                                 int64_t* __restrict__ n_accept) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= W) return;
+  if (gctr) gstep += *gctr;
   const uint32_t wi = (uint32_t)(first_walker + (uint64_t)w);
   const int nblk = (n3 + 3) / 4;
   const u4 x = philox4x32_10(u4{(uint32_t)nblk, wi, (uint32_t)gstep, (uint32_t)(gstep >> 32)}, (uint32_t)seed,
@@ -95,6 +101,9 @@ __global__ void __launch_bounds__(128) k_init_walkers(InitSpec spec, int64_t W, 
   }
 }
 
+// the step counter of a replayed step graph: one more step done
+__global__ void k_step_advance(unsigned long long* ctr) { *ctr += 1ull; }
+
 // sum of the per-walker acceptance counts into out[0] (fixed order)
 __global__ void k_sum_counts(const int64_t* __restrict__ c, int64_t W, double* __restrict__ out) {
   __shared__ long long red[256];
@@ -122,19 +131,27 @@ cudaError_t launch_sum_counts(const int64_t* counts, int64_t W, double* out, cud
 }
 
 cudaError_t launch_propose(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
-                           double step, uint64_t seed, uint64_t first_walker, uint64_t gstep, cudaStream_t st) {
+                           double step, uint64_t seed, uint64_t first_walker, uint64_t gstep, const uint64_t* gctr,
+                           cudaStream_t st) {
   if (W == 0) return cudaSuccess;
   k_propose<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(3 * wf.n_elec, walkers, W, ldw, ws.prop, ws.ldm, step,
-                                                          seed, first_walker, gstep);
+                                                          seed, first_walker, gstep,
+                                                          reinterpret_cast<const unsigned long long*>(gctr));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_advance(uint64_t* gctr, cudaStream_t st) {
+  k_step_advance<<<1, 1, 0, st>>>(reinterpret_cast<unsigned long long*>(gctr));
   return cudaGetLastError();
 }
 
 cudaError_t launch_accept(const WfDev& wf, double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
-                          uint64_t seed, uint64_t first_walker, uint64_t gstep, int64_t* n_accept,
-                          cudaStream_t st) {
+                          uint64_t seed, uint64_t first_walker, uint64_t gstep, const uint64_t* gctr,
+                          int64_t* n_accept, cudaStream_t st) {
   if (W == 0) return cudaSuccess;
   k_accept<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(3 * wf.n_elec, walkers, W, ldw, ws.prop, ws.ldm, ws.lp,
-                                                         ws.lp_new, seed, first_walker, gstep, n_accept);
+                                                         ws.lp_new, seed, first_walker, gstep,
+                                                         reinterpret_cast<const unsigned long long*>(gctr), n_accept);
   return cudaGetLastError();
 }
 

@@ -106,6 +106,7 @@ struct Workspace {
   double* prop;    // [3N][ldm] proposed positions (sampling)
   double* lp;      // [ldm] current log|Psi| (sampling)
   double* lp_new;  // [ldm] proposed log|Psi| (sampling)
+  uint64_t* ctr;   // step counter of a replayed Metropolis step graph
 };
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -248,9 +249,12 @@ size_t det_explicit_smem_bytes(const WfDev& wf, bool kin);
 cudaError_t launch_det_explicit(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,
                                 double* e_loc, double* log_psi, cudaStream_t st);
 cudaError_t launch_propose(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
-                           double step, uint64_t seed, uint64_t first_walker, uint64_t gstep, cudaStream_t st);
+                           double step, uint64_t seed, uint64_t first_walker, uint64_t gstep, const uint64_t* gctr,
+                           cudaStream_t st);
 cudaError_t launch_accept(const WfDev& wf, double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
-                          uint64_t seed, uint64_t first_walker, uint64_t gstep, int64_t* n_accept,
-                          cudaStream_t st);
+                          uint64_t seed, uint64_t first_walker, uint64_t gstep, const uint64_t* gctr,
+                          int64_t* n_accept, cudaStream_t st);
+// *gctr += 1 (one thread): the step counter of a replayed step graph
+cudaError_t launch_step_advance(uint64_t* gctr, cudaStream_t st);
 
 }  // namespace qmc

@@ -62,5 +62,6 @@ struct qmc_wf {
   bool timed_once = false;
   cudaEvent_t tev[6] = {};  // Jastrow, AO+MO, det (start, end)
   int det_method = QMC_DET_TABLE;
+  cudaStream_t cap_stream = nullptr;  // capture stream of the Metropolis step graph
   std::mutex mu;
 };

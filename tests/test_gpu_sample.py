@@ -118,3 +118,26 @@ def test_backflow_chain_matches_oracle(pkg):
     _, lp_e = wf.local_energy(x)
     assert torch.allclose(lp, lp_e, rtol=0, atol=1e-12)
     wf.close()
+
+
+@pytest.mark.parametrize("name,precision", [("lih", "fp64"), ("co", "mixed_tf32"), ("li2", "fp64")])
+def test_step_graph_replays_the_plain_loop(pkg, name, precision):
+    """n_steps >= 4 run as a replayed CUDA graph of one step; one-step calls
+    run the plain launch loop.  Same chain bit for bit: positions, log|Psi|
+    and acceptance counts."""
+    mol = qi.make_molecule(name)
+    W = 777
+    r0 = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=5)), device="cuda")
+    wf = pkg.Wavefunction(mol, precision=precision)
+    a, b = r0.clone(), r0.clone()
+    lpa = torch.empty(W, dtype=torch.float64, device="cuda")
+    lpb = torch.empty_like(lpa)
+    acca = torch.zeros(W, dtype=torch.int64, device="cuda")
+    accb = torch.zeros_like(acca)
+    wf.sample(a, n_steps=12, step=0.1, seed=99, step_offset=3, log_psi=lpa, n_accept=acca)
+    for t in range(12):
+        wf.sample(b, n_steps=1, step=0.1, seed=99, step_offset=3 + t, log_psi=lpb, n_accept=accb)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(lpa, lpb) and torch.equal(acca, accb)
+    assert 0 < int(acca.sum()) < 12 * W
+    wf.close()
