@@ -535,8 +535,13 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
   h.det_exc.assign(dets->exc, dets->exc + 10 * (size_t)dets->n_det);
   h.w0p = jastrow->w0_par; h.w0a = jastrow->w0_anti; h.b = jastrow->b; h.w = jastrow->backflow_w;
   qmc_status st = build_tables(wf);
+  if (st == QMC_OK) {  // the proposal kernels' Box-Muller tables on this device
+    DeviceGuard guard(wf->device);
+    const cudaError_t e = init_box_muller_tables();
+    if (e != cudaSuccess) st = cuda_fail(e, "Box-Muller tables");
+  }
   if (st != QMC_OK) {
-    delete wf;
+    qmc_destroy_wf(wf);
     return st;
   }
   *out = wf;

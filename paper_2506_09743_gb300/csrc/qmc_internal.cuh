@@ -254,6 +254,9 @@ cudaError_t launch_propose(const WfDev& wf, const double* walkers, int64_t W, in
 cudaError_t launch_accept(const WfDev& wf, double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                           uint64_t seed, uint64_t first_walker, uint64_t gstep, const uint64_t* gctr,
                           int64_t* n_accept, cudaStream_t st);
+// the Box-Muller tables of the proposal kernels on the current device (once
+// per device; synchronous)
+cudaError_t init_box_muller_tables();
 // *gctr += 1 (one thread): the step counter of a replayed step graph
 cudaError_t launch_step_advance(uint64_t* gctr, cudaStream_t st);
 

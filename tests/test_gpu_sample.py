@@ -141,3 +141,31 @@ def test_step_graph_replays_the_plain_loop(pkg, name, precision):
     assert torch.equal(a, b) and torch.equal(lpa, lpb) and torch.equal(acca, accb)
     assert 0 < int(acca.sum()) < 12 * W
     wf.close()
+
+
+def test_proposal_gaussians_match_library_box_muller(pkg):
+    """The proposal kernel's table-driven Box-Muller against the oracle's
+    FP64 library Box-Muller on the same Philox words: one step of 1 bohr, so
+    an accepted walker moves by its Gaussian vector; agreement to a few ulp
+    over 40,000 walkers x 12 coordinates (the far tail included)."""
+    from oracle import philox
+
+    mol = qi.make_lih()
+    W = 40000
+    x0 = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=8)), device="cuda")
+    x = x0.clone()
+    wf = pkg.Wavefunction(mol, precision="fp64")
+    acc = torch.zeros(W, dtype=torch.int64, device="cuda")
+    wf.sample(x, n_steps=1, step=1.0, seed=4242, step_offset=17, n_accept=acc)
+    torch.cuda.synchronize()
+    z_ref, _ = philox.walker_normals_and_uniform(4242, np.arange(W), 17, 3 * mol.n_elec)
+    a = acc.cpu().numpy() == 1
+    assert a.sum() > 1000
+    x0n, x1n = x0.cpu().numpy().T[a], x.cpu().numpy().T[a]
+    z = z_ref[a]
+    eps = np.finfo(np.float64).eps
+    # the subtraction x1 - x0 rounds at the positions' scale; the Gaussians
+    # themselves are compared at a few ulp
+    tol = 2 * eps * (np.abs(x0n) + np.abs(x1n)) + 8 * eps * np.maximum(1.0, np.abs(z))
+    assert np.all(np.abs((x1n - x0n) - z) <= tol), float((np.abs((x1n - x0n) - z) / tol).max())
+    wf.close()
