@@ -84,15 +84,22 @@ __device__ void mo_channels(const WfDev& wf, const GenShared& g, const double p[
     for (int d = 0; d < 3; ++d) dphi[m][d] = T(0.0);
     for (int c = 0; c < 6; ++c) hphi[m][c] = T(0.0);
   }
+  int cur_atom = -1;  // shells come grouped by atom: one displacement and distance per atom
+  T dx = T(0.0), dy = T(0.0), dz = T(0.0), r2 = T(0.0), rho = T(0.0), ir2 = T(0.0);
   for (int s = 0; s < wf.n_shell; ++s) {
     const ShellDev& sh = g.sh[s];
-    const T dx = p[0] - R[sh.atom][0], dy = p[1] - R[sh.atom][1], dz = p[2] - R[sh.atom][2];
-    const T r2 = dx * dx + dy * dy + dz * dz;
-    const T rho = sqrt(r2);
+    if (sh.atom != cur_atom) {
+      cur_atom = sh.atom;
+      dx = p[0] - R[cur_atom][0];
+      dy = p[1] - R[cur_atom][1];
+      dz = p[2] - R[cur_atom][2];
+      r2 = dx * dx + dy * dy + dz * dz;
+      rho = sqrt(r2);
+      ir2 = 1.0 / r2;
+    }
     T f, g1, f2;
     radial(sh, r2, rho, f, g1, f2);
     const T dv[3] = {dx, dy, dz};
-    const T ir2 = 1.0 / r2;
     for (int k = 0; k < sh.n_ao; ++k) {
       const int b = sh.ao_first + k;
       const int pw = g.pw[b];
@@ -268,12 +275,18 @@ template <int NO>
 __device__ __forceinline__ void mo_values(const WfDev& wf, const GenShared& g, const double (&p)[3], int n_occ, double (&phi)[NO]) {
 #pragma unroll
   for (int m = 0; m < NO; ++m) phi[m] = 0.0;
+  int cur_atom = -1;  // shells come grouped by atom: one displacement and distance per atom
+  double dx = 0.0, dy = 0.0, dz = 0.0, r2 = 0.0, rho = 0.0;
   for (int s = 0; s < wf.n_shell; ++s) {
     const ShellDev& sh = g.sh[s];
-    const double dx = p[0] - wf.atom_xyz[sh.atom][0], dy = p[1] - wf.atom_xyz[sh.atom][1],
-                 dz = p[2] - wf.atom_xyz[sh.atom][2];
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    const double rho = sqrt(r2);
+    if (sh.atom != cur_atom) {
+      cur_atom = sh.atom;
+      dx = p[0] - wf.atom_xyz[cur_atom][0];
+      dy = p[1] - wf.atom_xyz[cur_atom][1];
+      dz = p[2] - wf.atom_xyz[cur_atom][2];
+      r2 = dx * dx + dy * dy + dz * dz;
+      rho = sqrt(r2);
+    }
     double f, g1, f2;
     radial(sh, r2, rho, f, g1, f2);
     for (int k = 0; k < sh.n_ao; ++k) {
