@@ -932,6 +932,7 @@ static size_t gen_table_bytes(const WfDev& wf) {
     const int ns = wf.n_up > wf.n_down ? wf.n_up : wf.n_down;         \
     if (wf.n_elec <= 2 && ns <= 1) { constexpr int NE = 2, NO = 1; CALL; } \
     else if (wf.n_elec <= 4 && ns <= 2) { constexpr int NE = 4, NO = 2; CALL; } \
+    else if (wf.n_elec <= 6 && ns <= 3) { constexpr int NE = 6, NO = 3; CALL; } \
     else if (wf.n_elec <= 8 && ns <= 4) { constexpr int NE = 8, NO = 4; CALL; } \
     else return cudaErrorInvalidValue;                                \
   }
