@@ -32,6 +32,10 @@ struct Dual {
     for (int k = 0; k < K; ++k) d[k] += o.d[k];
     return *this;
   }
+  __device__ __forceinline__ Dual& operator+=(double o) {  // a constant: the tangents stay
+    v += o;
+    return *this;
+  }
   __device__ __forceinline__ Dual& operator-=(const Dual& o) {
     v -= o.v;
 #pragma unroll
