@@ -187,8 +187,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
       // value channel P f and kinetic channel
       //   (lap + 2 grad J . grad)(P f) = f lap P + P (f2 + 2 (l+1) g1 + 2 g1 gJ.d) + 2 f gJ.grad P
       auto emit = [&](int col, float v, float kin) {
-        put(0, col, live ? v : 0.f);
-        if (NCH == 2) put(1, col, live ? kin : 0.f);
+        // rows past the last walker keep whatever their (zero) positions give:
+        // an MMA row depends on its own A row only, and those rows are never stored
+        put(0, col, v);
+        if (NCH == 2) put(1, col, kin);
       };
       for (int q = s_begin; q < s_end; ++q) {
         const int ent = list_s[q];
