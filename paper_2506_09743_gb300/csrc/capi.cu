@@ -279,20 +279,21 @@ qmc_status build_tables(qmc_wf* wf) {
   if ((int)shells.size() > kMaxShells) return fail(QMC_ERR_UNSUPPORTED, "too many shells");
   d.n_shell = (int)shells.size();
   // ---- tensor-core AO stage: pack the shells into K-passes of kTcPass
-  // columns in AO order (a shell that would straddle a pass boundary starts
-  // the next pass), then deal each pass's shells to the four thread parts by
+  // columns, then deal each pass's shells to the four thread parts by
   // estimated cost, largest first, each part's list kept in shell order so
-  // that shells of one atom stay together.
+  // that shells of one atom stay together.  Within each atom the complete d
+  // shells are placed first, on columns = 0 (mod 4), then the complete p
+  // shells on even columns, then the rest into the first free columns (the
+  // gaps the alignment leaves), so that the kernel writes a d shell's first
+  // four columns with one 16-byte store and pairs of p and d columns with
+  // 8-byte stores; a shell that does not fit in the pass starts the next one.
   std::vector<int> ao_col(nao, 0), tc_shells;
   d.n_pass = 0;
   if (tc) {
-    std::vector<int> first_shell;  // first shell of each pass
-    int col = 0;
-    std::vector<int> shell_col(d.n_shell), shell_type(d.n_shell);
+    std::vector<int> shell_col(d.n_shell), shell_type(d.n_shell), shell_pass(d.n_shell);
+    std::vector<int> canon_all(nao, 0);
     for (int s = 0; s < d.n_shell; ++s) {
       const ShellDev& q = shells[s];
-      if (col % kTcPass + q.n_ao > kTcPass) col = (int)round_up(col, kTcPass);
-      if (col % kTcPass == 0 && (int)first_shell.size() == col / kTcPass) first_shell.push_back(s);
       // a complete Cartesian s, p or d shell gets its columns in the
       // canonical order (x, y, z / xx, xy, xz, yy, yz, zz), which the kernel
       // evaluates without per-AO power lookups
@@ -305,18 +306,50 @@ qmc_status build_tables(qmc_wf* wf) {
         canon[k] = j;
       }
       shell_type[s] = complete ? 1 + q.l : 0;
-      shell_col[s] = col % kTcPass;
-      for (int k = 0; k < q.n_ao; ++k) ao_col[q.ao_first + k] = col + (complete ? canon[k] : k);
-      col += q.n_ao;
+      for (int k = 0; k < q.n_ao; ++k) canon_all[q.ao_first + k] = complete ? canon[k] : k;
     }
-    d.n_pass = (int)first_shell.size();
+    // placement order: atom by atom (shell order), d first, then p, then the rest
+    std::vector<int> order;
+    for (int s0 = 0; s0 < d.n_shell;) {
+      int s1 = s0;
+      while (s1 < d.n_shell && shells[s1].atom == shells[s0].atom) ++s1;
+      for (int want : {3, 2, -1})
+        for (int s = s0; s < s1; ++s)
+          if ((want >= 0 && shell_type[s] == want) || (want < 0 && shell_type[s] != 3 && shell_type[s] != 2))
+            order.push_back(s);
+      s0 = s1;
+    }
+    unsigned used = 0;  // columns taken in the current pass
+    int pass = 0;
+    std::vector<unsigned> pass_used;
+    for (int s : order) {
+      const ShellDev& q = shells[s];
+      const int align = shell_type[s] == 3 ? 4 : shell_type[s] == 2 ? 2 : 1;
+      const unsigned span = q.n_ao >= 32 ? 0xFFFFFFFFu : ((1u << q.n_ao) - 1u);
+      int c = -1;
+      for (int tries = 0; tries < 2 && c < 0; ++tries) {
+        for (int k = 0; k + q.n_ao <= kTcPass; k += align)
+          if (((span << k) & used) == 0) { c = k; break; }
+        if (c < 0) {  // start the next pass
+          pass_used.push_back(used);
+          used = 0;
+          ++pass;
+        }
+      }
+      if (c < 0) return fail(QMC_ERR_UNSUPPORTED, "an AO shell wider than a tensor-core pass");
+      used |= span << c;
+      shell_col[s] = c;
+      shell_pass[s] = pass;
+      for (int k = 0; k < q.n_ao; ++k) ao_col[q.ao_first + k] = pass * kTcPass + c + canon_all[q.ao_first + k];
+    }
+    pass_used.push_back(used);
+    d.n_pass = (int)pass_used.size();
     if (d.n_pass > kMaxTcPass) return fail(QMC_ERR_UNSUPPORTED, "too many AO passes");
-    first_shell.push_back(d.n_shell);
     for (int p = 0; p < d.n_pass; ++p) {
-      const int s0 = first_shell[p], s1 = first_shell[p + 1];
-      d.pass_cols[p] = ao_col[shells[s1 - 1].ao_first + shells[s1 - 1].n_ao - 1] - p * kTcPass + 1;
+      d.pass_zero[p] = ~pass_used[p];
       std::vector<int> by_cost;
-      for (int s = s0; s < s1; ++s) by_cost.push_back(s);
+      for (int s = 0; s < d.n_shell; ++s)
+        if (shell_pass[s] == p) by_cost.push_back(s);
       auto cost = [&](int s) { return 3 * shells[s].n_prim + 4 * shells[s].n_ao + 2; };
       std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return cost(a) > cost(b); });
       std::vector<std::vector<int>> part(4);

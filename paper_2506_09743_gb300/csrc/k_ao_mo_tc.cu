@@ -171,6 +171,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
       A[(size_t)(ch * 2 + 0) * tile_words + off] = hi;
       A[(size_t)(ch * 2 + 1) * tile_words + off] = tf32_rna(lo);
     };
+    // two or four consecutive columns of one 16-byte core-matrix row (k even,
+    // resp. k = 0 mod 4) with one 8- or 16-byte store per buffer: a warp's 32
+    // rows then cover every bank instead of a quarter of them
+    auto put2 = [&](int ch, int k, float v0, float v1) {
+      const size_t off = (size_t)(row / 8) * (kPass / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4 + (k % 4);
+      const uint32_t h0 = tf32_rna(v0), h1 = tf32_rna(v1);
+      *reinterpret_cast<uint2*>(A + (size_t)(ch * 2 + 0) * tile_words + off) = make_uint2(h0, h1);
+      *reinterpret_cast<uint2*>(A + (size_t)(ch * 2 + 1) * tile_words + off) =
+          make_uint2(tf32_rna(v0 - __uint_as_float(h0)), tf32_rna(v1 - __uint_as_float(h1)));
+    };
+    auto put4 = [&](int ch, int k, float v0, float v1, float v2, float v3) {
+      const size_t off = (size_t)(row / 8) * (kPass / 4) * 32 + (size_t)(k / 4) * 32 + (row % 8) * 4;
+      const uint32_t h0 = tf32_rna(v0), h1 = tf32_rna(v1), h2 = tf32_rna(v2), h3 = tf32_rna(v3);
+      *reinterpret_cast<uint4*>(A + (size_t)(ch * 2 + 0) * tile_words + off) = make_uint4(h0, h1, h2, h3);
+      *reinterpret_cast<uint4*>(A + (size_t)(ch * 2 + 1) * tile_words + off) =
+          make_uint4(tf32_rna(v0 - __uint_as_float(h0)), tf32_rna(v1 - __uint_as_float(h1)),
+                     tf32_rna(v2 - __uint_as_float(h2)), tf32_rna(v3 - __uint_as_float(h3)));
+    };
     bool ok = true;
     for (int pass = 0; pass < wf.n_pass; ++pass) {
       if (pass > 0) {
@@ -178,8 +196,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
         ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1) && ok;
       }
       // unused columns of the pass are zero (disjoint from the shells' columns)
-      for (int k = wf.pass_cols[pass] + part; k < kPass; k += kParts)
-        for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
+      const unsigned zero_cols = wf.pass_zero[pass];
+      for (int k = part; k < kPass; k += kParts)
+        if ((zero_cols >> k) & 1u)
+          for (int ch = 0; ch < NCH; ++ch) put(ch, k, 0.f);
       const int s_begin = wf.part_off[pass][part], s_end = wf.part_off[pass][part + 1];
       int cur_atom = -1, pow_atom = -1;
       float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, rho = 0.f, irho = 0.f, G = 0.f;
@@ -211,18 +231,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
         if (type == 1) {
           emit(c0, f, RL);
         } else if (type == 2) {
-          emit(c0 + 0, dx * f, dx * RL + tf * gjx);
-          emit(c0 + 1, dy * f, dy * RL + tf * gjy);
-          emit(c0 + 2, dz * f, dz * RL + tf * gjz);
+          const float v0 = dx * f, v1 = dy * f, v2 = dz * f;
+          const float k0 = dx * RL + tf * gjx, k1 = dy * RL + tf * gjy, k2 = dz * RL + tf * gjz;
+          if ((c0 & 1) == 0) {  // uniform across the warp: every row has the same shell
+            put2(0, c0, v0, v1);
+            if (NCH == 2) put2(1, c0, k0, k1);
+          } else {
+            emit(c0 + 0, v0, k0);
+            emit(c0 + 1, v1, k1);
+          }
+          emit(c0 + 2, v2, k2);
         } else if (type == 3) {
           const float fx = f * dx, fy = f * dy, fz = f * dz;
           const float Rx = RL * dx, Ry = RL * dy, Rz = RL * dz;
-          emit(c0 + 0, fx * dx, tf + Rx * dx + 2.f * tf * gjx * dx);
-          emit(c0 + 1, fx * dy, Rx * dy + tf * (gjx * dy + gjy * dx));
-          emit(c0 + 2, fx * dz, Rx * dz + tf * (gjx * dz + gjz * dx));
-          emit(c0 + 3, fy * dy, tf + Ry * dy + 2.f * tf * gjy * dy);
-          emit(c0 + 4, fy * dz, Ry * dz + tf * (gjy * dz + gjz * dy));
-          emit(c0 + 5, fz * dz, tf + Rz * dz + 2.f * tf * gjz * dz);
+          const float v0 = fx * dx, v1 = fx * dy, v2 = fx * dz, v3 = fy * dy, v4 = fy * dz, v5 = fz * dz;
+          const float k0 = tf + Rx * dx + 2.f * tf * gjx * dx, k1 = Rx * dy + tf * (gjx * dy + gjy * dx),
+                      k2 = Rx * dz + tf * (gjx * dz + gjz * dx), k3 = tf + Ry * dy + 2.f * tf * gjy * dy,
+                      k4 = Ry * dz + tf * (gjy * dz + gjz * dy), k5 = tf + Rz * dz + 2.f * tf * gjz * dz;
+          if ((c0 & 3) == 0) {
+            put4(0, c0, v0, v1, v2, v3);
+            put2(0, c0 + 4, v4, v5);
+            if (NCH == 2) {
+              put4(1, c0, k0, k1, k2, k3);
+              put2(1, c0 + 4, k4, k5);
+            }
+          } else {
+            emit(c0 + 0, v0, k0);
+            emit(c0 + 1, v1, k1);
+            emit(c0 + 2, v2, k2);
+            emit(c0 + 3, v3, k3);
+            emit(c0 + 4, v4, k4);
+            emit(c0 + 5, v5, k5);
+          }
         } else {
           if (pow_atom != cur_atom) {
             pow_atom = cur_atom;

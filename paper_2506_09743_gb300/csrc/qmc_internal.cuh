@@ -84,8 +84,8 @@ struct WfDev {
   // tensor-core AO stage: AO b sits in column ao_col[b] of the K dimension,
   // packed into n_pass passes of kTcPass columns (no shell straddles two
   // passes); in pass p, thread part q evaluates the shells
-  // tc_shells[part_off[p][q] .. part_off[p][q+1]), and columns
-  // [pass_cols[p], kTcPass) of the pass are unused (zero).  A list entry is
+  // tc_shells[part_off[p][q] .. part_off[p][q+1]), and the columns of
+  // pass_zero[p] (bit k = column k) are unused (zero).  A list entry is
   // shell | first column within the pass << 8 | type << 16, type 1 + l for a
   // complete s, p or d shell whose AOs sit in canonical Cartesian order
   // (x, y, z; xx, xy, xz, yy, yz, zz) from that column, 0 otherwise
@@ -93,7 +93,7 @@ struct WfDev {
   const int* tc_shells;  // [n_shell]
   int k_pad;             // n_pass * kTcPass (0 when the form has no tensor-core stage)
   int n_pass;
-  int pass_cols[kMaxTcPass];
+  unsigned pass_zero[kMaxTcPass];
   int part_off[kMaxTcPass][5];
 };
 
