@@ -61,10 +61,25 @@ typedef enum {
  *  QMC_MIXED_TF32  FP32 AOs; AO->MO contraction on tcgen05 tensor cores with
  *                  TF32 inputs split into high and low parts (three products,
  *                  FP32 accumulation in tensor memory); FP64 determinants.
- *  QMC_MIXED_BF16  as MIXED_TF32 with BF16 high/low parts (kind::f16).
- * Jastrow and Coulomb terms are FP64 in QMC_FP64 and use FP32 pair
- * arithmetic with FP64 sums in the other forms. */
-typedef enum { QMC_FP64 = 0, QMC_FP32 = 1, QMC_MIXED_TF32 = 2, QMC_MIXED_BF16 = 3 } qmc_precision;
+ *  QMC_MIXED_BF16  not built: QMC_ERR_UNSUPPORTED.
+ *  QMC_FP32X2      AOs and the AO->MO contraction in pairs of FP32 (hi + lo,
+ *                  about 48 significant bits, on the FP32 pipes), Coulomb
+ *                  potential in pairs of FP32, FP64 determinants: MO values
+ *                  within a few 2^-46 of |AO||C|, so that the local energy
+ *                  matches the FP64 form to 2e-4 Ha on every walker away from
+ *                  the nodes (where FP32 AOs leave about one CO walker in six
+ *                  beyond it).
+ * Jastrow terms are FP64 in QMC_FP64 and use FP32 pair arithmetic with
+ * compensated sums in the other forms; the Coulomb potential is FP64 in
+ * QMC_FP64, pairs of FP32 in QMC_FP32X2 and FP32 terms with compensated
+ * sums otherwise.  Backflow wavefunctions run in QMC_FP64 only. */
+typedef enum {
+  QMC_FP64 = 0,
+  QMC_FP32 = 1,
+  QMC_MIXED_TF32 = 2,
+  QMC_MIXED_BF16 = 3,
+  QMC_FP32X2 = 4
+} qmc_precision;
 
 /* Compiled limits (QMC_ERR_UNSUPPORTED beyond them). */
 #define QMC_MAX_ATOMS 16

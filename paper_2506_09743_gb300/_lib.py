@@ -15,8 +15,9 @@ LIB_PATH = os.path.join(HERE, "libqmc_gb300.so")
 QMC_OK, QMC_ERR_ARG, QMC_ERR_OOM, QMC_ERR_CUDA, QMC_ERR_TIMEOUT, QMC_ERR_UNSUPPORTED = range(6)
 STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA", 4: "QMC_ERR_TIMEOUT",
                 5: "QMC_ERR_UNSUPPORTED"}
-QMC_FP64, QMC_FP32, QMC_MIXED_TF32, QMC_MIXED_BF16 = range(4)
-PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "mixed_tf32": QMC_MIXED_TF32, "mixed_bf16": QMC_MIXED_BF16}
+QMC_FP64, QMC_FP32, QMC_MIXED_TF32, QMC_MIXED_BF16, QMC_FP32X2 = range(5)
+PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "mixed_tf32": QMC_MIXED_TF32, "mixed_bf16": QMC_MIXED_BF16,
+              "fp32x2": QMC_FP32X2}
 
 # every exported symbol declared in include/qmc.h
 EXPORTED = (

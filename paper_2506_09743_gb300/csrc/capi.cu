@@ -278,6 +278,27 @@ qmc_status build_tables(qmc_wf* wf) {
   }
   if ((int)shells.size() > kMaxShells) return fail(QMC_ERR_UNSUPPORTED, "too many shells");
   d.n_shell = (int)shells.size();
+  // ---- pairs of FP32 of the shell parameters (FP32X2 form), and the
+  // canonical order of complete s, p and d shells: the FP32X2 kernel
+  // evaluates such a shell's AOs in closed form in the order s; x, y, z; xx,
+  // xy, xz, yy, yz, zz and reads MO-table row x2_row[b] for AO b
+  std::vector<int> x2_row(nao);
+  for (ShellDev& q : shells) {
+    for (int p = 0; p < q.n_prim; ++p) {
+      q.expo_lo[p] = (float)(q.expo[p] - (double)q.expo_f[p]);
+      q.coef_lo[p] = (float)(q.coef[p] - (double)q.coef_f[p]);
+    }
+    std::vector<int> canon(q.n_ao, -1);
+    bool complete = q.l <= 2 && q.n_ao == (q.l + 1) * (q.l + 2) / 2;
+    for (int k = 0; k < q.n_ao && complete; ++k) {
+      const int pw = ao_pow[q.ao_first + k];
+      const int j = tc_canonical_index(q.l, pw & 15, (pw >> 4) & 15, (pw >> 8) & 15);
+      for (int k2 = 0; k2 < k; ++k2) complete = complete && canon[k2] != j;
+      canon[k] = j;
+    }
+    q.canon = complete ? 1 + q.l : 0;
+    for (int k = 0; k < q.n_ao; ++k) x2_row[q.ao_first + k] = q.ao_first + (complete ? canon[k] : k);
+  }
   // ---- tensor-core AO stage: pack the shells into K-passes of kTcPass
   // columns, then deal each pass's shells to the four thread parts by
   // estimated cost, largest first, each part's list kept in shell order so
@@ -369,11 +390,23 @@ qmc_status build_tables(qmc_wf* wf) {
   }
   std::vector<double> mo64((size_t)nao * nmo);
   std::vector<float> mo32((size_t)nao * nmo);
+  std::vector<float> mo_x2((size_t)nao * nmo * 2);  // rows in x2_row order, (hi, lo)
   for (int b = 0; b < nao; ++b)
     for (int m = 0; m < nmo; ++m) {
-      mo64[(size_t)b * nmo + m] = h.mo[(size_t)b * nmo + m] * ang[b];
-      mo32[(size_t)b * nmo + m] = (float)mo64[(size_t)b * nmo + m];
+      const double c = h.mo[(size_t)b * nmo + m] * ang[b];
+      mo64[(size_t)b * nmo + m] = c;
+      mo32[(size_t)b * nmo + m] = (float)c;
+      const size_t o = 2 * ((size_t)x2_row[b] * nmo + m);
+      mo_x2[o] = (float)c;
+      mo_x2[o + 1] = (float)(c - (double)(float)c);
     }
+  // 2^(j/64), j = 0..63, as pairs of FP32 for the FP32X2 exponential
+  std::vector<float> exp_tab(128);
+  for (int j = 0; j < 64; ++j) {
+    const long double v = std::exp2((long double)j / 64.0L);
+    exp_tab[2 * j] = (float)v;
+    exp_tab[2 * j + 1] = (float)(v - (long double)exp_tab[2 * j]);
+  }
 
   // ---- determinants: unique excitation records per spin.  The expansion is
   // stored sorted by (rank up, rank down): the determinant stage hands
@@ -477,7 +510,8 @@ qmc_status build_tables(qmc_wf* wf) {
       {det_w_sorted.data(), sizeof(double) * ndet},      {tc_hi.data(), sizeof(uint32_t) * tc_hi.size()},
       {tc_lo.data(), sizeof(uint32_t) * tc_lo.size()},  {ang.data(), sizeof(double) * nao},
       {h.prim_start.data(), sizeof(int) * (nao + 1)}, {ao_col.data(), sizeof(int) * nao},
-      {tc_shells.data(), sizeof(int) * tc_shells.size()}, {det_tab.data(), sizeof(int) * det_tab.size()}};
+      {tc_shells.data(), sizeof(int) * tc_shells.size()}, {det_tab.data(), sizeof(int) * det_tab.size()},
+      {mo_x2.data(), sizeof(float) * mo_x2.size()},      {exp_tab.data(), sizeof(float) * exp_tab.size()}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
   void* blob = nullptr;
@@ -513,6 +547,8 @@ qmc_status build_tables(qmc_wf* wf) {
   d.ao_col = reinterpret_cast<const int*>(ptr[11]);
   d.tc_shells = reinterpret_cast<const int*>(ptr[12]);
   d.det_tab = reinterpret_cast<const int4*>(ptr[13]);
+  d.mo_x2 = reinterpret_cast<const float2*>(ptr[14]);
+  d.exp_tab = reinterpret_cast<const float*>(ptr[15]);
   // the previous tables may still be read by work in flight on any stream
   if (wf->blob) {
     cudaDeviceSynchronize();
@@ -543,7 +579,7 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
   if (nmo < 1 || nmo > QMC_MAX_MO || !mos->coeff) return fail(QMC_ERR_ARG, "bad MO table");
   if (nmo < nup || nmo < ndn) return fail(QMC_ERR_ARG, "fewer MOs than electrons of one spin");
   const int prec = opt->precision;
-  if (prec < QMC_FP64 || prec > QMC_MIXED_BF16) return fail(QMC_ERR_ARG, "bad precision");
+  if (prec < QMC_FP64 || prec > QMC_FP32X2) return fail(QMC_ERR_ARG, "bad precision");
   if (!dets->weight || !dets->exc || dets->n_det < 1 || dets->n_det > kMaxDets)
     return fail(QMC_ERR_ARG, "bad determinant list");
   const int n_prim = basis->ao_prim_start[nao];
@@ -673,8 +709,9 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   if (mapped) walkers = stage;
   mark(wf, 1, st);
   mark(wf, 2, st);
-  s = launch_status(tc ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag, st)
-                       : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, v, nch, st),
+  s = launch_status(tc                                ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag, st)
+                    : wf->precision == QMC_FP32X2 ? launch_ao_mo_x2(d, walkers, W, ldw, v, nch, st)
+                                                  : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, v, nch, st),
                     "ao_mo");
   if (s) return s;
   mark(wf, 3, st);

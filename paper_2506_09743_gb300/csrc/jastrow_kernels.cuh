@@ -421,7 +421,19 @@ struct KahanF {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-template <int NMAX, bool MB>
+// r_i - r_j (d) of two positions held as float pairs, as a pair
+__device__ __forceinline__ f32x2 pair_diff_x2(float ah, float al, float bh, float bl) {
+  const f32x2 s = two_sum(ah, -bh);
+  return two_sum(s.hi, x2_add_rn(s.lo, x2_sub_rn(al, bl)));
+}
+// 1 / |v| of a difference vector given as pairs
+__device__ __forceinline__ f32x2 inv_dist_x2(f32x2 x, f32x2 y, f32x2 z) { return rsqrt_x2(x * x + y * y + z * z); }
+
+// VX2 (the QMC_FP32X2 form): the Coulomb potential is summed in pairs of
+// FP32.  Its terms 1/r_ij and Z/r_ia grow without bound at coalescence
+// points, where FP32 terms would cost 2^-24 of several hundred Ha; the
+// Jastrow terms are bounded and stay FP32.
+template <int NMAX, bool MB, bool VX2>
 __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                      int64_t ldw, double* __restrict__ copy,
                                                      float* __restrict__ gradJ, double* __restrict__ jscal,
@@ -445,6 +457,7 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
       g[i][d] = 0.f;
     }
   KahanF J, V, lap;
+  f32x2 vx(0.f, 0.f);  // V in pairs (VX2)
 #pragma unroll
   for (int i = 0; i < NMAX; ++i) {
 #pragma unroll
@@ -460,7 +473,12 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
         const float rden = __frcp_rn(1.0f + b * dist);
         const float u1 = w0 * rden * rden;
         J.add(w0 * dist * rden);
-        V.add(inv);
+        if (VX2)
+          vx = vx + inv_dist_x2(pair_diff_x2(rh[i][0], rl[i][0], rh[j][0], rl[j][0]),
+                                pair_diff_x2(rh[i][1], rl[i][1], rh[j][1], rl[j][1]),
+                                pair_diff_x2(rh[i][2], rl[i][2], rh[j][2], rl[j][2]));
+        else
+          V.add(inv);
         if (deriv) {
           lap.add(2.0f * (-2.0f * b * u1 * rden + 2.0f * u1 * inv));
           const float s = u1 * inv;
@@ -479,10 +497,17 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
 #pragma unroll
     for (int i = 0; i < NMAX; ++i)
       if (i < n) {
-        const float dx = (rh[i][0] - ah[0]) + (rl[i][0] - al[0]);
-        const float dy = (rh[i][1] - ah[1]) + (rl[i][1] - al[1]);
-        const float dz = (rh[i][2] - ah[2]) + (rl[i][2] - al[2]);
-        V.add(-zh * rsqrtf(dx * dx + dy * dy + dz * dz));
+        if (VX2) {
+          vx = vx - inv_dist_x2(pair_diff_x2(rh[i][0], rl[i][0], ah[0], al[0]),
+                                pair_diff_x2(rh[i][1], rl[i][1], ah[1], al[1]),
+                                pair_diff_x2(rh[i][2], rl[i][2], ah[2], al[2])) *
+                        f32x2(zh, zl);
+        } else {
+          const float dx = (rh[i][0] - ah[0]) + (rl[i][0] - al[0]);
+          const float dy = (rh[i][1] - ah[1]) + (rl[i][1] - al[1]);
+          const float dz = (rh[i][2] - ah[2]) + (rl[i][2] - al[2]);
+          V.add(-zh * rsqrtf(dx * dx + dy * dy + dz * dz));
+        }
       }
   }
   if (MB) {
@@ -507,7 +532,7 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
   }
   jscal[w] = J.value();
   jscal[ldm + w] = lap.value();
-  jscal[2 * ldm + w] = V.value() + wf.vnn;
+  jscal[2 * ldm + w] = (VX2 ? widen(vx) : V.value()) + wf.vnn;
 }
 
 // Launch one kernel instance; NM is the electron-count bracket.  If copy is
@@ -521,9 +546,12 @@ cudaError_t launch_jastrow_nm(const WfDev& wf, int prec, const double* walkers, 
   if (prec == QMC_FP64)
     k_jastrow_f64<NM, MB><<<grid, block, 0, st>>>(wf, walkers, W, ldw, copy, static_cast<double*>(ws.gradJ),
                                                   ws.jscal, ws.ldm, derivs);
+  else if (prec == QMC_FP32X2)
+    k_jastrow_f32<NM, MB, true><<<grid, block, 0, st>>>(wf, walkers, W, ldw, copy, static_cast<float*>(ws.gradJ),
+                                                        ws.jscal, ws.ldm, wf.jb_f, wf.w0p_f, wf.w0a_f, derivs);
   else
-    k_jastrow_f32<NM, MB><<<grid, block, 0, st>>>(wf, walkers, W, ldw, copy, static_cast<float*>(ws.gradJ),
-                                                  ws.jscal, ws.ldm, wf.jb_f, wf.w0p_f, wf.w0a_f, derivs);
+    k_jastrow_f32<NM, MB, false><<<grid, block, 0, st>>>(wf, walkers, W, ldw, copy, static_cast<float*>(ws.gradJ),
+                                                         ws.jscal, ws.ldm, wf.jb_f, wf.w0p_f, wf.w0a_f, derivs);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/qmc.h"
+#include "f32x2.cuh"
 
 namespace qmc {
 
@@ -37,11 +38,15 @@ constexpr int kMaxTcPass = 16;   // passes (QMC_MAX_AO columns, gaps of < kMaxSh
 // folded into coef; the per-AO angular factor is folded into the MO table.
 struct ShellDev {
   int atom, kind, kn, l;
-  int n_prim, ao_first, n_ao, pad;
+  int n_prim, ao_first, n_ao;
+  int canon;  // 1 + l for a complete Cartesian s, p or d shell, else 0 (FP32X2 form:
+              // its MO table rows are in the canonical order s; x, y, z; xx, xy, xz, yy, yz, zz)
   double expo[QMC_MAX_PRIM];
   double coef[QMC_MAX_PRIM];
   float expo_f[QMC_MAX_PRIM];  // FP32 copies: FP32 kernels must not convert
   float coef_f[QMC_MAX_PRIM];  // (double->float runs on the FP64 pipe)
+  float expo_lo[QMC_MAX_PRIM];  // expo - expo_f and coef - coef_f as floats: the
+  float coef_lo[QMC_MAX_PRIM];  // pairs (hi, lo) of the FP32X2 form (2^-48)
 };
 
 // Everything a kernel needs, passed by value (pointers are device memory).
@@ -68,6 +73,8 @@ struct WfDev {
   const int* ao_pow;       // [n_ao] kx | ky << 4 | kz << 8
   const double* mo64;      // [n_ao][n_mo] MO coefficients x AO angular factors
   const float* mo32;       // same, FP32
+  const float2* mo_x2;     // same as pairs of FP32 (hi, lo) for the FP32X2 form
+  const float* exp_tab;    // [64][2] 2^(j/64) as pairs: exp of the FP32X2 form
   const int* exc;          // [2][kMaxExc][5] rank, h1, h2, p1, p2
   const int* det_idx;      // [n_det][2] excitation index per spin
   const double* det_w;     // [n_det]
@@ -111,6 +118,9 @@ struct Workspace {
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// the precision form keeps its Jastrow gradient in FP64 (QMC_FP64) or FP32
+inline bool grad_fp64(int prec) { return prec == QMC_FP64; }
+
 // padded orbital count of an MO row: the tensor-core forms always use 16
 inline int mo_row_pad(int n_mo, bool tensor_core) {
   if (tensor_core) return 16;
@@ -149,6 +159,8 @@ __device__ __forceinline__ double widen(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ double widen(double d) { return d; }
+// hi + lo of a pair, exact in FP64 (|lo| <= 2^-24 |hi|: at most 48 bits)
+__device__ __forceinline__ double widen(f32x2 a) { return widen(a.hi) + widen(a.lo); }
 
 // Bitwise select c ? x : y, opaque to the optimiser.  Register arrays that
 // are permuted by runtime pivot indices stay in registers (a plain select
@@ -240,6 +252,9 @@ cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int
                            const Workspace& ws, bool derivs, cudaStream_t st);
 cudaError_t launch_ao_mo_simt(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
                               const Workspace& ws, int nch, cudaStream_t st);
+// pairs of FP32 (QMC_FP32X2 form)
+cudaError_t launch_ao_mo_x2(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                            int nch, cudaStream_t st);
 cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
                             const Workspace& ws, int nch, int* err_flag, cudaStream_t st);
 cudaError_t launch_det(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,

@@ -6,7 +6,7 @@ import torch
 import qmc_inputs as qi
 from oracle import qmc_oracle as O
 
-from gpu_common import fp64_check, mixed_check, oracle_reference
+from gpu_common import fp64_check, oracle_reference, reduced_check
 
 pytestmark = pytest.mark.gpu
 
@@ -51,13 +51,13 @@ def test_fp64_parity(pkg, name):
 
 
 @pytest.mark.parametrize("name", ["h2", "lih", "co"])
-@pytest.mark.parametrize("precision", ["fp32", "mixed_tf32"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed_tf32", "fp32x2"])
 def test_reduced_precision_parity(pkg, name, precision):
     mol = MOLS[name]()
     r = qi.walkers(mol, 1000, seed=22)
     E_ref, lp_ref, sens = oracle_reference(mol, r)
     E, lp = _run(pkg, mol, r, precision)
-    st = mixed_check(E, E_ref, sens)
+    st = reduced_check(precision, E, E_ref, sens)
     print(f"{name} {precision} |dE| Ha {st}")
 
 
@@ -94,7 +94,7 @@ def _co_with_general_shells():
         prim_exp=np.asarray(pexp), prim_coef=np.asarray(pcoef), mo_coeff=mo)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_tf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_tf32", "fp32x2"])
 def test_general_shells_parity(pkg, precision):
     """f shells and incomplete shells take the general angular path of the AO
     stages (the tensor-core stage evaluates complete s/p/d shells in a
@@ -106,10 +106,10 @@ def test_general_shells_parity(pkg, precision):
     if precision == "fp64":
         fp64_check(E, E_ref, sens, min_within=0.98)
     else:
-        mixed_check(E, E_ref, sens)
+        reduced_check(precision, E, E_ref, sens)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed_tf32"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tf32", "fp32x2"])
 @pytest.mark.parametrize("n_det", [1, 100, 1716])
 def test_explicit_method_parity(pkg, precision, n_det):
     """Explicit per-excitation LU (the baseline of the paper's comparison,
@@ -132,7 +132,7 @@ def test_explicit_method_parity(pkg, precision, n_det):
         scale = np.maximum(1.0, np.abs(lp_ref))
         assert np.all(np.abs(lp - lp_ref) <= 128 * 2.0 ** -53 * sens * scale)
     else:
-        mixed_check(E, E_ref, sens)
+        reduced_check(precision, E, E_ref, sens)
     # both methods see the same MO values; they differ by rounding only
     Et = out["table"][0]
     bound = 128 * (2.0 ** -53) * sens * np.maximum(1.0, np.abs(E_ref))
@@ -140,7 +140,7 @@ def test_explicit_method_parity(pkg, precision, n_det):
         assert np.all(np.abs(E - Et) <= 2 * bound)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_tf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_tf32", "fp32x2"])
 @pytest.mark.parametrize("name", ["lih", "co"])
 def test_manybody_jastrow_parity(pkg, name, precision):
     """Electron-nucleus and electron-electron-nucleus Jastrow kernels (App. D)
@@ -155,7 +155,7 @@ def test_manybody_jastrow_parity(pkg, name, precision):
         scale = np.maximum(1.0, np.abs(lp_ref))
         assert np.all(np.abs(lp - lp_ref) <= 128 * 2.0 ** -53 * sens * scale + 1e-13 * scale)
     else:
-        mixed_check(E, E_ref, sens)
+        reduced_check(precision, E, E_ref, sens)
     # the terms change the energy (the test is not vacuous)
     E0, _, _ = oracle_reference(base, r)
     assert np.abs(E_ref - E0).max() > 1e-3
@@ -227,7 +227,7 @@ def test_manybody_een_shared_memory_limit(pkg):
     e, _ = wf.local_energy(torch.tensor(qi.to_soa(r), device="cuda"))
     wf.close()
     E_ref, _, sens = oracle_reference(mol, r)
-    mixed_check(e.cpu().numpy(), E_ref, sens)
+    reduced_check("mixed_tf32", e.cpu().numpy(), E_ref, sens)
 
 
 def test_closed_forms_on_gpu(pkg):
@@ -241,7 +241,7 @@ def test_closed_forms_on_gpu(pkg):
     r1, r2 = np.linalg.norm(r[:, 0], axis=-1), np.linalg.norm(r[:, 1], axis=-1)
     r12 = np.linalg.norm(r[:, 0] - r[:, 1], axis=-1)
     ref = -z * z + (z - 2) * (1 / r1 + 1 / r2) + 1 / r12
-    for prec, tol in (("fp64", 1e-12), ("mixed_tf32", 1e-4)):
+    for prec, tol in (("fp64", 1e-12), ("mixed_tf32", 1e-4), ("fp32x2", 1e-9)):
         E, _ = _run(pkg, he, r, prec)
         assert np.abs(E - ref).max() < tol * np.maximum(1, np.abs(ref)).max(), prec
 
@@ -251,12 +251,12 @@ def test_small_and_ragged_batches(pkg, W):
     mol = qi.make_co(n_det=20)
     r = qi.walkers(mol, W, seed=6)
     E_ref, _, sens = oracle_reference(mol, r)
-    for prec in ("fp64", "mixed_tf32"):
+    for prec in ("fp64", "mixed_tf32", "fp32x2"):
         E, _ = _run(pkg, mol, r, prec, ldw_pad=3)
         if prec == "fp64":
             fp64_check(E, E_ref, sens, min_within=0.0 if W < 100 else 0.99)
         else:
-            mixed_check(E, E_ref, sens)
+            reduced_check(prec, E, E_ref, sens)
 
 
 def test_zero_walkers_is_a_noop(pkg):
@@ -374,7 +374,7 @@ def test_full_size_co_sampled_parity(pkg):
     idx = np.random.default_rng(0).choice(W, size=256, replace=False)
     E_ref, _, sens = oracle_reference(mol, r[idx])
     x = torch.tensor(qi.to_soa(r), device="cuda")
-    for prec in ("fp64", "mixed_tf32"):
+    for prec in ("fp64", "mixed_tf32", "fp32x2"):
         wf = pkg.Wavefunction(mol, precision=prec)
         e, _ = wf.local_energy(x)
         torch.cuda.synchronize()
@@ -383,7 +383,7 @@ def test_full_size_co_sampled_parity(pkg):
         if prec == "fp64":
             fp64_check(E[idx], E_ref, sens)
         else:
-            mixed_check(E[idx], E_ref, sens)
+            print(prec, reduced_check(prec, E[idx], E_ref, sens))
         wf.close()
 
 
