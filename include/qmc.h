@@ -217,6 +217,31 @@ qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_wa
 qmc_status qmc_local_energy_noalloc(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw,
                                     double* e_loc, double* log_psi, void* stream);
 
+/* Bounded device waits (an engineering aid; the paper has no counterpart).  The
+ * tensor-core AO stage (QMC_MIXED_TF32) waits on mbarriers for its MMAs;
+ * every such wait is bounded (about one second of SM clock).  A wait that
+ * gives up makes its block record the failure, wait (bounded again) for the
+ * MMAs it already issued, write NaN for the MO values of the walkers it had
+ * left and stop, so the affected walkers' results are NaN; nothing hangs.
+ * The failure is reported as QMC_ERR_TIMEOUT:
+ *  - by qmc_local_energy_host, which synchronises anyway;
+ *  - in the status of a server result (qmc_result.status);
+ *  - for the stream-ordered calls (qmc_local_energy, qmc_local_energy_noalloc,
+ *    qmc_sample), by qmc_check_status below.
+ * The other precision forms run no device waits. */
+
+/* Waits for the work queued on `stream` and returns QMC_ERR_TIMEOUT if a
+ * bounded device wait of this wavefunction's kernels gave up since the last
+ * check (then clears the record), QMC_OK otherwise. */
+qmc_status qmc_check_status(qmc_wf* wf, void* stream);
+
+/* Testing aid: the budget of each bounded device wait in SM clock cycles
+ * (default 2^31, about one second).  0 makes every wait give up at once on a
+ * healthy GPU, which exercises the timeout path (QMC_ERR_TIMEOUT, NaN
+ * results); the drain of the MMAs already issued always keeps the default
+ * budget.  Applies to the calls that follow.  QMC_ERR_ARG if negative. */
+qmc_status qmc_set_wait_limit(qmc_wf* wf, int64_t cycles);
+
 /* Metropolis-Hastings walker steps (App. B): every step moves all electrons
  * of a walker by step * z, z ~ N(0, 1) per coordinate, and accepts with
  * probability min(1, |Psi'/Psi|^2).  Random numbers: Philox4x32-10 with key
@@ -396,7 +421,8 @@ typedef struct {
 
 typedef struct {
   int64_t ticket;
-  int32_t status;       /* QMC_OK or the error of this request */
+  int32_t status;       /* QMC_OK or the error of this request (QMC_ERR_TIMEOUT: a bounded
+                           device wait gave up; the statistics are NaN) */
   int32_t wf_id;
   int64_t n_walkers;
   double e_mean;        /* mean local energy, Ha */

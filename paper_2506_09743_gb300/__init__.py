@@ -191,6 +191,15 @@ class Wavefunction:
         code = {"table": 0, "explicit": 1}[method]
         _lib.check(self._lib.qmc_set_det_method(self._h, code))
 
+    def check_status(self, stream=None):
+        """Raise QmcError(QMC_ERR_TIMEOUT) if a bounded device wait gave up
+        since the last check (waits for the stream first)."""
+        _lib.check(self._lib.qmc_check_status(self._h, _stream_handle(stream)))
+
+    def set_wait_limit(self, cycles: int):
+        """Testing aid: budget of each bounded device wait in SM cycles (0 = give up at once)."""
+        _lib.check(self._lib.qmc_set_wait_limit(self._h, int(cycles)))
+
     def set_timing(self, enable: bool = True):
         """Record per-stage CUDA events on the call's stream (tracing aid)."""
         _lib.check(self._lib.qmc_set_timing(self._h, 1 if enable else 0))

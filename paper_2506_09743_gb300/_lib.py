@@ -16,6 +16,7 @@ QMC_OK, QMC_ERR_ARG, QMC_ERR_OOM, QMC_ERR_CUDA, QMC_ERR_TIMEOUT, QMC_ERR_UNSUPPO
 STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA", 4: "QMC_ERR_TIMEOUT",
                 5: "QMC_ERR_UNSUPPORTED"}
 QMC_FP64, QMC_FP32, QMC_MIXED_TF32, QMC_MIXED_BF16, QMC_FP32X2 = range(5)
+NOALLOC_SCRATCH_BYTES = 64 << 20  # QMC_NOALLOC_SCRATCH_BYTES of include/qmc.h
 PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "mixed_tf32": QMC_MIXED_TF32, "mixed_bf16": QMC_MIXED_BF16,
               "fp32x2": QMC_FP32X2}
 
@@ -26,7 +27,7 @@ EXPORTED = (
     "qmc_set_params", "qmc_server_create", "qmc_server_destroy", "qmc_server_add_wf", "qmc_server_submit",
     "qmc_server_progress", "qmc_server_results", "qmc_server_set_policy", "qmc_server_free_bytes", "qmc_server_clock",
     "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method", "qmc_optimize", "qmc_force_batches", "qmc_set_manybody_jastrow",
-    "qmc_last_error",
+    "qmc_check_status", "qmc_set_wait_limit", "qmc_last_error",
 )
 
 PD = POINTER(c_double)
@@ -150,6 +151,10 @@ def load(path: str = LIB_PATH):
     lib.qmc_server_clock.restype = c_double
     lib.qmc_server_last_error.argtypes = []
     lib.qmc_server_last_error.restype = c_char_p
+    lib.qmc_check_status.argtypes = [c_void_p, c_void_p]
+    lib.qmc_check_status.restype = c_int32
+    lib.qmc_set_wait_limit.argtypes = [c_void_p, c_int64]
+    lib.qmc_set_wait_limit.restype = c_int32
     lib.qmc_last_error.argtypes = []
     lib.qmc_last_error.restype = c_char_p
     _lib = lib

@@ -202,6 +202,7 @@ qmc_status build_tables(qmc_wf* wf) {
     d.atom_z[a] = h.z[a];
   }
   d.vnn = vnn_of(d);
+  d.wait_cycles = wf->wait_cycles;
   if (h.w != 0.0 && prec != QMC_FP64)
     return fail(QMC_ERR_UNSUPPORTED, "backflow wavefunctions run in the FP64 form only");
   d.mb_en = h.jen.empty() ? 0 : 1;
@@ -604,6 +605,16 @@ qmc_status qmc_create_wf(const qmc_atoms* atoms, const qmc_basis* basis, const q
   h.det_exc.assign(dets->exc, dets->exc + 10 * (size_t)dets->n_det);
   h.w0p = jastrow->w0_par; h.w0a = jastrow->w0_anti; h.b = jastrow->b; h.w = jastrow->backflow_w;
   qmc_status st = build_tables(wf);
+  if (st == QMC_OK) {  // the sticky status word of the bounded device waits, and its host mirror
+    DeviceGuard guard(wf->device);
+    cudaError_t e = cudaMalloc(&wf->err_wf, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(wf->err_wf, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&wf->status_host), sizeof(int), 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      st = fail(QMC_ERR_OOM, std::string("status word: ") + cudaGetErrorString(e));
+    }
+  }
   if (st == QMC_OK) {  // the proposal kernels' Box-Muller tables on this device
     DeviceGuard guard(wf->device);
     const cudaError_t e = init_box_muller_tables();
@@ -621,13 +632,23 @@ void qmc_destroy_wf(qmc_wf* wf) {
   if (!wf) return;
   {
     DeviceGuard guard(wf->device);
-    if (wf->blob) cudaFree(wf->blob);
-    if (wf->ws) cudaFree(wf->ws);
-    if (wf->stage) cudaFree(wf->stage);
-    if (wf->gws) cudaFree(wf->gws);
+    // a failure here has no caller to report to: it is recorded as the
+    // thread's qmc_last_error() text and cleared from the runtime
+    auto rel = [](cudaError_t e, const char* what) {
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_err = std::string("qmc_destroy_wf: ") + what + ": " + cudaGetErrorString(e);
+      }
+    };
+    if (wf->blob) rel(cudaFree(wf->blob), "tables");
+    if (wf->ws) rel(cudaFree(wf->ws), "workspace");
+    if (wf->stage) rel(cudaFree(wf->stage), "staging buffer");
+    if (wf->gws) rel(cudaFree(wf->gws), "gradient scratch");
+    if (wf->err_wf) rel(cudaFree(wf->err_wf), "status word");
+    if (wf->status_host) rel(cudaFreeHost(wf->status_host), "host status word");
     for (auto& e : wf->tev)
-      if (e) cudaEventDestroy(e);
-    if (wf->cap_stream) cudaStreamDestroy(wf->cap_stream);
+      if (e) rel(cudaEventDestroy(e), "timing event");
+    if (wf->cap_stream) rel(cudaStreamDestroy(wf->cap_stream), "capture stream");
   }
   delete wf;
 }
@@ -696,10 +717,6 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   }
   const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
   const int nch = kinetic ? 2 : 1;
-  if (tc) {
-    qmc_status s = launch_status(cudaMemsetAsync(err_flag, 0, sizeof(int), st), "error flag reset");
-    if (s) return s;
-  }
   const Workspace& v = ws;
   mark(wf, 0, st);
   qmc_status s = launch_status(
@@ -709,7 +726,8 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   if (mapped) walkers = stage;
   mark(wf, 1, st);
   mark(wf, 2, st);
-  s = launch_status(tc                                ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag, st)
+  s = launch_status(tc                                ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag,
+                                                                    wf->err_wf, st)
                     : wf->precision == QMC_FP32X2 ? launch_ao_mo_x2(d, walkers, W, ldw, v, nch, st)
                                                   : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, v, nch, st),
                     "ao_mo");
@@ -726,8 +744,22 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   return QMC_OK;
 }
 
-qmc_status qmc_local_energy(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_loc,
-                            double* log_psi, void* workspace, size_t workspace_bytes_, void* stream) {
+}  // extern "C"
+
+// Only the tensor-core forms run bounded device waits; their calls clear the
+// workspace's status word first (a later read tells whether this call's waits
+// gave up).
+static bool has_device_waits(const qmc_wf* wf) {
+  return wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
+}
+
+static qmc_status reset_status(const qmc_wf* wf, int* err_flag, cudaStream_t st) {
+  if (!has_device_waits(wf)) return QMC_OK;
+  return launch_status(cudaMemsetAsync(err_flag, 0, sizeof(int), st), "status word reset");
+}
+
+qmc_status local_energy_call(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_loc,
+                             double* log_psi, void* workspace, size_t workspace_bytes_, void* stream, bool reset) {
   if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
   if (n_walkers < 0 || ldw < n_walkers) return fail(QMC_ERR_ARG, "bad walker count or leading dimension");
   if (n_walkers == 0) return QMC_OK;
@@ -739,8 +771,16 @@ qmc_status qmc_local_energy(qmc_wf* wf, const double* walkers, int64_t n_walkers
   if (s) return s;
   int* err_flag;
   Workspace ws = carve(wf, base, n_walkers, &err_flag);
-  return eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, log_psi,
-                   static_cast<cudaStream_t>(stream));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (reset && (s = reset_status(wf, err_flag, st))) return s;
+  return eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, log_psi, st);
+}
+
+extern "C" {
+
+qmc_status qmc_local_energy(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_loc,
+                            double* log_psi, void* workspace, size_t workspace_bytes_, void* stream) {
+  return local_energy_call(wf, walkers, n_walkers, ldw, e_loc, log_psi, workspace, workspace_bytes_, stream, true);
 }
 
 qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_walkers, double* e_loc,
@@ -793,12 +833,18 @@ qmc_status qmc_local_energy_host(qmc_wf* wf, const double* walkers, int64_t n_wa
   if (s) return s;
   int* err_flag;
   Workspace ws = carve(wf, base, W, &err_flag);
+  if ((s = reset_status(wf, err_flag, st))) return s;
   s = eval_path(wf, d_in, W, W, ws, err_flag, true, d_e, log_psi ? d_lp : nullptr, st, mapped, d_in);
   if (s) return s;
   cudaError_t e = cudaMemcpyAsync(e_loc, d_e, sizeof(double) * W, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && log_psi) e = cudaMemcpyAsync(log_psi, d_lp, sizeof(double) * W, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && has_device_waits(wf))
+    e = cudaMemcpyAsync(wf->status_host, err_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? QMC_OK : cuda_fail(e, "result download");
+  if (e != cudaSuccess) return cuda_fail(e, "result download");
+  if (has_device_waits(wf) && *wf->status_host != 0)
+    return fail(QMC_ERR_TIMEOUT, "a bounded device wait gave up: the affected walkers' results are NaN");
+  return QMC_OK;
 }
 
 // Metropolis steps as a CUDA graph: one step (proposal, value path on the
@@ -854,9 +900,11 @@ static qmc_status sample_graph(qmc_wf* wf, double* walkers, int64_t W, int64_t l
   return QMC_OK;
 }
 
-qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_steps, double step,
-                      uint64_t seed, uint64_t first_walker, uint64_t step_offset, double* log_psi,
-                      int64_t* n_accept, void* workspace, size_t workspace_bytes_, void* stream) {
+}  // extern "C"
+
+qmc_status sample_call(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_steps, double step,
+                       uint64_t seed, uint64_t first_walker, uint64_t step_offset, double* log_psi, int64_t* n_accept,
+                       void* workspace, size_t workspace_bytes_, void* stream, bool reset) {
   if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
   if (n_walkers < 0 || ldw < n_walkers || n_steps < 0) return fail(QMC_ERR_ARG, "bad sizes");
   if (n_walkers == 0) return QMC_OK;
@@ -870,6 +918,7 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
   int* err_flag;
   Workspace ws = carve(wf, base, n_walkers, &err_flag);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (reset && (s = reset_status(wf, err_flag, st))) return s;
   s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, false, nullptr, ws.lp, st);
   if (s) return s;
   Workspace wp = ws;  // value path on the proposals: walkers = prop, ldw = ldm
@@ -894,6 +943,50 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
     cudaError_t e = cudaMemcpyAsync(log_psi, ws.lp, sizeof(double) * n_walkers, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "log_psi copy");
   }
+  return QMC_OK;
+}
+
+extern "C" {
+
+qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_steps, double step,
+                      uint64_t seed, uint64_t first_walker, uint64_t step_offset, double* log_psi,
+                      int64_t* n_accept, void* workspace, size_t workspace_bytes_, void* stream) {
+  return sample_call(wf, walkers, n_walkers, ldw, n_steps, step, seed, first_walker, step_offset, log_psi, n_accept,
+                     workspace, workspace_bytes_, stream, true);
+}
+
+}  // extern "C"
+
+int* workspace_status(const qmc_wf* wf, void* workspace, int64_t n_walkers) {
+  int* flag = nullptr;
+  carve(wf, workspace, n_walkers, &flag);
+  return flag;
+}
+
+extern "C" {
+
+qmc_status qmc_check_status(qmc_wf* wf, void* stream) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(wf->status_host, wf->err_wf, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (*wf->status_host == 0) return QMC_OK;
+  e = cudaMemsetAsync(wf->err_wf, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status reset");
+  return fail(QMC_ERR_TIMEOUT,
+              "a bounded device wait gave up since the last check: the affected walkers' results are NaN");
+}
+
+qmc_status qmc_set_wait_limit(qmc_wf* wf, int64_t cycles) {
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  if (cycles < 0) return fail(QMC_ERR_ARG, "negative wait budget");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  wf->wait_cycles = cycles;
+  wf->dev.wait_cycles = wf->wait_cycles;
   return QMC_OK;
 }
 
@@ -941,8 +1034,10 @@ qmc_status qmc_local_energy_noalloc(qmc_wf* wf, const double* walkers, int64_t n
   }
   int* err_flag;
   Workspace ws = carve(wf, base, n_walkers, &err_flag);
-  return eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, log_psi,
-                   static_cast<cudaStream_t>(stream));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  qmc_status s = reset_status(wf, err_flag, st);
+  if (s) return s;
+  return eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, log_psi, st);
 }
 
 qmc_status qmc_set_params(qmc_wf* wf, const double* params) {

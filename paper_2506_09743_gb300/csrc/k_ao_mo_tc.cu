@@ -25,8 +25,11 @@
 // (row % 8) * 16 + (k % 4) * 4, LBO = 128 B (next core matrix along K) and
 // SBO = (K extent / 4) * 128 B (next 8-row group).
 //
-// Every wait on an mbarrier is bounded (about one second), after which the
-// kernel raises an error flag and writes NaN instead of hanging.
+// Every wait on an mbarrier is bounded (WfDev::wait_cycles, about one second
+// by default), after which the CTA raises the error flags, waits (bounded
+// again) for the MMAs it has issued, writes NaN for its remaining outputs,
+// frees its tensor memory and stops instead of hanging; the host reports
+// QMC_ERR_TIMEOUT (qmc_check_status, and the calls that synchronise).
 #include <algorithm>
 
 #include "ao_eval.cuh"
@@ -75,9 +78,13 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(kIdescTf32), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+// Wait for the mbarrier phase of the given parity for at most `budget` SM
+// clock cycles (and 2^24 tries); false if it did not complete in time.  A
+// budget of 0 gives up before the first try (the timeout path's test).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase, long long budget) {
   const long long t0 = clock64();
   for (int it = 0; it < (1 << 24); ++it) {
+    if (clock64() - t0 >= budget) break;
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -87,10 +94,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase)
         : "r"(mbar), "r"(phase)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > (1ll << 31)) break;  // ~1 s at 2 GHz
   }
   return false;
 }
+
+// budget of the drain after a failed wait: the MMAs a CTA issued must have
+// completed before its shared and tensor memory are released (~1 s)
+constexpr long long kDrainCycles = 1ll << 31;
 
 // int words of the AO power, column and shell-list tables, rounded up so that
 // the mbarrier behind them is 16-byte aligned
@@ -103,7 +113,7 @@ template <int NCH>
 __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                          int64_t ldw, const float* __restrict__ gradJ,
                                                          double* __restrict__ mo_out, int64_t ldm,
-                                                         int* __restrict__ err_flag) {
+                                                         int* __restrict__ err_flag, int* __restrict__ err_wf) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int kp = wf.k_pad;
   constexpr size_t tile_words = (size_t)kRows * kPass;
@@ -193,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
     for (int pass = 0; pass < wf.n_pass; ++pass) {
       if (pass > 0) {
         // the previous pass's MMAs must have read the A buffer before it is overwritten
-        ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1) && ok;
+        ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1, wf.wait_cycles) && ok;
       }
       // unused columns of the pass are zero (disjoint from the shells' columns)
       const unsigned zero_cols = wf.pass_zero[pass];
@@ -304,13 +314,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_ao_mo_tc(WfDev wf, const double
       }
       ++commits;
     }
-    if (ok) ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1);
+    if (ok) ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1, wf.wait_cycles);
     ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {
-      // an MMA did not complete in time: poison this CTA's remaining outputs
-      // (this tile and the tiles it would have taken) and stop
-      if (tid == 0) atomicExch(err_flag, 1);
+      // an MMA did not complete in time: record it (per call and per
+      // wavefunction), let the MMAs already issued finish (at most one commit
+      // is outstanding: every pass waits for the previous one before it
+      // commits), poison this CTA's remaining outputs (this tile and the
+      // tiles it would have taken) and stop
+      if (tid == 0) {
+        atomicExch(err_flag, 1);
+        atomicExch(err_wf, 1);
+      }
+      if (commits > 0) mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1, kDrainCycles);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int ch = tid >> 7;
       for (int64_t t = tile; t < n_tiles; t += gridDim.x) {
         const int ti = (int)(t % wf.n_elec);
@@ -354,7 +372,7 @@ size_t tc_smem_bytes(const WfDev& wf, int nch) {
 }
 
 cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
-                            const Workspace& ws, int nch, int* err_flag, cudaStream_t st) {
+                            const Workspace& ws, int nch, int* err_flag, int* err_wf, cudaStream_t st) {
   if (W == 0) return cudaSuccess;
   if (prec != QMC_MIXED_TF32) return cudaErrorInvalidValue;
   // persistent grid: two CTAs per SM (the occupancy the kernel is built
@@ -369,10 +387,10 @@ cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, in
   double* mo = ws.mo;
   if (nch == 2) {
     cudaFuncSetAttribute(k_ao_mo_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ao_mo_tc<2><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, mo, ws.ldm, err_flag);
+    k_ao_mo_tc<2><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, mo, ws.ldm, err_flag, err_wf);
   } else {
     cudaFuncSetAttribute(k_ao_mo_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ao_mo_tc<1><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, mo, ws.ldm, err_flag);
+    k_ao_mo_tc<1><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, mo, ws.ldm, err_flag, err_wf);
   }
   return cudaGetLastError();
 }

@@ -98,6 +98,7 @@ struct WfDev {
   // (x, y, z; xx, xy, xz, yy, yz, zz) from that column, 0 otherwise
   const int* ao_col;     // [n_ao]
   const int* tc_shells;  // [n_shell]
+  long long wait_cycles; // budget of a bounded device wait, SM clock cycles (qmc_set_wait_limit)
   int k_pad;             // n_pass * kTcPass (0 when the form has no tensor-core stage)
   int n_pass;
   unsigned pass_zero[kMaxTcPass];
@@ -256,7 +257,7 @@ cudaError_t launch_ao_mo_simt(const WfDev& wf, int prec, const double* walkers, 
 cudaError_t launch_ao_mo_x2(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                             int nch, cudaStream_t st);
 cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
-                            const Workspace& ws, int nch, int* err_flag, cudaStream_t st);
+                            const Workspace& ws, int nch, int* err_flag, int* err_wf, cudaStream_t st);
 cudaError_t launch_det(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,
                        double* e_loc, double* log_psi, cudaStream_t st);
 // explicit per-excitation determinants (the baseline of the table method)

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <string>
@@ -97,7 +98,7 @@ struct Slot {
   bool busy = false;
   Pending job{};
   size_t off = 0, bytes = 0;
-  double* host = nullptr;  // pinned [4]: mean, variance, accepted moves, spare
+  double* host = nullptr;  // pinned [4]: mean, variance, accepted moves, status word (bytes of [3])
   double t_admit = 0.0;
 };
 
@@ -165,15 +166,21 @@ qmc_status launch_job(qmc_server* srv, Slot& sl) {
   if (r.walkers) e = cudaMemcpyAsync(walkers, r.walkers, sizeof(double) * 3 * N * W, cudaMemcpyHostToDevice, st);
   else e = launch_init_walkers(srv->homes[r.wf_id], W, W, walkers, r.seed, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(int64_t) * W, st);
+  // the workspace's status word records a bounded device wait that gave up,
+  // over the whole request (cleared once here, read at retirement)
+  int* status = workspace_status(wf, ws, W);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e != cudaSuccess) return sfail(QMC_ERR_CUDA, std::string("request setup: ") + cudaGetErrorString(e));
   qmc_status s = QMC_OK;
   if (r.n_steps > 0)
-    s = qmc_sample(wf, walkers, W, W, r.n_steps, r.step, r.seed, 0, 0, nullptr, acc, ws, ws_bytes, st);
-  if (s == QMC_OK) s = qmc_local_energy(wf, walkers, W, W, e_loc, nullptr, ws, ws_bytes, st);
+    s = sample_call(wf, walkers, W, W, r.n_steps, r.step, r.seed, 0, 0, nullptr, acc, ws, ws_bytes, st, false);
+  if (s == QMC_OK) s = local_energy_call(wf, walkers, W, W, e_loc, nullptr, ws, ws_bytes, st, false);
   if (s != QMC_OK) return sfail(s, std::string("request kernels: ") + qmc_last_error());
   e = launch_mean_var(e_loc, W, stats, st);
   if (e == cudaSuccess) e = launch_sum_counts(acc, W, stats + 2, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sl.host, stats, sizeof(double) * 3, cudaMemcpyDeviceToHost, st);
+  sl.host[3] = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host[3], status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
   if (e != cudaSuccess) return sfail(QMC_ERR_CUDA, std::string("request reduction: ") + cudaGetErrorString(e));
   return QMC_OK;
@@ -269,7 +276,12 @@ qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n
     res.t_submit = sl.job.t_submit;
     res.t_admit = sl.t_admit;
     res.t_done = now_s();
-    if (q == cudaSuccess) {
+    int timed_out = 0;
+    std::memcpy(&timed_out, &sl.host[3], sizeof(int));
+    if (q == cudaSuccess && timed_out) {
+      res.status = QMC_ERR_TIMEOUT;
+      res.e_mean = res.e_var = res.accept_rate = NAN;
+    } else if (q == cudaSuccess) {
       res.status = QMC_OK;
       res.e_mean = sl.host[0];
       res.e_var = sl.host[1];

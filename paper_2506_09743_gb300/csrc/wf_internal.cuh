@@ -63,5 +63,22 @@ struct qmc_wf {
   cudaEvent_t tev[6] = {};  // Jastrow, AO+MO, det (start, end)
   int det_method = QMC_DET_TABLE;
   cudaStream_t cap_stream = nullptr;  // capture stream of the Metropolis step graph
+  // bounded device waits: budget in SM cycles (about 1 s at 2 GHz), the
+  // sticky status word their kernels set when one gives up (qmc_check_status)
+  // and a page-locked host word the status is read into
+  long long wait_cycles = 1ll << 31;
+  int* err_wf = nullptr;
+  int* status_host = nullptr;
   std::mutex mu;
 };
+
+// qmc_sample / qmc_local_energy with the choice of clearing the workspace's
+// status word first (reset = true, the public calls) or keeping it (the
+// server clears it once per request and reads it when the request retires)
+qmc_status sample_call(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_steps, double step,
+                       uint64_t seed, uint64_t first_walker, uint64_t step_offset, double* log_psi, int64_t* n_accept,
+                       void* workspace, size_t workspace_bytes, void* stream, bool reset);
+qmc_status local_energy_call(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_loc,
+                             double* log_psi, void* workspace, size_t workspace_bytes, void* stream, bool reset);
+// the status word inside a workspace of qmc_workspace_size(wf, n_walkers) bytes
+int* workspace_status(const qmc_wf* wf, void* workspace, int64_t n_walkers);
