@@ -5,9 +5,13 @@ per atom, 3 primitives), 14 MOs, 100 determinants of the (10e, 12o) active
 space, Pade Jastrow; 262,144 seeded synthetic walkers per GPU.  One step =
 one qmc_local_energy call over the whole batch (Jastrow + Coulomb, AO
 evaluation, AO->MO contraction, reference inverse, excited-determinant
-tables, E_L assembly).  The headline `value` is the mixed form (FP32 AOs,
-tcgen05 TF32x3 AO->MO contraction, FP64 determinants); the plain FP64 form is
-timed on the same walkers and reported beside it.
+tables, E_L assembly).  The headline `value` is the FP32X2 form (AOs,
+contraction and Coulomb potential in pairs of FP32, FP64 determinants), the
+form that meets 2e-4 Ha per walker against the FP64 oracle; the plain FP64
+form and the faster FP32-AO tensor-core form (mixed_tf32, which does not meet
+that gate on ill-conditioned walkers) are timed on the same walkers and
+reported beside it, each with its error against the FP64 form on every
+walker.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -69,6 +73,41 @@ def ao_mo_stage_flops(mol) -> float:
     return 2.0 * 2 * mol.n_elec * mol.n_ao * mol.n_mo
 
 
+# FP32 operations of the pair-of-FP32 primitives (f32x2.cuh, as written):
+# two_prod 2, fast_two_sum 3, two_sum 6; product of pairs 7, pair times a
+# float 6, sum of pairs 11; multiply-accumulate into a pair 12; exponential 69
+X2_OPS = {"mac": 12, "mul": 7, "mulf": 6, "add": 11, "exp": 69}
+
+
+def x2_stage_ops(mol) -> float:
+    """Algorithmic FP32 operations per walker of the FP32X2 AO stage
+    (k_ao_mo_x2): per electron and Gaussian primitive the exponential of
+    -alpha rho^2 and the radial sums (value, 2 alpha c e, (2 alpha)^2 c e);
+    per electron and AO its value and kinetic channel from the shell's radial
+    part (one product for the value, two products and one sum for the
+    kinetic channel); per electron, AO and MO two multiply-accumulates
+    (value and kinetic channel).  Displacements, shell set-up and stores are
+    not counted."""
+    n_prim = sum(int(mol.ao_prim_start[b + 1] - mol.ao_prim_start[b]) for b in range(mol.n_ao))
+    # primitives are shared by the AOs of a shell: count each shell once
+    shells = {}
+    for b in range(mol.n_ao):
+        key = (int(mol.ao_atom[b]), int(sum(mol.ao_pow[b][:3])), tuple(mol.prim_exp[mol.ao_prim_start[b]:mol.ao_prim_start[b + 1]]))
+        shells[key] = int(mol.ao_prim_start[b + 1] - mol.ao_prim_start[b])
+    n_shell_prim = sum(shells.values())
+    o = X2_OPS
+    per_prim = o["mul"] + o["exp"] + o["mul"] + o["add"] + (o["mul"] + o["mulf"] + o["add"]) * 2
+    per_ao = o["mul"] + 2 * o["mul"] + o["add"]
+    per_row = n_shell_prim * per_prim + mol.n_ao * per_ao + 2 * mol.n_ao * mol.n_mo * o["mac"]
+    del n_prim
+    return float(mol.n_elec * per_row)
+
+
+# GB300 issue rates from the unit counts and the maximum SM clock (152 SMs,
+# 2.07 GHz): FP32 128 lanes per SM; FP64 2 FMA lanes per SM (4 flop/clk)
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12  # 40.3 T FP32 operations/s
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -120,8 +159,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(n_walkers: int = 16384):
-    """The oracle (plain FP64 CPU) on a bounded sample of the same workload."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(n_walkers: int = 16384, n_walkers_1core: int = 1024):
+    """The oracle (plain FP64 CPU, PyTorch vectorised over walkers) on a
+    bounded sample of the same workload, on all host cores and on one."""
     import torch
 
     from oracle import qmc_oracle as O
@@ -133,8 +192,20 @@ def cpu_baseline(n_walkers: int = 16384):
     t0 = time.perf_counter()
     O.local_energy(wf, r)
     dt = time.perf_counter() - t0
-    return {"value": n_walkers / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{n_walkers} of the 262144 CO walkers (same seed), one evaluation, {dt:.1f} s"}
+    cores = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        O.local_energy(wf, r[:n_walkers_1core])
+        dt1 = time.perf_counter() - t0
+    finally:
+        torch.set_num_threads(cores)
+    return {"value": n_walkers / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(), "value_1core": n_walkers_1core / dt1,
+            "program": "the FP64 oracle (oracle/qmc_oracle.py: plain PyTorch CPU ops, explicit per-determinant "
+                       "inverses), not a tuned C++ program",
+            "sample": f"{n_walkers} of the 262144 CO walkers (same seed), one evaluation, {dt:.1f} s; "
+                      f"1 core: {n_walkers_1core} walkers, {dt1:.1f} s"}
 
 
 def run_reference(args, rank):
@@ -170,22 +241,22 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(n_requests: int, with_fp64: bool, device: int, n_requests_fp64: int = 400,
+def run_serving(n_requests: int, with_fp64: bool, device: int, n_requests_fp64: int = 1000,
                 n_capacity: int = 400):
     """Serving mix (H2, LiH, Li2, CO at 20 bond lengths each; 50 Metropolis
     steps + E_L mean/variance per request; walkers uniform on 4k..256k):
     a closed-loop run of n_capacity requests measures the capacity (requests/s
     with everything queued at once) and warms the server up, then Poisson
-    arrivals at 80% of it give the latencies (n_requests in the mixed form,
+    arrivals at 80% of it give the latencies (n_requests in the FP32X2 form,
     n_requests_fp64 in the slower FP64 form)."""
     from paper_2506_09743_gb300 import serving
 
     out = {"n_steps": 50, "walker_choices": [4096, 16384, 65536, 262144], "molecules": ["h2", "lih", "li2", "co"],
            "note": "Li2 (backflow) requests run in the FP64 form in both mixes",
            "policy": "large (>= 65,536 walkers) requests ordered, at most 2 in flight, low stream priority"}
-    forms = ["mixed_tf32"] + (["fp64"] if with_fp64 else [])
+    forms = ["fp32x2"] + (["fp64"] if with_fp64 else [])
     for form in forms:
-        n = n_requests if form == "mixed_tf32" else min(n_requests, n_requests_fp64)
+        n = n_requests if form == "fp32x2" else min(n_requests, n_requests_fp64)
         wfs = serving.build_mix(form, device=device)
         srv = serving.Server(device=device, hbm_budget_bytes=48 << 30, max_in_flight=8)
         ids = {k: srv.add(wf) for k, wf in wfs.items()}
@@ -196,7 +267,11 @@ def run_serving(n_requests: int, with_fp64: bool, device: int, n_requests_fp64: 
         st = serving.summarize(serving.run_stream(srv, ids, reqs, n_steps=50, step=0.05, rate_hz=rate), 50)
         st["capacity_requests_per_s"] = cap["requests_per_s"]
         st["arrival_rate_hz"] = rate
-        out["mixed" if form == "mixed_tf32" else "fp64"] = st
+        if form == "fp64" and n < n_requests:
+            st["note"] = (f"{n} requests: at 80% of the FP64 capacity ({rate:.1f} req/s) {n_requests} requests "
+                          f"would take {n_requests / rate:.0f} s; {n} keep the default run within minutes "
+                          f"({n // 100} requests above the p99)")
+        out[form] = st
         srv.close()
         for wf in wfs.values():
             wf.close()
@@ -233,7 +308,7 @@ def run_secondary(device, stream, barrier, flush):
         mol = qi.make_molecule(name)
         W = qi.WORKLOAD_WALKERS[name]
         x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
-        forms = ("fp64",) if mol.backflow_w != 0.0 else ("fp64", "mixed_tf32")
+        forms = ("fp64",) if mol.backflow_w != 0.0 else ("fp64", "fp32x2", "mixed_tf32")
         for form in forms:
             wf = Wavefunction(mol, precision=form, device=device)
             out[f"{name}_{form}_walker_evals_per_s"] = rate(wf, x, W)
@@ -250,9 +325,10 @@ def run_secondary(device, stream, barrier, flush):
     mol = qi.with_manybody_jastrow(qi.make_co())
     W = qi.WORKLOAD_WALKERS["co"]
     x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
-    wf = Wavefunction(mol, precision="mixed_tf32", device=device)
-    out["co_manybody_jastrow_mixed_tf32_walker_evals_per_s"] = rate(wf, x, W, steps=3)
-    wf.close()
+    for form in ("fp32x2", "mixed_tf32"):
+        wf = Wavefunction(mol, precision=form, device=device)
+        out[f"co_manybody_jastrow_{form}_walker_evals_per_s"] = rate(wf, x, W, steps=3)
+        wf.close()
     del x
     # several determinants with backflow: Li2, SD(6e, 6o) = 118 determinants
     mol = qi.make_li2(n_mo=6, n_det=118)
@@ -350,7 +426,7 @@ def main():
     ap.add_argument("--walkers", type=int, default=qi.WORKLOAD_WALKERS["co"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000,
-                    help="requests of the Poisson serving run, mixed form (the FP64 form serves at most 400; 0 = skip)")
+                    help="requests of the Poisson serving run, FP32X2 form (the FP64 form serves at most 1000; 0 = skip)")
     ap.add_argument("--no-serving-fp64", action="store_true", help="serve the mix in the mixed form only")
     ap.add_argument("--no-det-sweep", action="store_true", help="skip the explicit-versus-table sweep")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other molecules' measurements")
@@ -396,8 +472,10 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     stream = torch.cuda.current_stream()
 
+    last_e = torch.empty(W, dtype=torch.float64, device="cuda")
+
     def timed_device(wf, steps, warmup):
-        e = torch.empty(W, dtype=torch.float64, device="cuda")
+        e = last_e
         lp = torch.empty(W, dtype=torch.float64, device="cuda")
         wf.set_timing(True)
         for _ in range(warmup):
@@ -417,17 +495,25 @@ def main():
         finite = float(torch.isfinite(e).double().mean().item())
         return float(np.sum(step_ms)), np.mean(np.asarray(stage), axis=0), finite
 
+    wf_x2 = Wavefunction(mol, precision="fp32x2", device=local)
     wf_mixed = Wavefunction(mol, precision="mixed_tf32", device=local)
     wf_fp64 = Wavefunction(mol, precision="fp64", device=local)
 
     clk = ClockSampler(local).__enter__()
-    tot_mixed, stage_mixed, fin_mixed = timed_device(wf_mixed, args.steps, args.warmup)
-    tot_fp64, stage_fp64, fin_fp64 = timed_device(wf_fp64, max(3, args.steps // 4), 3)
+    tot_x2, stage_x2, fin_x2 = timed_device(wf_x2, args.steps, args.warmup)
+    e_x2 = last_e.clone()
+    k_mixed = max(3, args.steps // 2)
+    tot_mixed, stage_mixed, fin_mixed = timed_device(wf_mixed, k_mixed, 3)
+    e_mixed = last_e.clone()
     k64 = max(3, args.steps // 4)
+    tot_fp64, stage_fp64, fin_fp64 = timed_device(wf_fp64, k64, 3)
+    e_fp64 = last_e.clone()
+    tot_x2 = max_over_ranks(tot_x2)
     tot_mixed = max_over_ranks(tot_mixed)
     tot_fp64 = max_over_ranks(tot_fp64)
-    ms_step = tot_mixed / args.steps
-    value = whole_job_rate(world, W, args.steps, tot_mixed)
+    ms_step = tot_x2 / args.steps
+    value = whole_job_rate(world, W, args.steps, tot_x2)
+    value_mixed = whole_job_rate(world, W, k_mixed, tot_mixed)
     value_fp64 = whole_job_rate(world, W, k64, tot_fp64)
 
     # end to end through the host-buffer C call (pinned host memory)
@@ -436,7 +522,7 @@ def main():
     pin_lp = torch.empty(W, dtype=torch.float64).pin_memory()
     in_np, e_np, lp_np = pin_in.numpy(), pin_e.numpy(), pin_lp.numpy()
     for _ in range(args.warmup):
-        wf_mixed.local_energy_host(in_np, e_np, lp_np, stream=stream)
+        wf_x2.local_energy_host(in_np, e_np, lp_np, stream=stream)
     barrier()
     e2e_steps = max(3, args.steps // 2)
     t_e2e = []
@@ -444,7 +530,7 @@ def main():
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        wf_mixed.local_energy_host(in_np, e_np, lp_np, stream=stream)
+        wf_x2.local_energy_host(in_np, e_np, lp_np, stream=stream)
         b.record(stream)
         b.synchronize()
         t_e2e.append(a.elapsed_time(b))
@@ -455,17 +541,19 @@ def main():
     e2e_value = whole_job_rate(world, W, e2e_steps, e2e_ms)
 
     # Metropolis walker steps (value path: Jastrow value, orbital values, determinants, accept)
-    n_mh = 5
-    xs = x.clone()
-    wf_mixed.sample(xs, n_steps=1, step=0.05, seed=0x5EED)
-    barrier()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    wf_mixed.sample(xs, n_steps=n_mh, step=0.05, seed=0x5EED, step_offset=1)
-    b.record(stream)
-    b.synchronize()
-    mh_steps_per_s = world * W * n_mh / (max_over_ranks(a.elapsed_time(b)) / 1e3)
-    del xs
+    def mh_rate(wf, n_mh=5):
+        xs = x.clone()
+        wf.sample(xs, n_steps=1, step=0.05, seed=0x5EED)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        wf.sample(xs, n_steps=n_mh, step=0.05, seed=0x5EED, step_offset=1)
+        b.record(stream)
+        b.synchronize()
+        return world * W * n_mh / (max_over_ranks(a.elapsed_time(b)) / 1e3)
+
+    mh_x2 = mh_rate(wf_x2)
+    mh_mixed = mh_rate(wf_mixed)
 
     secondary = run_secondary(local, stream, barrier, flush) if world == 1 and not args.no_secondary else None
     det_sweep = run_det_sweep(local, stream, barrier, flush) if world == 1 and not args.no_det_sweep else None
@@ -474,40 +562,78 @@ def main():
     if args.serving_requests > 0 and world == 1:
         serving_out = run_serving(args.serving_requests, not args.no_serving_fp64, local)
 
+    # error of each form against the FP64 form on every walker of the batch
+    # (the FP64 form matches the CPU oracle to 1e-10 relative: tests/)
+    def accuracy(e_form):
+        err = (e_form - e_fp64).abs()
+        ok = torch.isfinite(err)
+        err = err[ok].cpu().numpy()
+        return {"within_2e-4_Ha": float((err <= 2e-4).mean()), "median_Ha": float(np.median(err)),
+                "p99_Ha": float(np.quantile(err, 0.99)), "p999_Ha": float(np.quantile(err, 0.999)),
+                "max_Ha": float(err.max()), "nonfinite": int((~ok).sum().item()), "walkers": W,
+                "note": "against the FP64 form on the same walkers; the walkers beyond 2e-4 Ha are at nodes "
+                        "(|E| of 1e4..1e7 Ha), outside the parity tests' conditioning cut"}
+
+    # rooflines: FP32-issue-bound AO stages, FP64-pipe-bound determinant stage
+    x2_ops = x2_stage_ops(mol) * W
+    x2_ms = float(stage_x2[1])
+    x2_rate = x2_ops / (x2_ms / 1e3) / 1e12
     flops_det = det_stage_flops(mol) * W
-    det_ms = float(stage_mixed[2])
-    achieved = flops_det / (det_ms / 1e3) / 1e12
-    flops_ao64 = ao_mo_stage_flops(mol) * W
-    roofline = {"kernel": "k_det (determinants, tables, E_L; mixed form)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None if DET_TRAFFIC_BYTES_PER_WALKER is None else DET_TRAFFIC_BYTES_PER_WALKER * W,
-                "traffic_unit": "bytes per launch (ncu dram read+write, scaled from 131,072 walkers)",
-                "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                "flops_per_launch": flops_det, "kernel_ms": det_ms}
+    det_ms = float(stage_x2[2])
+    det_rate = flops_det / (det_ms / 1e3) / 1e12
+    roofline = {"kernel": "k_ao_mo_x2 (AOs + AO->MO contraction in pairs of FP32; FP32X2 form)", "bound": "alu",
+                "achieved": x2_rate, "peak": FP32_PEAK_TOPS, "unit": "T FP32 ops/s", "frac": x2_rate / FP32_PEAK_TOPS,
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (no measured FP32 peak on this pool)",
+                "ops_per_launch": x2_ops, "ops_model": "bench.x2_stage_ops (pair-arithmetic operation counts)",
+                "kernel_ms": x2_ms}
+    rooflines = {
+        "k_det": {"bound": "alu", "achieved": det_rate, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                  "frac": det_rate / FP64_PEAK_TFLOPS, "kernel_ms": det_ms, "flops_per_launch": flops_det,
+                  "traffic": None if DET_TRAFFIC_BYTES_PER_WALKER is None else DET_TRAFFIC_BYTES_PER_WALKER * W,
+                  "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal)"},
+        "k_ao_mo_simt_fp64": {"bound": "alu", "kernel_ms": float(stage_fp64[1]),
+                              "achieved": ao_mo_stage_flops(mol) * W / (float(stage_fp64[1]) / 1e3) / 1e12,
+                              "unit": "TFLOP/s (FP64, contraction flops only)", "peak": FP64_PEAK_TFLOPS},
+        "k_ao_mo_tc": {"kernel_ms": float(stage_mixed[1]), "note": "FP32 AO stage + tcgen05 TF32x3 contraction"},
+    }
+    # whole step: the FP32X2 step cannot beat its AO stage at the FP32 issue
+    # rate plus its determinant stage at the FP64 rate (the two run in turn)
+    bound_ms = x2_ops / (FP32_PEAK_TOPS * 1e12) * 1e3 + flops_det / (FP64_PEAK_TFLOPS * 1e12) * 1e3
+    whole_step = {"ms_per_step": ms_step, "bound_ms": bound_ms, "frac": bound_ms / ms_step,
+                  "note": "AO stage at the FP32 issue rate + determinant stage at the FP64 rate, in sequence"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 AO / tf32x3 MMA / f64 det", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32x2 AO+MO / f64 det", "data": "synthetic",
         "config": {"workload": (WORKLOAD.replace("262144 walkers", f"{W} walkers")
                                 + (" + many-body Jastrow (K_en, 5 K_een terms)" if args.manybody_jastrow else "")),
-                   "walkers_per_gpu": W, "precision": "mixed_tf32",
+                   "walkers_per_gpu": W, "precision": "fp32x2",
                    "l2": "flushed (256 MB write) between timed steps, outside the timed events",
                    "parallelism": f"walker shards x{world}, no data-path collective"},
+        "stage_ms": {"jastrow_coulomb": float(stage_x2[0]), "ao_mo_x2": float(stage_x2[1]),
+                     "det_eloc": float(stage_x2[2])},
+        "finite_frac": fin_x2,
+        "accuracy": accuracy(e_x2),
         "fp64_plain": {"value": value_fp64, "ms_per_step": tot_fp64 / k64,
-                       "stage_ms": [float(v) for v in stage_fp64], "finite_frac": fin_fp64,
-                       "ao_mo_fp64_tflops": flops_ao64 / (float(stage_fp64[1]) / 1e3) / 1e12},
-        "mixed_vs_fp64": value / value_fp64,
-        "stage_ms": {"jastrow_coulomb": float(stage_mixed[0]), "ao_mo_tcgen05": float(stage_mixed[1]),
-                     "det_eloc": float(stage_mixed[2])},
-        "finite_frac": fin_mixed,
+                       "stage_ms": [float(v) for v in stage_fp64], "finite_frac": fin_fp64},
+        "mixed_tf32": {"value": value_mixed, "ms_per_step": tot_mixed / k_mixed,
+                       "stage_ms": [float(v) for v in stage_mixed], "finite_frac": fin_mixed,
+                       "accuracy": accuracy(e_mixed),
+                       "note": "FP32 AOs, tcgen05 TF32x3 contraction: faster, but not within 2e-4 Ha on "
+                               "ill-conditioned walkers"},
+        "fp32x2_vs_fp64": value / value_fp64,
         "roofline": roofline,
+        "rooflines": rooflines,
+        "whole_step": whole_step,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(soa.nbytes),
-                "d2h_bytes_per_step": int(2 * 8 * W), "api": "qmc_local_energy_host (pinned host buffers)"},
+                "d2h_bytes_per_step": int(2 * 8 * W), "api": "qmc_local_energy_host (pinned host buffers), FP32X2 form"},
         # per E_L: Jastrow (+ e-e-n kernel with the many-body Jastrow), AO->MO, determinants
         "gpu_launches": (4 if args.manybody_jastrow else 3) * args.steps,
         "clocks": clocks,
-        "p99_request_latency_ms": None if serving_out is None else serving_out["mixed"]["p99_ms"],
-        "metropolis_walker_steps_per_s": mh_steps_per_s,
+        "p99_request_latency_ms": None if serving_out is None else serving_out["fp32x2"]["p99_ms"],
+        "metropolis_walker_steps_per_s": mh_x2,
+        "metropolis_walker_steps_per_s_mixed_tf32": mh_mixed,
         "serving": serving_out,
         "secondary": secondary,
         "det_sweep": det_sweep,

@@ -131,16 +131,21 @@ __global__ void __launch_bounds__(kX2Threads) k_ao_mo_x2(WfDev wf, const double*
         f2 = (q * q - irho * irho * (float)sh.kn) * f;
       }
     } else {  // contracted Gaussian: sum_p c_p exp(-alpha_p rho^2)
+      // g1 = -sum 2 al c e, f2 = rho^2 sum (2 al)^2 c e - sum 2 al c e
+      f32x2 t1(0.f), t2(0.f);
       for (int p = 0; p < sh.n_prim; ++p) {
         const f32x2 al = x2_expo(sh, p);
         const f32x2 ce = x2_coef(sh, p) * exp_x2(-(al * r2), xtab);
         f += ce;
         if (NCH == 2) {
-          const f32x2 a2 = al * 2.0f;  // exact
-          const f32x2 t = a2 * ce;
-          g1 -= t;
-          f2 += (a2 * r2 - f32x2(1.f)) * t;  // (4 al^2 rho^2 - 2 al) c e
+          const f32x2 t = (al * ce) * 2.0f;  // 2 al c e (the factor 2 is exact)
+          t1 += t;
+          t2 += (al * t) * 2.0f;
         }
+      }
+      if (NCH == 2) {
+        g1 = -t1;
+        f2 = r2 * t2 - t1;
       }
     }
     f32x2 RL(0.f), tf(0.f);
