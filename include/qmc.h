@@ -51,7 +51,8 @@ typedef enum {
   QMC_ERR_OOM = 2,         /* device allocation failed or workspace too small */
   QMC_ERR_CUDA = 3,        /* a CUDA runtime error; message has the CUDA text */
   QMC_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
-  QMC_ERR_UNSUPPORTED = 5  /* shape outside the compiled limits (see below) */
+  QMC_ERR_UNSUPPORTED = 5, /* shape outside the compiled limits (see below) */
+  QMC_ERR_CANCELLED = 6    /* a server request cancelled by qmc_server_cancel */
 } qmc_status;
 
 /* Precision forms of the local energy.
@@ -279,6 +280,31 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
 qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_stats,
                            double* grad, double* forces, void* stream);
 
+/* Sharded batches (several GPUs, or batches too large for one call): the
+ * estimators of qmc_energy_grad are assembled from per-batch sums, so one
+ * all-reduce (sum) of these sums across the shards gives the estimator of
+ * the whole sample exactly (Eq. nabla_loss, Sec. 2.2; Eq. force, Sec. 2.3):
+ *   E_v    = S_E / M,  var = S_EE / M - E_v^2
+ *   grad   = 2 (S_E,dlogPsi - E_v S_dlogPsi) / M
+ *   forces = -(S_dE + S_E,dlnrho - E_v S_dlnrho) / M,   ln rho = 2 log|Psi|
+ * qmc_energy_grad_sums writes, stream-ordered into DEVICE memory `sums`
+ * (qmc_energy_grad_sums_size(wf) doubles, ready for an all-reduce in place):
+ *   [0] M (walkers), [1] S_E = sum E_L, [2] S_EE = sum E_L^2,
+ *   [3, 3 + P)          sum d log|Psi| / d theta_p   (qmc_param_layout order, P = n_param)
+ *   [3 + P, 3 + 2P)     sum E_L d log|Psi| / d theta_p
+ *   then three blocks of 3 n_atom (atom-major, x y z):
+ *                       sum d E_L / d R,  sum d ln rho / d R,  sum E_L d ln rho / d R.
+ * Same scope as qmc_energy_grad (QMC_ERR_UNSUPPORTED otherwise).  Sums run in
+ * a fixed order (bitwise reproducible).  qmc_assemble_energy_grad is the host
+ * arithmetic above on the (reduced) sums, copied to the host: e_stats [2],
+ * grad [n_param] (or NULL), forces [n_atom][3] (or NULL); QMC_ERR_ARG when
+ * the sums count no walker. */
+int64_t qmc_energy_grad_sums_size(const qmc_wf* wf);
+qmc_status qmc_energy_grad_sums(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* sums,
+                                void* stream);
+qmc_status qmc_assemble_energy_grad(int64_t n_param, int32_t n_atom, const double* sums, double* e_stats,
+                                    double* grad, double* forces);
+
 /* Replace the variational parameters (host [n_param] in qmc_param_layout
  * order: exponents, MO coefficients, CI weights, Jastrow b, backflow w) and
  * rebuild the device tables.  Waits for work in flight on the device.
@@ -425,12 +451,13 @@ typedef struct {
                            device wait gave up; the statistics are NaN) */
   int32_t wf_id;
   int64_t n_walkers;
-  double e_mean;        /* mean local energy, Ha */
-  double e_var;         /* variance of the local energy, Ha^2 */
+  double e_mean;        /* mean local energy over the walkers with a finite one, Ha */
+  double e_var;         /* variance of those local energies, Ha^2 */
   double accept_rate;   /* accepted moves / (n_walkers n_steps) */
   double t_submit;      /* qmc_server_clock() at submission, admission and completion, s */
   double t_admit;
   double t_done;
+  int64_t n_nonfinite;  /* walkers whose local energy is not finite (left out of e_mean, e_var) */
 } qmc_result;
 
 /* Create a server on `device` with a device-memory arena of hbm_budget_bytes
@@ -449,6 +476,13 @@ qmc_status qmc_server_submit(qmc_server* srv, const qmc_request* req, int64_t* t
 /* Retire finished requests and admit queued ones; returns the numbers in
  * flight and still queued.  Call it repeatedly (it does not block). */
 qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n_queued);
+
+/* Cancel a request: a queued one is removed at once (no device work) and a
+ * request in flight finishes its kernels but its statistics are dropped;
+ * either way its result carries QMC_ERR_CANCELLED with NaN statistics and
+ * its memory returns to the arena.  QMC_ERR_ARG for a ticket that is
+ * neither queued nor in flight (unknown, or already finished). */
+qmc_status qmc_server_cancel(qmc_server* srv, int64_t ticket);
 
 /* Move up to `capacity` finished results into out (oldest first). */
 qmc_status qmc_server_results(qmc_server* srv, qmc_result* out, int32_t capacity, int32_t* n_out);

@@ -783,6 +783,45 @@ def energy_grad(wf, r):
     return Ev, var, grad.detach(), forces.detach()
 
 
+def energy_grad_sums(wf, r):
+    """Raw per-batch sums from which Eq. nabla_loss and Eq. force are
+    assembled after the batches of a sharded sample are added together:
+    [M, sum E, sum E^2, sum d_theta log|Psi| (n_param), sum E d_theta log|Psi|
+    (n_param), sum d_R E (3 n_atom), sum d_R ln rho, sum E d_R ln rho],
+    ln rho = 2 log|Psi|, every derivative by autograd."""
+    params = list(wf.params().values())
+    E = local_energy(wf, r)
+    lp, _ = log_psi(wf, r)
+    Ed = E.detach()
+
+    def pgrad(y):
+        g = torch.autograd.grad(y, params, allow_unused=True, retain_graph=True)
+        return torch.cat([(gi if gi is not None else torch.zeros_like(p)).reshape(-1) for gi, p in zip(g, params)])
+
+    s_dlp = pgrad(lp.sum())
+    s_edlp = pgrad((Ed * lp).sum())
+    s_de = torch.autograd.grad(E.sum(), wf.atom_xyz, retain_graph=True)[0].reshape(-1)
+    s_dr = torch.autograd.grad((2.0 * lp).sum(), wf.atom_xyz, retain_graph=True)[0].reshape(-1)
+    s_edr = torch.autograd.grad((Ed * 2.0 * lp).sum(), wf.atom_xyz)[0].reshape(-1)
+    head = torch.tensor([float(r.shape[0]), float(Ed.sum()), float((Ed * Ed).sum())], dtype=DT)
+    return torch.cat([head, s_dlp.detach(), s_edlp.detach(), s_de.detach(), s_dr.detach(), s_edr.detach()])
+
+
+def assemble_energy_grad(sums, n_param, n_atom):
+    """(E_v, variance, gradient, forces) from the sums of energy_grad_sums:
+    E_v = S_E / M, var = S_EE / M - E_v^2, grad = 2 (S_E,dlp - E_v S_dlp) / M,
+    forces = -(S_dE + S_E,dlnrho - E_v S_dlnrho) / M (Eqs. nabla_loss, force)."""
+    M = sums[0]
+    ev = sums[1] / M
+    var = sums[2] / M - ev * ev
+    P, A3 = n_param, 3 * n_atom
+    s_dlp, s_edlp = sums[3:3 + P], sums[3 + P:3 + 2 * P]
+    s_de, s_dr, s_edr = (sums[3 + 2 * P + k * A3:3 + 2 * P + (k + 1) * A3] for k in range(3))
+    grad = 2.0 * (s_edlp - ev * s_dlp) / M
+    forces = -(s_de + s_edr - ev * s_dr) / M
+    return ev, var, grad, forces.reshape(n_atom, 3)
+
+
 # ---------------------------------------------------------------------------
 # Metropolis-Hastings sampler (App. B: Gaussian proposal, all electrons moved
 # at once, accept with probability min(1, |Psi'/Psi|^2))

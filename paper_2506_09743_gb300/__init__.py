@@ -148,6 +148,20 @@ class Wavefunction:
                                              _stream_handle(stream)))
         return float(stats[0]), float(stats[1]), grad, forces
 
+    def energy_grad_sums(self, walkers, n_walkers: int | None = None, sums=None, stream=None):
+        """Per-batch sums of the energy-gradient estimators (device float64
+        [qmc_energy_grad_sums_size]), stream-ordered: all-reduce them across
+        shards, then assemble with _lib.assemble_energy_grad."""
+        import torch
+
+        W = walkers.shape[1] if n_walkers is None else int(n_walkers)
+        n = int(self._lib.qmc_energy_grad_sums_size(self._h))
+        if sums is None:
+            sums = torch.empty(n, dtype=torch.float64, device=walkers.device)
+        _lib.check(self._lib.qmc_energy_grad_sums(self._h, _dptr(walkers), W, walkers.stride(0), _dptr(sums),
+                                                  _stream_handle(stream)))
+        return sums
+
     def optimize(self, walkers, n_iter: int, n_equil: int, n_resample: int, step: float, seed: int,
                  lr: float = 1e-2, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, mask=None,
                  n_walkers: int | None = None, stream=None):

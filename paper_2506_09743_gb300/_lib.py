@@ -12,9 +12,9 @@ from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_size_t, c_ui
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqmc_gb300.so")
 
-QMC_OK, QMC_ERR_ARG, QMC_ERR_OOM, QMC_ERR_CUDA, QMC_ERR_TIMEOUT, QMC_ERR_UNSUPPORTED = range(6)
+QMC_OK, QMC_ERR_ARG, QMC_ERR_OOM, QMC_ERR_CUDA, QMC_ERR_TIMEOUT, QMC_ERR_UNSUPPORTED, QMC_ERR_CANCELLED = range(7)
 STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA", 4: "QMC_ERR_TIMEOUT",
-                5: "QMC_ERR_UNSUPPORTED"}
+                5: "QMC_ERR_UNSUPPORTED", 6: "QMC_ERR_CANCELLED"}
 QMC_FP64, QMC_FP32, QMC_MIXED_TF32, QMC_MIXED_BF16, QMC_FP32X2 = range(5)
 NOALLOC_SCRATCH_BYTES = 64 << 20  # QMC_NOALLOC_SCRATCH_BYTES of include/qmc.h
 PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "mixed_tf32": QMC_MIXED_TF32, "mixed_bf16": QMC_MIXED_BF16,
@@ -25,9 +25,10 @@ EXPORTED = (
     "qmc_create_wf", "qmc_destroy_wf", "qmc_set_geometry", "qmc_workspace_size", "qmc_local_energy",
     "qmc_local_energy_host", "qmc_local_energy_noalloc", "qmc_sample", "qmc_param_layout", "qmc_energy_grad",
     "qmc_set_params", "qmc_server_create", "qmc_server_destroy", "qmc_server_add_wf", "qmc_server_submit",
-    "qmc_server_progress", "qmc_server_results", "qmc_server_set_policy", "qmc_server_free_bytes", "qmc_server_clock",
+    "qmc_server_progress", "qmc_server_results", "qmc_server_cancel", "qmc_server_set_policy", "qmc_server_free_bytes", "qmc_server_clock",
     "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method", "qmc_optimize", "qmc_force_batches", "qmc_set_manybody_jastrow",
-    "qmc_check_status", "qmc_set_wait_limit", "qmc_last_error",
+    "qmc_check_status", "qmc_set_wait_limit", "qmc_energy_grad_sums_size", "qmc_energy_grad_sums",
+    "qmc_assemble_energy_grad", "qmc_last_error",
 )
 
 PD = POINTER(c_double)
@@ -67,7 +68,7 @@ class Request(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("ticket", c_int64), ("status", c_int32), ("wf_id", c_int32), ("n_walkers", c_int64),
                 ("e_mean", c_double), ("e_var", c_double), ("accept_rate", c_double), ("t_submit", c_double),
-                ("t_admit", c_double), ("t_done", c_double)]
+                ("t_admit", c_double), ("t_done", c_double), ("n_nonfinite", c_int64)]
 
 
 class OptConfig(ctypes.Structure):
@@ -143,6 +144,8 @@ def load(path: str = LIB_PATH):
     lib.qmc_server_progress.restype = c_int32
     lib.qmc_server_results.argtypes = [c_void_p, POINTER(Result), c_int32, POINTER(c_int32)]
     lib.qmc_server_results.restype = c_int32
+    lib.qmc_server_cancel.argtypes = [c_void_p, c_int64]
+    lib.qmc_server_cancel.restype = c_int32
     lib.qmc_server_set_policy.argtypes = [c_void_p, c_int64, c_int32]
     lib.qmc_server_set_policy.restype = c_int32
     lib.qmc_server_free_bytes.argtypes = [c_void_p]
@@ -155,6 +158,12 @@ def load(path: str = LIB_PATH):
     lib.qmc_check_status.restype = c_int32
     lib.qmc_set_wait_limit.argtypes = [c_void_p, c_int64]
     lib.qmc_set_wait_limit.restype = c_int32
+    lib.qmc_energy_grad_sums_size.argtypes = [c_void_p]
+    lib.qmc_energy_grad_sums_size.restype = c_int64
+    lib.qmc_energy_grad_sums.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p]
+    lib.qmc_energy_grad_sums.restype = c_int32
+    lib.qmc_assemble_energy_grad.argtypes = [c_int64, c_int32, PD, PD, PD, PD]
+    lib.qmc_assemble_energy_grad.restype = c_int32
     lib.qmc_last_error.argtypes = []
     lib.qmc_last_error.restype = c_char_p
     _lib = lib
@@ -171,3 +180,18 @@ def check_server(status: int):
     if status != QMC_OK:
         msg = _lib.qmc_server_last_error().decode() if _lib is not None else ""
         raise QmcError(status, msg)
+
+
+def assemble_energy_grad(sums, n_param: int, n_atom: int):
+    """qmc_assemble_energy_grad on host sums (e.g. after an all-reduce over
+    the shards): returns (E_v, variance, grad [n_param], forces [n_atom, 3])."""
+    import numpy as np
+
+    lib = load()
+    s = np.ascontiguousarray(sums, dtype=np.float64)
+    e = np.empty(2)
+    g = np.empty(max(n_param, 1))
+    f = np.empty((n_atom, 3))
+    check(lib.qmc_assemble_energy_grad(int(n_param), int(n_atom), s.ctypes.data_as(PD), e.ctypes.data_as(PD),
+                                       g.ctypes.data_as(PD), f.ctypes.data_as(PD)))
+    return float(e[0]), float(e[1]), g[:n_param], f

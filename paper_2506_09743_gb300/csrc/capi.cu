@@ -1061,32 +1061,32 @@ qmc_status qmc_set_params(qmc_wf* wf, const double* params) {
   return st;
 }
 
-qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_stats,
-                           double* grad, double* forces, void* stream) {
+}  // extern "C"
+
+// Preconditions and scratch of the energy-gradient calls: the library-owned
+// workspace, and in the gradient scratch e_loc [W], stats [4] and the block
+// partial sums (rows x blocks, rows up to max(n_param, 9 n_atom)).
+static qmc_status grad_setup(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, bool want_grad,
+                             int64_t* n_param, Workspace* ws, int** err_flag, double** e_loc, double** stats,
+                             double** partial) {
   if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
   if (n_walkers < 1 || ldw < n_walkers) return fail(QMC_ERR_ARG, "need n_walkers >= 1 and ldw >= n_walkers");
-  if (!walkers || !e_stats) return fail(QMC_ERR_ARG, "null walkers or e_stats");
+  if (!walkers) return fail(QMC_ERR_ARG, "null walkers");
   if (wf->precision != QMC_FP64) return fail(QMC_ERR_UNSUPPORTED, "energy gradients are computed in the FP64 form");
   if (!general_supported(wf->dev))
     return fail(QMC_ERR_UNSUPPORTED, "energy gradients need one determinant, <= 8 electrons, <= 4 per spin");
   if (wf->dev.mb_en || wf->dev.n_een)
     return fail(QMC_ERR_UNSUPPORTED, "energy gradients do not cover the many-body Jastrow");
-  int64_t n_param = 0;
-  qmc_param_layout(wf, &n_param, nullptr);
-  if (grad && grad_smem_bytes(wf->dev, (int)n_param) > 227 * 1024)
+  qmc_param_layout(wf, n_param, nullptr);
+  if (want_grad && grad_smem_bytes(wf->dev, (int)*n_param) > 227 * 1024)
     return fail(QMC_ERR_UNSUPPORTED, "too many parameters for the gradient kernel's shared memory");
-  std::lock_guard<std::mutex> lock(wf->mu);
-  DeviceGuard guard(wf->device);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   void* base;
   qmc_status s = get_workspace(wf, n_walkers, nullptr, 0, &base);
   if (s) return s;
-  int* err_flag;
-  Workspace ws = carve(wf, base, n_walkers, &err_flag);
-  // gradient scratch: e_loc [W], stats [2], block partial sums
+  *ws = carve(wf, base, n_walkers, err_flag);
   const int64_t nb = general_blocks(n_walkers);
-  const size_t need = align256(sizeof(double) * n_walkers) + align256(sizeof(double) * 2) +
-                      align256(sizeof(double) * nb * std::max<int64_t>(n_param, 3 * wf->dev.n_atom));
+  const size_t need = align256(sizeof(double) * n_walkers) + align256(sizeof(double) * 4) +
+                      align256(sizeof(double) * nb * std::max<int64_t>(*n_param, 9 * wf->dev.n_atom));
   if (wf->gws_bytes < need) {
     if (wf->gws) cudaFree(wf->gws);
     wf->gws = nullptr;
@@ -1099,9 +1099,28 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
     wf->gws_bytes = need;
   }
   char* p = static_cast<char*>(wf->gws);
-  double* e_loc = reinterpret_cast<double*>(p);
-  double* stats = reinterpret_cast<double*>(p + align256(sizeof(double) * n_walkers));
-  double* partial = reinterpret_cast<double*>(p + align256(sizeof(double) * n_walkers) + align256(16));
+  *e_loc = reinterpret_cast<double*>(p);
+  *stats = reinterpret_cast<double*>(p + align256(sizeof(double) * n_walkers));
+  *partial = reinterpret_cast<double*>(p + align256(sizeof(double) * n_walkers) + align256(sizeof(double) * 4));
+  return QMC_OK;
+}
+
+extern "C" {
+
+qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* e_stats,
+                           double* grad, double* forces, void* stream) {
+  if (!e_stats) return fail(QMC_ERR_ARG, "null e_stats");
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int64_t n_param = 0;
+  Workspace ws;
+  int* err_flag;
+  double *e_loc, *stats, *partial;
+  qmc_status s = grad_setup(wf, walkers, n_walkers, ldw, grad != nullptr, &n_param, &ws, &err_flag, &e_loc, &stats,
+                            &partial);
+  if (s) return s;
   s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, nullptr, st);
   if (s) return s;
   s = launch_status(launch_mean_var(e_loc, n_walkers, stats, st), "mean/variance");
@@ -1119,6 +1138,62 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
   cudaError_t e = cudaMemcpyAsync(e_stats, stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? QMC_OK : cuda_fail(e, "energy statistics");
+}
+
+int64_t qmc_energy_grad_sums_size(const qmc_wf* wf) {
+  if (!wf) return 0;
+  int64_t n_param = 0;
+  qmc_param_layout(wf, &n_param, nullptr);
+  return 3 + 2 * n_param + 9 * (int64_t)wf->dev.n_atom;
+}
+
+qmc_status qmc_energy_grad_sums(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, double* sums,
+                                void* stream) {
+  if (!sums) return fail(QMC_ERR_ARG, "null sums");
+  if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
+  std::lock_guard<std::mutex> lock(wf->mu);
+  DeviceGuard guard(wf->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int64_t n_param = 0;
+  Workspace ws;
+  int* err_flag;
+  double *e_loc, *stats, *partial;
+  qmc_status s =
+      grad_setup(wf, walkers, n_walkers, ldw, true, &n_param, &ws, &err_flag, &e_loc, &stats, &partial);
+  if (s) return s;
+  s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, nullptr, st);
+  if (s) return s;
+  s = launch_status(launch_energy_sums(e_loc, n_walkers, sums, st), "energy sums");
+  if (s) return s;
+  for (int weight = 1; weight <= 2 && !s; ++weight)
+    s = launch_status(launch_grad(wf->dev, walkers, n_walkers, ldw, e_loc, stats, wf->dev.ao_ang, wf->dev.ao_prim,
+                                  (int)n_param, partial, sums + 3 + (weight - 1) * n_param, st, weight),
+                      "parameter gradient sums");
+  if (s) return s;
+  return launch_status(launch_forces(wf->dev, walkers, n_walkers, ldw, e_loc, stats, partial, sums + 3 + 2 * n_param,
+                                     st, true),
+                       "force sums");
+}
+
+qmc_status qmc_assemble_energy_grad(int64_t n_param, int32_t n_atom, const double* sums, double* e_stats,
+                                    double* grad, double* forces) {
+  if (n_param < 0 || n_atom < 1 || !sums || !e_stats) return fail(QMC_ERR_ARG, "bad sizes or null sums / e_stats");
+  const double M = sums[0];
+  if (!(M >= 1.0)) return fail(QMC_ERR_ARG, "the sums cover no walker");
+  const double ev = sums[1] / M;
+  e_stats[0] = ev;
+  e_stats[1] = sums[2] / M - ev * ev;
+  const double* s_dlp = sums + 3;
+  const double* s_edlp = sums + 3 + n_param;
+  if (grad)
+    for (int64_t k = 0; k < n_param; ++k) grad[k] = 2.0 * (s_edlp[k] - ev * s_dlp[k]) / M;
+  const int64_t na3 = 3 * (int64_t)n_atom;
+  const double* s_de = sums + 3 + 2 * n_param;
+  const double* s_dr = s_de + na3;
+  const double* s_edr = s_dr + na3;
+  if (forces)
+    for (int64_t k = 0; k < na3; ++k) forces[k] = -(s_de[k] + s_edr[k] - ev * s_dr[k]) / M;
+  return QMC_OK;
 }
 
 qmc_status qmc_set_manybody_jastrow(qmc_wf* wf, const double* en, int32_t n_een, const double* een) {

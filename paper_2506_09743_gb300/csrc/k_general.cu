@@ -114,6 +114,51 @@ cudaError_t launch_eloc_general(const WfDev& wf, const double* walkers, int64_t 
   return cudaGetLastError();
 }
 
+// As k_mean_var over the finite values only: [0] mean, [1] mean square
+// deviation, [2] the number of non-finite values (a request's walkers on a
+// nucleus, a coalescence point or a node).
+__global__ void k_mean_var_finite(const double* __restrict__ x, int64_t W, double* __restrict__ stats) {
+  __shared__ double red[256];
+  __shared__ double cnt[256];
+  double s = 0.0, c = 0.0;
+  for (int64_t k = threadIdx.x; k < W; k += blockDim.x)
+    if (isfinite(x[k])) {
+      s += x[k];
+      c += 1.0;
+    }
+  red[threadIdx.x] = s;
+  cnt[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red[threadIdx.x] += red[threadIdx.x + o];
+      cnt[threadIdx.x] += cnt[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const double n = cnt[0], mean = n > 0.0 ? red[0] / n : __longlong_as_double(0x7ff8000000000000ll);
+  __syncthreads();
+  s = 0.0;
+  for (int64_t k = threadIdx.x; k < W; k += blockDim.x)
+    if (isfinite(x[k])) s += (x[k] - mean) * (x[k] - mean);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    stats[0] = mean;
+    stats[1] = n > 0.0 ? red[0] / n : mean;
+    stats[2] = (double)W - n;
+  }
+}
+
+cudaError_t launch_mean_var_finite(const double* x, int64_t W, double* stats, cudaStream_t st) {
+  k_mean_var_finite<<<1, 256, 0, st>>>(x, W, stats);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mean_var(const double* x, int64_t W, double* stats, cudaStream_t st) {
   k_mean_var<<<1, 256, 0, st>>>(x, W, stats);
   return cudaGetLastError();

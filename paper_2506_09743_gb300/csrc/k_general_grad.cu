@@ -8,18 +8,22 @@ namespace qmc {
 // Forces, Eq. force: per walker the tangents of E_L and log|Psi| along the
 // three coordinates of nucleus `atom` (forward mode), combined as
 //   f = -(d E_L + (E_L - E_v) 2 d log|Psi|) / M
-// and summed per block in a fixed order.
+// and summed per block in a fixed order.  With raw = true the kernel keeps
+// the three sums the estimator is assembled from instead (sharded batches):
+//   sum d E_L,  sum d ln rho,  sum E_L d ln rho      (ln rho = 2 log|Psi|)
+// in rows q * 3 n_atom + 3 atom + c, q = 0, 1, 2.
 template <int NE, int NO>
 __global__ void __launch_bounds__(128) k_forces(WfDev wf, const double* __restrict__ walkers, int64_t W, int64_t ldw,
                                                 const double* __restrict__ e_loc, const double* __restrict__ stats,
-                                                double* __restrict__ partial) {
+                                                double* __restrict__ partial, bool raw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GenShared g;
   stage_tables(wf, g, smem_raw);
-  __shared__ double red[3][128];
+  __shared__ double red[9][128];
   const int atom = blockIdx.y;
+  const int nq = raw ? 9 : 3;
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double f[3] = {0.0, 0.0, 0.0};
+  double f[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (w < W) {
     double r[NE][3];
     load_walker<NE>(walkers, ldw, w, wf.n_elec, r);
@@ -31,18 +35,30 @@ __global__ void __launch_bounds__(128) k_forces(WfDev wf, const double* __restri
       }
     Dual<3> e, lp;
     eval_walker<Dual<3>, NE, NO>(wf, g, r, R, true, e, lp, atom);
-    const double M = (double)W, de = e_loc[w] - stats[0];
-    for (int c = 0; c < 3; ++c) f[c] = -(e.d[c] + de * 2.0 * lp.d[c]) / M;
+    if (raw) {
+      const double el = e_loc[w];
+      for (int c = 0; c < 3; ++c) {
+        f[c] = e.d[c];
+        f[3 + c] = 2.0 * lp.d[c];
+        f[6 + c] = el * 2.0 * lp.d[c];
+      }
+    } else {
+      const double M = (double)W, de = e_loc[w] - stats[0];
+      for (int c = 0; c < 3; ++c) f[c] = -(e.d[c] + de * 2.0 * lp.d[c]) / M;
+    }
   }
-  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = f[c];
+  for (int q = 0; q < nq; ++q) red[q][threadIdx.x] = f[q];
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o)
-      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+      for (int q = 0; q < nq; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int c = 0; c < 3; ++c) partial[((size_t)atom * 3 + c) * gridDim.x + blockIdx.x] = red[c][0];
+    for (int q = 0; q < nq; ++q) {
+      const size_t row = (size_t)(q / 3) * 3 * wf.n_atom + (size_t)atom * 3 + q % 3;
+      partial[row * gridDim.x + blockIdx.x] = red[q][0];
+    }
 }
 
 // Parameter gradient of log|Psi| per walker (reverse mode written out), weighted
@@ -54,12 +70,16 @@ __global__ void __launch_bounds__(128) k_forces(WfDev wf, const double* __restri
 //   d log|Psi| / d d_0       = 1 / d_0
 //   d log|Psi| / d b         = -sum_{i<j} w0 r_ij^2 / (1 + b r_ij)^2
 //   d log|Psi| / d w         = sum_i sum_m (A^-1)_{m i} grad phi_m(r~_i) . sum_{j!=i} (r_i - r_j)/r_ij
+//
+// weight selects the per-walker factor: 0 the estimator's 2 (E_L - E_v) / M,
+// 1 one (sum d log|Psi|), 2 E_L (sum E_L d log|Psi|): the raw sums of a
+// sharded batch.
 template <int NE, int NO>
 __global__ void __launch_bounds__(128) k_grad_logpsi(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                      int64_t ldw, const double* __restrict__ e_loc,
                                                      const double* __restrict__ stats, const double* __restrict__ ang,
                                                      const int* __restrict__ prim_start, int n_param,
-                                                     double* __restrict__ partial) {
+                                                     double* __restrict__ partial, int weight) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GenShared g;
   stage_tables(wf, g, smem_raw);
@@ -72,7 +92,8 @@ __global__ void __launch_bounds__(128) k_grad_logpsi(WfDev wf, const double* __r
   const int off_c = n_prim, off_d = off_c + wf.n_ao * wf.n_mo, off_b = off_d + wf.n_det, off_w = off_b + 1;
   if (w < W) {
     const int N = wf.n_elec, nu = wf.n_up;
-    const double M = (double)W, wt = 2.0 * (e_loc[w] - stats[0]) / M;
+    const double M = (double)W;
+    const double wt = weight == 0 ? 2.0 * (e_loc[w] - stats[0]) / M : weight == 1 ? 1.0 : e_loc[w];
     double r[NE][3];
     load_walker<NE>(walkers, ldw, w, N, r);
     Pairs<NE> P;
@@ -175,13 +196,13 @@ __global__ void k_row_sums(const double* __restrict__ partial, int n_rows, int n
 // launchers
 
 cudaError_t launch_forces(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const double* e_loc,
-                          const double* stats, double* partial, double* forces, cudaStream_t st) {
+                          const double* stats, double* partial, double* forces, cudaStream_t st, bool raw) {
   const size_t smem = gen_table_bytes(wf);
   const dim3 grid((unsigned)general_blocks(W), (unsigned)wf.n_atom);
-  QMC_GEN_DISPATCH((k_forces<NE, NO><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, e_loc, stats, partial)));
+  QMC_GEN_DISPATCH((k_forces<NE, NO><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, e_loc, stats, partial, raw)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int rows = 3 * wf.n_atom;
+  const int rows = (raw ? 9 : 3) * wf.n_atom;
   k_row_sums<<<(rows + 127) / 128, 128, 0, st>>>(partial, rows, grid.x, forces);
   return cudaGetLastError();
 }
@@ -190,16 +211,46 @@ size_t grad_smem_bytes(const WfDev& wf, int n_param) { return gen_table_bytes(wf
 
 cudaError_t launch_grad(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const double* e_loc,
                         const double* stats, const double* ang, const int* prim_start, int n_param, double* partial,
-                        double* grad, cudaStream_t st) {
+                        double* grad, cudaStream_t st, int weight) {
   const size_t smem = grad_smem_bytes(wf, n_param);
   const dim3 grid((unsigned)general_blocks(W));
   QMC_GEN_DISPATCH((cudaFuncSetAttribute(k_grad_logpsi<NE, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem),
                     k_grad_logpsi<NE, NO><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, e_loc, stats, ang,
-                                                                   prim_start, n_param, partial)));
+                                                                   prim_start, n_param, partial, weight)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_row_sums<<<(n_param + 127) / 128, 128, 0, st>>>(partial, n_param, grid.x, grad);
+  return cudaGetLastError();
+}
+
+// M, sum E_L and sum E_L^2 of a batch in a fixed order (one block)
+__global__ void k_energy_sums(const double* __restrict__ e, int64_t W, double* __restrict__ out) {
+  __shared__ double s1[256], s2[256];
+  double a = 0.0, b = 0.0;
+  for (int64_t w = threadIdx.x; w < W; w += blockDim.x) {
+    a += e[w];
+    b += e[w] * e[w];
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = (double)W;
+    out[1] = s1[0];
+    out[2] = s2[0];
+  }
+}
+
+cudaError_t launch_energy_sums(const double* e_loc, int64_t W, double* out, cudaStream_t st) {
+  k_energy_sums<<<1, 256, 0, st>>>(e_loc, W, out);
   return cudaGetLastError();
 }
 

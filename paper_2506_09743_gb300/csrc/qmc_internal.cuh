@@ -238,11 +238,18 @@ size_t grad_smem_bytes(const WfDev& wf, int n_param);
 cudaError_t launch_eloc_general(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, bool kinetic,
                                 double* e_loc, double* log_psi, cudaStream_t st);
 cudaError_t launch_mean_var(const double* x, int64_t W, double* stats, cudaStream_t st);
+// mean and variance of the finite values; stats[2] = number of non-finite values
+cudaError_t launch_mean_var_finite(const double* x, int64_t W, double* stats, cudaStream_t st);
+// raw = false: the forces of Eq. force; raw = true: the three sums of a
+// sharded batch (sum d E_L, sum d ln rho, sum E_L d ln rho), 9 n_atom values
 cudaError_t launch_forces(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const double* e_loc,
-                          const double* stats, double* partial, double* forces, cudaStream_t st);
+                          const double* stats, double* partial, double* forces, cudaStream_t st, bool raw = false);
+// weight 0: the gradient of Eq. nabla_loss; 1: sum d log|Psi|; 2: sum E_L d log|Psi|
 cudaError_t launch_grad(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const double* e_loc,
                         const double* stats, const double* ang, const int* prim_start, int n_param, double* partial,
-                        double* grad, cudaStream_t st);
+                        double* grad, cudaStream_t st, int weight = 0);
+// out[0..2] = M, sum E_L, sum E_L^2 (one block, fixed order)
+cudaError_t launch_energy_sums(const double* e_loc, int64_t W, double* out, cudaStream_t st);
 
 // kernel launchers (return cudaError_t of the launch)
 // dynamic shared memory of the electron-electron-nucleus Jastrow kernel

@@ -98,7 +98,8 @@ struct Slot {
   bool busy = false;
   Pending job{};
   size_t off = 0, bytes = 0;
-  double* host = nullptr;  // pinned [4]: mean, variance, accepted moves, status word (bytes of [3])
+  double* host = nullptr;  // pinned [6]: mean, variance, non-finite count, accepted moves, status word (bytes of [4])
+  bool cancelled = false;  // qmc_server_cancel while in flight: reported as cancelled on retirement
   double t_admit = 0.0;
 };
 
@@ -142,7 +143,7 @@ InitSpec make_homes(const qmc_wf* wf) {
 size_t request_bytes(qmc_wf* wf, int64_t W) {
   const int N = wf->dev.n_elec;
   return a256(sizeof(double) * 3 * N * W) + a256(sizeof(double) * W) + a256(sizeof(int64_t) * W) +
-         a256(sizeof(double) * 4) + a256(qmc_workspace_size(wf, W));
+         a256(sizeof(double) * 8) + a256(qmc_workspace_size(wf, W));
 }
 
 qmc_status launch_job(qmc_server* srv, Slot& sl) {
@@ -157,8 +158,8 @@ qmc_status launch_job(qmc_server* srv, Slot& sl) {
   p += a256(sizeof(double) * W);
   int64_t* acc = reinterpret_cast<int64_t*>(p);
   p += a256(sizeof(int64_t) * W);
-  double* stats = reinterpret_cast<double*>(p);
-  p += a256(sizeof(double) * 4);
+  double* stats = reinterpret_cast<double*>(p);  // mean, variance, non-finite count, accepted moves
+  p += a256(sizeof(double) * 8);
   void* ws = p;
   const size_t ws_bytes = qmc_workspace_size(wf, W);
   cudaStream_t st = sl.stream;
@@ -176,11 +177,11 @@ qmc_status launch_job(qmc_server* srv, Slot& sl) {
     s = sample_call(wf, walkers, W, W, r.n_steps, r.step, r.seed, 0, 0, nullptr, acc, ws, ws_bytes, st, false);
   if (s == QMC_OK) s = local_energy_call(wf, walkers, W, W, e_loc, nullptr, ws, ws_bytes, st, false);
   if (s != QMC_OK) return sfail(s, std::string("request kernels: ") + qmc_last_error());
-  e = launch_mean_var(e_loc, W, stats, st);
-  if (e == cudaSuccess) e = launch_sum_counts(acc, W, stats + 2, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.host, stats, sizeof(double) * 3, cudaMemcpyDeviceToHost, st);
-  sl.host[3] = 0.0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host[3], status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  e = launch_mean_var_finite(e_loc, W, stats, st);
+  if (e == cudaSuccess) e = launch_sum_counts(acc, W, stats + 3, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.host, stats, sizeof(double) * 4, cudaMemcpyDeviceToHost, st);
+  sl.host[4] = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host[4], status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
   if (e != cudaSuccess) return sfail(QMC_ERR_CUDA, std::string("request reduction: ") + cudaGetErrorString(e));
   return QMC_OK;
@@ -212,7 +213,7 @@ qmc_status qmc_server_create(int32_t device, size_t hbm_budget_bytes, int32_t ma
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.hi, cudaStreamNonBlocking, greatest);
     sl.stream = sl.hi;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost(&sl.host, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&sl.host, sizeof(double) * 6);
     if (e != cudaSuccess) {
       qmc_server_destroy(srv);
       return sfail(QMC_ERR_CUDA, std::string("server slots: ") + cudaGetErrorString(e));
@@ -277,16 +278,20 @@ qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n
     res.t_admit = sl.t_admit;
     res.t_done = now_s();
     int timed_out = 0;
-    std::memcpy(&timed_out, &sl.host[3], sizeof(int));
-    if (q == cudaSuccess && timed_out) {
+    std::memcpy(&timed_out, &sl.host[4], sizeof(int));
+    if (sl.cancelled) {
+      res.status = QMC_ERR_CANCELLED;
+      res.e_mean = res.e_var = res.accept_rate = NAN;
+    } else if (q == cudaSuccess && timed_out) {
       res.status = QMC_ERR_TIMEOUT;
       res.e_mean = res.e_var = res.accept_rate = NAN;
     } else if (q == cudaSuccess) {
       res.status = QMC_OK;
       res.e_mean = sl.host[0];
       res.e_var = sl.host[1];
+      res.n_nonfinite = (int64_t)sl.host[2];
       const double moves = (double)sl.job.req.n_walkers * sl.job.req.n_steps;
-      res.accept_rate = moves > 0 ? sl.host[2] / moves : 0.0;
+      res.accept_rate = moves > 0 ? sl.host[3] / moves : 0.0;
     } else {
       res.status = QMC_ERR_CUDA;
       res.e_mean = res.e_var = res.accept_rate = NAN;
@@ -294,6 +299,7 @@ qmc_status qmc_server_progress(qmc_server* srv, int32_t* n_in_flight, int32_t* n
     srv->results.push_back(res);
     srv->arena.release(sl.off, sl.bytes);
     sl.busy = false;
+    sl.cancelled = false;
   }
   // Admit queued requests in arrival order while a slot and memory are free.
   // Large requests (>= big_walkers walkers) keep their arrival order among
@@ -364,6 +370,30 @@ qmc_status qmc_server_results(qmc_server* srv, qmc_result* out, int32_t capacity
   srv->results.erase(srv->results.begin(), srv->results.begin() + n);
   *n_out = n;
   return QMC_OK;
+}
+
+qmc_status qmc_server_cancel(qmc_server* srv, int64_t ticket) {
+  if (!srv) return sfail(QMC_ERR_ARG, "null server");
+  for (auto it = srv->queue.begin(); it != srv->queue.end(); ++it)
+    if (it->ticket == ticket) {  // never admitted: no device work, no memory
+      qmc_result res{};
+      res.ticket = ticket;
+      res.status = QMC_ERR_CANCELLED;
+      res.wf_id = it->req.wf_id;
+      res.n_walkers = it->req.n_walkers;
+      res.e_mean = res.e_var = res.accept_rate = NAN;
+      res.t_submit = it->t_submit;
+      res.t_admit = res.t_done = now_s();
+      srv->results.push_back(res);
+      srv->queue.erase(it);
+      return QMC_OK;
+    }
+  for (auto& sl : srv->slots)
+    if (sl.busy && sl.job.ticket == ticket) {  // in flight: its kernels finish, its result is dropped
+      sl.cancelled = true;
+      return QMC_OK;
+    }
+  return sfail(QMC_ERR_ARG, "ticket " + std::to_string(ticket) + " is neither queued nor in flight");
 }
 
 qmc_status qmc_server_set_policy(qmc_server* srv, int64_t big_walkers, int32_t max_big_in_flight) {

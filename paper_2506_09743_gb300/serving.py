@@ -71,6 +71,10 @@ class Server:
             out.append({f: getattr(r, f) for f, _ in _lib.Result._fields_})
         return out
 
+    def cancel(self, ticket: int):
+        """Cancel a queued or running request (its result reports QMC_ERR_CANCELLED)."""
+        _lib.check_server(self._lib.qmc_server_cancel(self._h, int(ticket)))
+
     def set_policy(self, big_walkers: int, max_big_in_flight: int):
         _lib.check_server(self._lib.qmc_server_set_policy(self._h, int(big_walkers), int(max_big_in_flight)))
 
@@ -142,6 +146,7 @@ def summarize(done, n_steps: int):
     return {
         "requests": len(done),
         "failed": int(sum(1 for d in done if d["status"] != 0)),
+        "nonfinite_walkers": int(sum(d.get("n_nonfinite", 0) for d in done)),
         "p50_ms": float(np.percentile(lat, 50) * 1e3),
         "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "makespan_s": float(t_last - t_first),

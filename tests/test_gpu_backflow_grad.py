@@ -186,3 +186,29 @@ def test_full_size_li2_energy_gradient_runs(pkg):
     e, _ = wf.local_energy(_x(r))
     torch.cuda.synchronize()
     fp64_check(e.cpu().numpy()[idx], E_ref, sens)
+
+
+@pytest.mark.parametrize("name", ["li2", "lih"])
+def test_sharded_sums_reproduce_the_whole_batch(pkg, name):
+    """Per-batch sums of two uneven halves, added (the all-reduce of a
+    sharded sample) and assembled, give qmc_energy_grad on the whole batch
+    (Eq. nabla_loss, Eq. force) to 1e-10."""
+    from paper_2506_09743_gb300 import _lib
+
+    mol = qi.make_molecule(name)
+    W, cut = 1000, 417
+    r = qi.walkers(mol, W, seed=53)
+    wf = pkg.Wavefunction(mol, precision="fp64")
+    e_mean, e_var, grad, forces = wf.energy_grad(_x(r))
+    s = wf.energy_grad_sums(_x(r[:cut])) + wf.energy_grad_sums(_x(r[cut:]))
+    n, _ = wf.param_layout()
+    ev, var, g, f = _lib.assemble_energy_grad(s.cpu().numpy(), n, mol.n_atom)
+    g_ref, f_ref = grad.cpu().numpy(), forces.cpu().numpy()
+    assert abs(ev - e_mean) <= 1e-10 * abs(e_mean)
+    assert abs(var - e_var) <= 1e-8 * e_var
+    assert np.abs(g - g_ref).max() <= 1e-10 * np.abs(g_ref).max()
+    assert np.abs(f - f_ref).max() <= 1e-10 * max(1.0, np.abs(f_ref).max())
+    s1 = wf.energy_grad_sums(_x(r))
+    s2 = wf.energy_grad_sums(_x(r))
+    assert torch.equal(s1, s2)  # fixed summation order
+    wf.close()

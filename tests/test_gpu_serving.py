@@ -150,3 +150,60 @@ def test_policy_arguments_are_checked(mix):
     with pytest.raises(QmcError):
         srv.set_policy(1000, 0)
     srv.close()
+
+
+def test_cancel_queued_and_running_requests(pkg):
+    """qmc_server_cancel: a queued request is removed without device work, a
+    running one finishes its kernels but reports QMC_ERR_CANCELLED; the other
+    requests are unaffected and the arena is whole again."""
+    from paper_2506_09743_gb300 import serving
+    from paper_2506_09743_gb300._lib import QMC_ERR_ARG, QMC_ERR_CANCELLED, QmcError
+
+    wf = pkg.Wavefunction(qi.make_lih(), precision="fp64")
+    srv = serving.Server(hbm_budget_bytes=1 << 30, max_in_flight=1)
+    i = srv.add(wf)
+    t = [srv.submit(i, 4096, 10, 0.05, 100 + k) for k in range(5)]
+    srv.progress()  # admits t[0] (one slot)
+    srv.cancel(t[0])  # running
+    srv.cancel(t[2])  # queued
+    srv.cancel(t[3])  # queued
+    res = {r["ticket"]: r for r in srv.drain()}
+    assert sorted(res) == sorted(t)
+    for k in (0, 2, 3):
+        assert res[t[k]]["status"] == QMC_ERR_CANCELLED and np.isnan(res[t[k]]["e_mean"])
+    for k in (1, 4):
+        assert res[t[k]]["status"] == 0 and np.isfinite(res[t[k]]["e_mean"])
+    with pytest.raises(QmcError) as ei:
+        srv.cancel(t[1])  # already finished
+    assert ei.value.status == QMC_ERR_ARG
+    assert srv.free_bytes() == srv.budget
+    # the cancelled requests' seeds give the same results when run afresh
+    t2 = srv.submit(i, 4096, 10, 0.05, 101)
+    again = srv.drain()
+    assert again[0]["e_mean"] == res[t[1]]["e_mean"]
+    srv.close()
+    wf.close()
+
+
+def test_nonfinite_walkers_are_counted_not_averaged(pkg):
+    """A walker with an electron exactly on a nucleus has no finite local
+    energy: the request's result counts it and averages the others."""
+    from paper_2506_09743_gb300 import serving
+
+    mol = qi.make_h2()
+    W = 256
+    r = qi.walkers(mol, W, seed=61)
+    r[5, 0] = mol.atom_xyz[0]  # electron 0 of walker 5 on nucleus 0
+    r[9, 1] = mol.atom_xyz[1]
+    wf = pkg.Wavefunction(mol, precision="fp64")
+    srv = serving.Server(hbm_budget_bytes=1 << 28, max_in_flight=2)
+    i = srv.add(wf)
+    srv.submit(i, W, 0, 0.05, 1, walkers=qi.to_soa(r))
+    res = srv.drain()[0]
+    e, _ = wf.local_energy(torch.tensor(qi.to_soa(r), device="cuda"))
+    e = e.cpu().numpy()
+    fin = np.isfinite(e)
+    assert res["status"] == 0 and res["n_nonfinite"] == int((~fin).sum()) == 2
+    assert abs(res["e_mean"] - e[fin].mean()) <= 1e-12 * abs(e[fin].mean())
+    srv.close()
+    wf.close()

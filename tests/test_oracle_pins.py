@@ -536,3 +536,24 @@ def test_planted_mistake_in_transposed_inverse_is_caught(monkeypatch):
     real_inv = torch.linalg.inv
     monkeypatch.setattr(torch.linalg, "inv", lambda A: real_inv(A).transpose(-1, -2))
     assert _rel(O.local_energy(wf, r), good) > 1e-6
+
+
+def test_energy_gradient_sums_assemble_to_the_estimator():
+    """The per-batch sums assembled by the closed formulas give the same
+    estimator as the direct one, with the batch mean as E_v (Eq. nabla_loss,
+    Eq. force); and splitting the batch into two parts and adding their sums
+    changes nothing (the sums are additive)."""
+    mol = qi.make_lih()
+    wf = O.Wavefunction(mol, requires_grad=True)
+    r = torch.tensor(qi.walkers(mol, 24, seed=52))
+    Ev, var, grad, F = O.energy_grad(wf, r)
+    n_param = sum(p.numel() for p in wf.params().values())
+    whole = O.energy_grad_sums(wf, r)
+    parts = O.energy_grad_sums(wf, r[:10]) + O.energy_grad_sums(wf, r[10:])
+    assert whole.shape[0] == 3 + 2 * n_param + 9 * mol.n_atom
+    for sums in (whole, parts):
+        ev2, var2, g2, f2 = O.assemble_energy_grad(sums, n_param, mol.n_atom)
+        assert abs(float(ev2 - Ev)) <= 1e-12 * abs(float(Ev))
+        assert abs(float(var2 - var)) <= 1e-10 * float(var)
+        assert float((g2 - grad).abs().max()) <= 1e-12 * float(grad.abs().max())
+        assert float((f2 - F).abs().max()) <= 1e-12 * max(1.0, float(F.abs().max()))
