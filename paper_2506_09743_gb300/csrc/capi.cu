@@ -311,7 +311,7 @@ qmc_status build_tables(qmc_wf* wf) {
   // 8-byte stores; a shell that does not fit in the pass starts the next one.
   std::vector<int> ao_col(nao, 0), tc_shells;
   d.n_pass = 0;
-  if (tc) {
+  if (tc || prec == QMC_FP32X2) {
     std::vector<int> shell_col(d.n_shell), shell_type(d.n_shell), shell_pass(d.n_shell);
     std::vector<int> canon_all(nao, 0);
     for (int s = 0; s < d.n_shell; ++s) {
@@ -482,7 +482,7 @@ qmc_status build_tables(qmc_wf* wf) {
     return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
 
   // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
-  d.k_pad = tc ? d.n_pass * kTcPass : 0;
+  d.k_pad = (tc || prec == QMC_FP32X2) ? d.n_pass * kTcPass : 0;
   if (tc && tc_smem_bytes(d, 2) > 227 * 1024)
     return fail(QMC_ERR_UNSUPPORTED, "tensor-core AO stage exceeds shared memory (too many AOs or shells)");
   std::vector<uint32_t> tc_hi, tc_lo;
@@ -502,6 +502,39 @@ qmc_status build_tables(qmc_wf* wf) {
       }
   }
 
+  // ---- FP32X2 form on the tensor cores: MO column m scaled by 2^-f_m
+  // (max |C_bm| < 2^f_m) and written as six balanced digits of 8 bits,
+  // exactly (FP64 steps), as BF16 in the K-major core-matrix layout
+  std::vector<uint16_t> mo_oz;
+  d.oz = 0;
+  for (int m = 0; m < 16; ++m) d.oz_colexp[m] = 0;
+  if (prec == QMC_FP32X2 && nmo <= 16 && d.n_pass > 0) {
+    const int kp = d.k_pad;
+    mo_oz.assign((size_t)6 * 16 * kp, 0);
+    for (int m = 0; m < nmo; ++m) {
+      double cmax = 0.0;
+      for (int b = 0; b < nao; ++b) cmax = std::max(cmax, std::fabs(mo64[(size_t)b * nmo + m]));
+      int f = 0;
+      if (cmax > 0.0) std::frexp(cmax, &f);  // cmax = x 2^f, x in [0.5, 1)
+      d.oz_colexp[m] = f;
+      for (int b = 0; b < nao; ++b) {
+        double y = std::ldexp(mo64[(size_t)b * nmo + m], -f);
+        const int k = ao_col[b];
+        const size_t off = (size_t)(m / 8) * (kp / 8) * 64 + (size_t)(k / 8) * 64 + (m % 8) * 8 + (k % 8);
+        for (int l = 0; l < 6; ++l) {
+          y *= 256.0;
+          const double dl = std::nearbyint(y);
+          y -= dl;
+          const float df = (float)dl;  // |dl| <= 256: exact in BF16
+          uint32_t u;
+          std::memcpy(&u, &df, 4);
+          mo_oz[(size_t)l * 16 * kp + off] = (uint16_t)(u >> 16);
+        }
+      }
+    }
+    d.oz = 1;  // confirmed by oz_supported below, once the other tables are known
+  }
+
   // ---- upload everything in one blob
   DeviceGuard guard(wf->device);
   std::vector<std::pair<const void*, size_t>> parts = {
@@ -512,7 +545,8 @@ qmc_status build_tables(qmc_wf* wf) {
       {tc_lo.data(), sizeof(uint32_t) * tc_lo.size()},  {ang.data(), sizeof(double) * nao},
       {h.prim_start.data(), sizeof(int) * (nao + 1)}, {ao_col.data(), sizeof(int) * nao},
       {tc_shells.data(), sizeof(int) * tc_shells.size()}, {det_tab.data(), sizeof(int) * det_tab.size()},
-      {mo_x2.data(), sizeof(float) * mo_x2.size()},      {exp_tab.data(), sizeof(float) * exp_tab.size()}};
+      {mo_x2.data(), sizeof(float) * mo_x2.size()},      {exp_tab.data(), sizeof(float) * exp_tab.size()},
+      {mo_oz.data(), sizeof(uint16_t) * mo_oz.size()}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
   void* blob = nullptr;
@@ -550,6 +584,8 @@ qmc_status build_tables(qmc_wf* wf) {
   d.det_tab = reinterpret_cast<const int4*>(ptr[13]);
   d.mo_x2 = reinterpret_cast<const float2*>(ptr[14]);
   d.exp_tab = reinterpret_cast<const float*>(ptr[15]);
+  d.mo_oz = reinterpret_cast<const uint16_t*>(ptr[16]);
+  if (d.oz && !oz_supported(d)) d.oz = 0;  // the SIMT pair kernel serves this wavefunction
   // the previous tables may still be read by work in flight on any stream
   if (wf->blob) {
     cudaDeviceSynchronize();
@@ -726,10 +762,11 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   if (mapped) walkers = stage;
   mark(wf, 1, st);
   mark(wf, 2, st);
-  s = launch_status(tc                                ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag,
-                                                                    wf->err_wf, st)
-                    : wf->precision == QMC_FP32X2 ? launch_ao_mo_x2(d, walkers, W, ldw, v, nch, st)
-                                                  : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, v, nch, st),
+  const bool x2 = wf->precision == QMC_FP32X2;
+  s = launch_status(tc          ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag, wf->err_wf, st)
+                    : x2 && d.oz ? launch_ao_mo_oz(d, walkers, W, ldw, v, nch, err_flag, wf->err_wf, st)
+                    : x2         ? launch_ao_mo_x2(d, walkers, W, ldw, v, nch, st)
+                                 : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, v, nch, st),
                     "ao_mo");
   if (s) return s;
   mark(wf, 3, st);
@@ -750,7 +787,8 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
 // workspace's status word first (a later read tells whether this call's waits
 // gave up).
 static bool has_device_waits(const qmc_wf* wf) {
-  return wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
+  return wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16 ||
+         (wf->precision == QMC_FP32X2 && wf->dev.oz);
 }
 
 static qmc_status reset_status(const qmc_wf* wf, int* err_flag, cudaStream_t st) {

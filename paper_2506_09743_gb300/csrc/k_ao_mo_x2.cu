@@ -36,16 +36,6 @@ __device__ __forceinline__ f32x2 ld_x2(const float2* p) {
   return f32x2(v.x, v.y);
 }
 
-// r - a for a position r and a nucleus a given in FP64, as a pair (both are
-// split into pairs first; the difference is exact to 2^-48 of max(|r|, |a|))
-__device__ __forceinline__ f32x2 diff_x2(double r, double a) {
-  float rh, rl, ah, al;
-  split_f64(r, rh, rl);
-  split_f64(a, ah, al);
-  const f32x2 s = two_sum(rh, -ah);
-  return two_sum(s.hi, x2_add_rn(s.lo, x2_sub_rn(rl, al)));
-}
-
 __device__ __forceinline__ f32x2 x2_expo(const ShellDev& sh, int p) { return f32x2(sh.expo_f[p], sh.expo_lo[p]); }
 __device__ __forceinline__ f32x2 x2_coef(const ShellDev& sh, int p) { return f32x2(sh.coef_f[p], sh.coef_lo[p]); }
 

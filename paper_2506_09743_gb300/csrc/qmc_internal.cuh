@@ -74,6 +74,12 @@ struct WfDev {
   const double* mo64;      // [n_ao][n_mo] MO coefficients x AO angular factors
   const float* mo32;       // same, FP32
   const float2* mo_x2;     // same as pairs of FP32 (hi, lo) for the FP32X2 form
+  // FP32X2 form on the tensor cores: MO columns scaled by 2^-oz_colexp[m] and
+  // cut into six signed 8-bit digits, BF16 [6][16][k_pad] in the K-major
+  // core-matrix layout of the B operand (oz_digits.cuh, k_ao_mo_oz.cu)
+  const uint16_t* mo_oz;
+  int oz_colexp[16];
+  int oz;                  // 1: the FP32X2 form contracts on the tensor cores
   const float* exp_tab;    // [64][2] 2^(j/64) as pairs: exp of the FP32X2 form
   const int* exc;          // [2][kMaxExc][5] rank, h1, h2, p1, p2
   const int* det_idx;      // [n_det][2] excitation index per spin
@@ -260,7 +266,12 @@ cudaError_t launch_jastrow(const WfDev& wf, int prec, const double* walkers, int
                            const Workspace& ws, bool derivs, cudaStream_t st);
 cudaError_t launch_ao_mo_simt(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,
                               const Workspace& ws, int nch, cudaStream_t st);
-// pairs of FP32 (QMC_FP32X2 form)
+// pairs of FP32 (QMC_FP32X2 form): SIMT contraction, and the digit-sliced
+// tensor-core contraction where oz_supported
+size_t oz_smem_bytes(const WfDev& wf, int nch);
+bool oz_supported(const WfDev& wf);
+cudaError_t launch_ao_mo_oz(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                            int nch, int* err_flag, int* err_wf, cudaStream_t st);
 cudaError_t launch_ao_mo_x2(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                             int nch, cudaStream_t st);
 cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, int64_t W, int64_t ldw,

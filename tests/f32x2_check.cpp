@@ -4,9 +4,11 @@
 // that the error-free transformations are evaluated as written.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <random>
 
 #include "../paper_2506_09743_gb300/csrc/f32x2.cuh"
+#include "../paper_2506_09743_gb300/csrc/oz_digits.cuh"
 
 using qmc::f32x2;
 
@@ -73,6 +75,58 @@ int main() {
     e_dot = std::fmax(e_dot, (double)(fabsl(val(s) - ref) / mag));
     e_norm = std::fmax(e_norm, fabsf(s.lo) / fmaxf(fabsf(s.hi), 1e-30f));
   }
+  // digit-sliced contraction (oz_digits.cuh): rows of 58 pair values of
+  // spread magnitude against FP64 columns, digits of both, exact integer
+  // class sums (checked below 2^24 and against the BF16 range), recombined;
+  // error relative to K 2^(e + f), the scale of the dropped digit classes
+  double e_oz = 0;
+  long long max_class = 0;
+  int bad_digit = 0;
+  for (int t = 0; t < 4000; ++t) {
+    const int K = 58;
+    f32x2 a[K];
+    double c[K];
+    long double amax = 0, cmax = 0;
+    for (int b = 0; b < K; ++b) {
+      a[b] = from_ld((u01(rng) - 0.5) * expl(-30.0L * u01(rng)));
+      c[b] = (u01(rng) - 0.5) * pow(10.0, -3.0 * u01(rng));
+      amax = fmaxl(amax, fabsl(val(a[b])));
+      cmax = fmaxl(cmax, fabsl((long double)c[b]));
+    }
+    // row scale from a bound within 2x of the maximum (the kernel's slack)
+    const int ea = ilogbl(amax * (1.0L + u01(rng))) + 2;
+    const int fc = ilogbl(cmax) + 1;
+    long long cls[qmc::kOzClasses] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < K; ++b) {
+      const f32x2 xs(ldexpf(a[b].hi, -ea), ldexpf(a[b].lo, -ea));
+      float d[qmc::kOzDigits];
+      qmc::oz_digits(xs, d);
+      double y = ldexp(c[b], -fc), dl[qmc::kOzDigits];
+      for (int l = 0; l < qmc::kOzDigits; ++l) {
+        y *= 256.0;
+        dl[l] = nearbyint(y);
+        y -= dl[l];
+      }
+      for (int k = 0; k < qmc::kOzDigits; ++k) {
+        if (fabsf(d[k]) > 256.0f || d[k] != nearbyintf(d[k])) ++bad_digit;
+        for (int l = 0; l < qmc::kOzDigits; ++l)
+          if (k + l <= 5) cls[k + l] += (long long)d[k] * (long long)dl[l];
+      }
+    }
+    float acc[qmc::kOzClasses];
+    for (int g = 0; g < qmc::kOzClasses; ++g) {
+      max_class = std::max(max_class, std::llabs(cls[g]));
+      acc[g] = (float)cls[g];
+    }
+    const f32x2 s = qmc::oz_combine(acc);
+    const long double got = ldexpl(val(s), ea + fc - 16);
+    long double ref = 0;
+    for (int b = 0; b < K; ++b) ref += val(a[b]) * (long double)c[b];
+    // the scheme's scale: K terms of at most 2^(ea + fc) each
+    e_oz = std::fmax(e_oz, (double)(fabsl(got - ref) / ldexpl((long double)K, ea + fc)));
+  }
+  std::printf("oz_contraction %.3e\noz_max_class_log2 %.3f\noz_bad_digits %d\n", e_oz,
+              std::log2((double)max_class), bad_digit);
   std::printf("exp %.3e\nexp_tiny_abs %.3e\nmul %.3e\nadd %.3e\ndiv %.3e\nsqrt %.3e\nrsqrt %.3e\ndot %.3e\nnorm %.3e\nexp_unnormalised %d\n",
               e_exp, e_exp_tiny, e_mul, e_add, e_div, e_sqrt, e_rsqrt, e_dot, e_norm, bad_norm);
   return 0;

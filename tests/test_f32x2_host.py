@@ -1,4 +1,5 @@
-"""Host check of the pair-of-FP32 arithmetic used by the QMC_FP32X2 form.
+"""Host check of the pair-of-FP32 arithmetic used by the QMC_FP32X2 form, and
+of the digit slicing that lets the tensor cores contract pairs exactly.
 
 The header paper_2506_09743_gb300/csrc/f32x2.cuh is compiled as plain C++ (no
 FMA contraction) together with tests/f32x2_check.cpp, which compares every
@@ -24,7 +25,18 @@ BOUNDS = {
     "rsqrt": 5e-14,
     "dot": 2e-13,     # relative to sum |a_k b_k|, 64 terms
     "norm": 2.0 ** -24 * 1.001,  # |lo| <= ulp(hi) / 2 after normalisation
+    # digit-sliced contraction: dropped digit classes and digit residuals,
+    # at most 2^-46 per term of K 2^(e + f)
+    "oz_contraction": 2.0 ** -46,
 }
+
+
+def test_digit_class_sums_stay_exact(results):
+    """Every class sum of digit products stays below 2^24 (exact in FP32
+    accumulation) and every digit is an integer of magnitude <= 256 (exact
+    in BF16)."""
+    assert results["oz_max_class_log2"] < 24.0
+    assert results["oz_bad_digits"] == 0
 
 
 @pytest.fixture(scope="module")
