@@ -63,13 +63,17 @@ typedef enum {
  *                  TF32 inputs split into high and low parts (three products,
  *                  FP32 accumulation in tensor memory); FP64 determinants.
  *  QMC_MIXED_BF16  not built: QMC_ERR_UNSUPPORTED.
- *  QMC_FP32X2      AOs and the AO->MO contraction in pairs of FP32 (hi + lo,
- *                  about 48 significant bits, on the FP32 pipes), Coulomb
- *                  potential in pairs of FP32, FP64 determinants: MO values
- *                  within a few 2^-46 of |AO||C|, so that the local energy
- *                  matches the FP64 form to 2e-4 Ha on every walker away from
- *                  the nodes (where FP32 AOs leave about one CO walker in six
- *                  beyond it).
+ *  QMC_FP32X2      local energies with AOs in pairs of FP32 (hi + lo, about
+ *                  48 significant bits, on the FP32 pipes), the AO->MO
+ *                  contraction exact on the tcgen05 tensor cores (the pairs
+ *                  cut into BF16 digits; SIMT pairs when n_mo > 16 or
+ *                  n_ao > 96), Coulomb potential in pairs of FP32, FP64
+ *                  determinants: MO values within about 2^-43 of |AO||C|, so
+ *                  that the local energy matches the FP64 form to 2e-4 Ha on
+ *                  every walker away from the nodes (where FP32 AOs leave
+ *                  about one CO walker in six beyond it).  The Metropolis
+ *                  value path (log|Psi| of the acceptance test) runs the
+ *                  MIXED_TF32 stages: FP32-level log|Psi|.
  * Jastrow terms are FP64 in QMC_FP64 and use FP32 pair arithmetic with
  * compensated sums in the other forms; the Coulomb potential is FP64 in
  * QMC_FP64, pairs of FP32 in QMC_FP32X2 and FP32 terms with compensated

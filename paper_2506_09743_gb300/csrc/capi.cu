@@ -485,8 +485,11 @@ qmc_status build_tables(qmc_wf* wf) {
   d.k_pad = (tc || prec == QMC_FP32X2) ? d.n_pass * kTcPass : 0;
   if (tc && tc_smem_bytes(d, 2) > 227 * 1024)
     return fail(QMC_ERR_UNSUPPORTED, "tensor-core AO stage exceeds shared memory (too many AOs or shells)");
+  // the FP32X2 form's Metropolis value path (log|Psi| for the acceptance
+  // test) runs the FP32-AO tensor-core stage when it fits
+  d.tc_value = (prec == QMC_FP32X2 && nmo <= 16 && d.n_pass > 0 && tc_smem_bytes(d, 1) <= 227 * 1024) ? 1 : 0;
   std::vector<uint32_t> tc_hi, tc_lo;
-  if (tc) {
+  if (tc || d.tc_value) {
     tc_hi.assign((size_t)16 * d.k_pad, 0u);
     tc_lo.assign((size_t)16 * d.k_pad, 0u);
     for (int m = 0; m < nmo; ++m)
@@ -754,16 +757,21 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   const bool tc = wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16;
   const int nch = kinetic ? 2 : 1;
   const Workspace& v = ws;
+  // FP32X2 value path: log|Psi| for the Metropolis acceptance test needs
+  // FP32-level MO values only (the 2e-4 Ha gate concerns E_L); it runs the
+  // Jastrow and FP32-AO tensor-core stages of the mixed form
+  const bool x2_value = wf->precision == QMC_FP32X2 && !kinetic && d.tc_value;
   mark(wf, 0, st);
-  qmc_status s = launch_status(
-      launch_jastrow(d, wf->precision, mapped ? mapped : walkers, W, ldw, mapped ? stage : nullptr, v, kinetic, st),
-      "jastrow");
+  qmc_status s = launch_status(launch_jastrow(d, x2_value ? QMC_MIXED_TF32 : wf->precision, mapped ? mapped : walkers, W,
+                                              ldw, mapped ? stage : nullptr, v, kinetic, st),
+                               "jastrow");
   if (s) return s;
   if (mapped) walkers = stage;
   mark(wf, 1, st);
   mark(wf, 2, st);
   const bool x2 = wf->precision == QMC_FP32X2;
-  s = launch_status(tc          ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag, wf->err_wf, st)
+  s = launch_status(x2_value    ? launch_ao_mo_tc(d, QMC_MIXED_TF32, walkers, W, ldw, v, nch, err_flag, wf->err_wf, st)
+                    : tc        ? launch_ao_mo_tc(d, wf->precision, walkers, W, ldw, v, nch, err_flag, wf->err_wf, st)
                     : x2 && d.oz ? launch_ao_mo_oz(d, walkers, W, ldw, v, nch, err_flag, wf->err_wf, st)
                     : x2         ? launch_ao_mo_x2(d, walkers, W, ldw, v, nch, st)
                                  : launch_ao_mo_simt(d, wf->precision, walkers, W, ldw, v, nch, st),
@@ -788,7 +796,7 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
 // gave up).
 static bool has_device_waits(const qmc_wf* wf) {
   return wf->precision == QMC_MIXED_TF32 || wf->precision == QMC_MIXED_BF16 ||
-         (wf->precision == QMC_FP32X2 && wf->dev.oz);
+         (wf->precision == QMC_FP32X2 && (wf->dev.oz || wf->dev.tc_value));
 }
 
 static qmc_status reset_status(const qmc_wf* wf, int* err_flag, cudaStream_t st) {

@@ -80,6 +80,7 @@ struct WfDev {
   const uint16_t* mo_oz;
   int oz_colexp[16];
   int oz;                  // 1: the FP32X2 form contracts on the tensor cores
+  int tc_value;            // 1: the FP32X2 form's Metropolis value path runs k_ao_mo_tc (FP32 AOs)
   const float* exp_tab;    // [64][2] 2^(j/64) as pairs: exp of the FP32X2 form
   const int* exc;          // [2][kMaxExc][5] rank, h1, h2, p1, p2
   const int* det_idx;      // [n_det][2] excitation index per spin
