@@ -44,13 +44,14 @@ __device__ __forceinline__ T mono(const T& x, const T& y, const T& z, int a, int
 
 // radial factor f, g1 = f'/rho, f2 = f'' of a shell (normalisation folded in)
 template <typename T>
-__device__ __forceinline__ void radial(const ShellDev& sh, const T& r2, const T& rho, T& f, T& g1, T& f2) {
+__device__ __forceinline__ void radial(const ShellDev& sh, const T& r2, const T& rho, T& f, T& g1, T& f2,
+                                       const T* irho = nullptr) {
   if (sh.kind == 0) {
     const double z = sh.expo[0];
     T rk = T(1.0);
     for (int k = 0; k < sh.kn; ++k) rk = rk * rho;
     f = sh.coef[0] * rk * exp(-z * rho);
-    const T inv = 1.0 / rho;
+    const T inv = irho ? *irho : 1.0 / rho;
     const T q = double(sh.kn) * inv - z;
     g1 = q * f * inv;
     f2 = (q * q - double(sh.kn) * inv * inv) * f;
@@ -88,10 +89,64 @@ struct GenShared {
 template <typename U, typename T, int NO>
 __device__ __forceinline__ void shell_channels(const WfDev& wf, const GenShared& g, const ShellDev& sh, const U& dx,
                                                const U& dy, const U& dz, const U& r2, const U& rho, const U& ir2,
-                                               int n_occ, T* phi, T (*dphi)[3], T (*hphi)[6], bool deriv) {
+                                               const U& irho, int n_occ, T* phi, T (*dphi)[3], T (*hphi)[6],
+                                               bool deriv) {
   U f, g1, f2;
-  radial(sh, r2, rho, f, g1, f2);
+  radial(sh, r2, rho, f, g1, f2, &irho);
   const U dv[3] = {dx, dy, dz};
+  auto add = [&](int b, const U& val, const U* grad, const U* hess) {
+    const double* Cb = g.C + (size_t)b * wf.n_mo;
+    for (int m = 0; m < NO; ++m) {
+      if (m < n_occ) {
+        const double c = Cb[m];
+        phi[m] += c * val;
+        if (deriv) {
+          for (int d = 0; d < 3; ++d) dphi[m][d] += c * grad[d];
+          for (int q = 0; q < 6; ++q) hphi[m][q] += c * hess[q];
+        }
+      }
+    }
+  };
+  if (sh.l <= 1) {
+    // closed forms: phi = f (s) or d_c f (p), with
+    //   grad_d (d_c f) = f delta_dc + d_c g1 d_d,
+    //   H_de f         = g1 delta_de + q d_d d_e,    q = (f2 - g1) / rho^2,
+    //   H_de (d_c f)   = g1 (delta_dc d_e + delta_ec d_d) + d_c H_de f
+    const U q = deriv ? (f2 - g1) * ir2 : U(0.0);
+    U hs[6], gs[3];
+    if (deriv) {
+      for (int d = 0; d < 3; ++d) gs[d] = g1 * dv[d];
+      hs[0] = g1 + q * dx * dx;
+      hs[1] = g1 + q * dy * dy;
+      hs[2] = g1 + q * dz * dz;
+      hs[3] = q * dx * dy;
+      hs[4] = q * dx * dz;
+      hs[5] = q * dy * dz;
+    }
+    for (int k = 0; k < sh.n_ao; ++k) {
+      const int b = sh.ao_first + k;
+      const int pw = g.pw[b];
+      if (sh.l == 0) {
+        add(b, f, gs, hs);
+        continue;
+      }
+      const int c = (pw & 15) ? 0 : ((pw >> 4) & 15) ? 1 : 2;
+      const U& x = dv[c];
+      U grad[3], hess[6];
+      if (deriv) {
+        for (int d = 0; d < 3; ++d) grad[d] = x * gs[d];
+        grad[c] += f;
+        for (int q2 = 0; q2 < 6; ++q2) hess[q2] = x * hs[q2];
+        // g1 (delta_dc d_e + delta_ec d_d): the diagonal element (c, c) gets
+        // 2 g1 d_c, the off-diagonal elements (c, e) get g1 d_e
+        hess[c] += 2.0 * gs[c];
+        for (int e = 0; e < 3; ++e)
+          if (e != c) hess[hidx(c, e)] += gs[e];
+      }
+      add(b, x * f, grad, hess);
+    }
+    return;
+  }
   for (int k = 0; k < sh.n_ao; ++k) {
     const int b = sh.ao_first + k;
     const int pw = g.pw[b];
@@ -144,8 +199,8 @@ __device__ void mo_channels(const WfDev& wf, const GenShared& g, const double p[
   }
   constexpr bool kDual = !std::is_same<T, double>::value;
   int cur_atom = -1;  // shells come grouped by atom: one displacement and distance per atom
-  T dx = T(0.0), dy = T(0.0), dz = T(0.0), r2 = T(0.0), rho = T(0.0), ir2 = T(0.0);
-  double xd = 0.0, yd = 0.0, zd = 0.0, r2d = 0.0, rhod = 0.0, ir2d = 0.0;
+  T dx = T(0.0), dy = T(0.0), dz = T(0.0), r2 = T(0.0), rho = T(0.0), ir2 = T(0.0), irho = T(0.0);
+  double xd = 0.0, yd = 0.0, zd = 0.0, r2d = 0.0, rhod = 0.0, ir2d = 0.0, irhod = 0.0;
   bool plain = !kDual;
   for (int s = 0; s < wf.n_shell; ++s) {
     const ShellDev& sh = g.sh[s];
@@ -158,20 +213,22 @@ __device__ void mo_channels(const WfDev& wf, const GenShared& g, const double p[
         zd = p[2] - value_of(R[cur_atom][2]);
         r2d = xd * xd + yd * yd + zd * zd;
         rhod = sqrt(r2d);
-        ir2d = 1.0 / r2d;
+        irhod = 1.0 / rhod;
+        ir2d = irhod * irhod;
       } else {
         dx = p[0] - R[cur_atom][0];
         dy = p[1] - R[cur_atom][1];
         dz = p[2] - R[cur_atom][2];
         r2 = dx * dx + dy * dy + dz * dz;
         rho = sqrt(r2);
-        ir2 = 1.0 / r2;
+        irho = 1.0 / rho;
+        ir2 = irho * irho;
       }
     }
     if (plain)
-      shell_channels<double, T, NO>(wf, g, sh, xd, yd, zd, r2d, rhod, ir2d, n_occ, phi, dphi, hphi, deriv);
+      shell_channels<double, T, NO>(wf, g, sh, xd, yd, zd, r2d, rhod, ir2d, irhod, n_occ, phi, dphi, hphi, deriv);
     else
-      shell_channels<T, T, NO>(wf, g, sh, dx, dy, dz, r2, rho, ir2, n_occ, phi, dphi, hphi, deriv);
+      shell_channels<T, T, NO>(wf, g, sh, dx, dy, dz, r2, rho, ir2, irho, n_occ, phi, dphi, hphi, deriv);
   }
 }
 
@@ -219,36 +276,83 @@ struct Pairs {
 
 template <int NE>
 __device__ void pair_geometry(const double (&r)[NE][3], int n, Pairs<NE>& P) {
+  for (int i = 0; i < NE; ++i) P.inv[i][i] = 0.0;
   for (int i = 0; i < NE; ++i)
-    for (int j = 0; j < NE; ++j) {
+    for (int j = i + 1; j < NE; ++j) {
       double v = 0.0;
-      if (i != j && i < n && j < n) {
+      if (i < n && j < n) {
         const double dx = r[i][0] - r[j][0], dy = r[i][1] - r[j][1], dz = r[i][2] - r[j][2];
         v = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
       }
       P.inv[i][j] = v;
+      P.inv[j][i] = v;
     }
 }
 
-// J1[i,.;k,e] and J2[i,.;k,e] (one row i, one coordinate (k, e))
+// The pair blocks of the backflow Jacobian, tabulated once per walker.  For
+// the ordered pair (a, b), v = r_a - r_b, eta = w / r, e1 = -w / r^3,
+// e2 = 3 w / r^5:
+//   G1_ab[d][e] = delta_de eta + e1 v_d v_e                (even in v: G1_ba = G1_ab)
+//   G2_ab[d][e] = 2 delta_de e1 v_e + e1 v_d + e2 v_d v_e^2  (odd in v:  G2_ba = -G2_ab)
+// and the rows of backflow_rows follow as
+//   i == k:  J1[i,d;i,e] = delta_de + sum_{j != i} G1_ij[d][e],  J2[i,d;i,e] = sum_{j != i} G2_ij[d][e]
+//   i != k:  J1[i,d;k,e] = -G1_ik[d][e],                          J2[i,d;k,e] = G2_ik[d][e].
+// G1 keeps its six distinct components (xx yy zz xy xz yz), G2 all nine;
+// pairs are stored once (a < b).
 template <int NE>
-__device__ void backflow_rows(const double (&r)[NE][3], const Pairs<NE>& P, int n, double w, int i, int k, int e,
-                              double j1[3], double j2[3]) {
-  for (int d = 0; d < 3; ++d) { j1[d] = (i == k && d == e) ? 1.0 : 0.0; j2[d] = 0.0; }
-  auto add = [&](int a, int b, double sgn_first, double sgn_second) {
-    const double iv = P.inv[a][b];
-    const double v[3] = {r[a][0] - r[b][0], r[a][1] - r[b][1], r[a][2] - r[b][2]};
-    const double eta = w * iv, e1 = -w * iv * iv * iv, e2 = 3.0 * w * iv * iv * iv * iv * iv;
-    for (int d = 0; d < 3; ++d) {
-      j1[d] += sgn_first * ((d == e ? eta : 0.0) + e1 * v[d] * v[e]);
-      j2[d] += sgn_second * ((d == e ? 2.0 * e1 * v[e] : 0.0) + e1 * v[d] + e2 * v[d] * v[e] * v[e]);
+struct BackflowTables {
+  static constexpr int kPairs = NE * (NE - 1) / 2;
+  double G1[kPairs][6], G2[kPairs][9];
+  double S1[NE][6], S2[NE][9];
+};
+
+__host__ __device__ constexpr int pair_index(int a, int b, int ne) { return a * ne - a * (a + 1) / 2 + (b - a - 1); }
+
+template <int NE>
+__device__ void backflow_tables(const double (&r)[NE][3], const Pairs<NE>& P, int n, double w, BackflowTables<NE>& T) {
+  for (int i = 0; i < NE; ++i) {
+    for (int q = 0; q < 6; ++q) T.S1[i][q] = 0.0;
+    for (int q = 0; q < 9; ++q) T.S2[i][q] = 0.0;
+  }
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b) {
+      const int pi = pair_index(a, b, NE);
+      const double iv = P.inv[a][b];
+      const double v[3] = {r[a][0] - r[b][0], r[a][1] - r[b][1], r[a][2] - r[b][2]};
+      const double iv2 = iv * iv, eta = w * iv, e1 = -w * iv * iv2, e2 = 3.0 * w * iv * iv2 * iv2;
+      for (int d = 0; d < 3; ++d)
+        for (int e = d; e < 3; ++e) {
+          const double g = (d == e ? eta : 0.0) + e1 * v[d] * v[e];
+          T.G1[pi][hidx(d, e)] = g;
+          T.S1[a][hidx(d, e)] += g;
+          T.S1[b][hidx(d, e)] += g;
+        }
+      for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e) {
+          const double g = (d == e ? 2.0 * e1 * v[e] : 0.0) + e1 * v[d] + e2 * v[d] * v[e] * v[e];
+          T.G2[pi][3 * d + e] = g;
+          T.S2[a][3 * d + e] += g;
+          T.S2[b][3 * d + e] -= g;
+        }
     }
-  };
+}
+
+// J1[i,.;k,e] and J2[i,.;k,e] from the tables
+template <int NE>
+__device__ __forceinline__ void backflow_rows_t(const BackflowTables<NE>& T, int i, int k, int e, double j1[3],
+                                                double j2[3]) {
   if (i == k) {
-    for (int j = 0; j < n; ++j)
-      if (j != i) add(i, j, 1.0, 1.0);
+    for (int d = 0; d < 3; ++d) {
+      j1[d] = (d == e ? 1.0 : 0.0) + T.S1[i][hidx(d, e)];
+      j2[d] = T.S2[i][3 * d + e];
+    }
   } else {
-    add(i, k, -1.0, 1.0);
+    const int pi = i < k ? pair_index(i, k, NE) : pair_index(k, i, NE);
+    const double sg = i < k ? 1.0 : -1.0;  // G2_ik = -G2_ki
+    for (int d = 0; d < 3; ++d) {
+      j1[d] = -T.G1[pi][hidx(d, e)];
+      j2[d] = sg * T.G2[pi][3 * d + e];
+    }
   }
 }
 
@@ -463,6 +567,8 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
   backflow_positions<NE>(r, P, N, w, rt);
   // orbitals at the backflow positions
   const int n_occ = nu > wf.n_down ? nu : wf.n_down;
+  BackflowTables<NE> BT;
+  if (kinetic && w != 0.0) backflow_tables<NE>(r, P, N, w, BT);
   T phi[NE][NO], dphi[NE][NO][3], hphi[NE][NO][6];
   for (int i = 0; i < N; ++i)
     mo_channels<T, NO>(wf, g, rt[i], R, n_occ, phi[i], dphi[i], hphi[i], kinetic, seeded);
@@ -479,6 +585,23 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
   }
   logpsi = J + logdet;
   if (!kinetic) return;
+  // Tr(A^-1 d_k^2 A) = sum_a [sum_q cq_a(k) Hc[a][q] + sum_d J2_a(k)_d Gc[a][d]] with
+  // the orbital gradients and Hessians of each row contracted with A^-1 once
+  // per walker: Gc[i][d] = sum_m (A^-1)_{m a} d_d phi_m(r~_i), Hc likewise
+  T Gc[NE][3], Hc[NE][6];
+  for (int i = 0; i < N; ++i) {
+    const int s = i < nu ? 0 : 1, n = s == 0 ? nu : wf.n_down, a = s == 0 ? i : i - nu;
+    for (int d = 0; d < 3; ++d) {
+      T acc = T(0.0);
+      for (int m = 0; m < n; ++m) acc += ainv[s][m][a] * dphi[i][m][d];
+      Gc[i][d] = acc;
+    }
+    for (int q = 0; q < 6; ++q) {
+      T acc = T(0.0);
+      for (int m = 0; m < n; ++m) acc += ainv[s][m][a] * hphi[i][m][q];
+      Hc[i][q] = acc;
+    }
+  }
   T kin = T(lapJ);
   for (int kk = 0; kk < N; ++kk) {
     const int sk = kk < nu ? 0 : 1;
@@ -487,36 +610,39 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
       for (int s = 0; s < 2; ++s) {
         const int n = s == 0 ? nu : wf.n_down, i0 = s == 0 ? 0 : nu;
         if (n == 0 || (w == 0.0 && s != sk)) continue;
-        T dA[NO][NO], d2A[NO][NO];
+        T dA[NO][NO];
+        T tr2 = T(0.0);
         for (int a = 0; a < n; ++a) {
           const int i = i0 + a;
           if (w == 0.0 && i != kk) {
-            for (int m = 0; m < n; ++m) { dA[a][m] = T(0.0); d2A[a][m] = T(0.0); }
+            for (int m = 0; m < n; ++m) dA[a][m] = T(0.0);
             continue;
           }
           double j1[3], j2[3];
-          backflow_rows<NE>(r, P, N, w, i, kk, e, j1, j2);
+          if (w != 0.0) {
+            backflow_rows_t<NE>(BT, i, kk, e, j1, j2);
+          } else {  // no backflow: only the moving electron's own row, J1 = unit, J2 = 0
+            for (int d = 0; d < 3; ++d) { j1[d] = d == e ? 1.0 : 0.0; j2[d] = 0.0; }
+          }
+          // sum_{d,f} j1_d j1_f H_df = sum_q cq[q] H_q over the six distinct
+          // Hessian components (xx yy zz xy xz yz)
+          const double cq[6] = {j1[0] * j1[0], j1[1] * j1[1], j1[2] * j1[2],
+                                2.0 * j1[0] * j1[1], 2.0 * j1[0] * j1[2], 2.0 * j1[1] * j1[2]};
+          for (int q = 0; q < 6; ++q) tr2 += cq[q] * Hc[i][q];
+          for (int d = 0; d < 3; ++d) tr2 += j2[d] * Gc[i][d];
           for (int m = 0; m < n; ++m) {
-            T v1 = T(0.0), v2 = T(0.0);
-            for (int d = 0; d < 3; ++d) {
-              v1 += j1[d] * dphi[i][m][d];
-              v2 += j2[d] * dphi[i][m][d];
-              for (int f = 0; f < 3; ++f) v2 += (j1[d] * j1[f]) * hphi[i][m][hidx(d, f)];
-            }
+            T v1 = T(0.0);
+            for (int d = 0; d < 3; ++d) v1 += j1[d] * dphi[i][m][d];
             dA[a][m] = v1;
-            d2A[a][m] = v2;
           }
         }
         T X1[NO][NO];
-        T tr2 = T(0.0);
         for (int m = 0; m < n; ++m)
           for (int q = 0; q < n; ++q) {
             T acc = T(0.0);
             for (int a = 0; a < n; ++a) acc += ainv[s][m][a] * dA[a][q];
             X1[m][q] = acc;
           }
-        for (int m = 0; m < n; ++m)
-          for (int a = 0; a < n; ++a) tr2 += ainv[s][m][a] * d2A[a][m];
         T tr1 = T(0.0), trsq = T(0.0);
         for (int m = 0; m < n; ++m) {
           tr1 += X1[m][m];
@@ -562,6 +688,8 @@ __device__ void eval_walker_md(const WfDev& wf, const GenShared& g, const double
   double J, lapJ, gJ[NE][3], rt[NE][3], V;
   jastrow_coulomb<double, NE>(wf, r, wf.atom_xyz, P, J, lapJ, gJ, V);
   backflow_positions<NE>(r, P, N, w, rt);
+  BackflowTables<NE> BT;
+  if (kinetic) backflow_tables<NE>(r, P, N, w, BT);
   const int ncol = wf.p_hi[0] > wf.p_hi[1] ? wf.p_hi[0] : wf.p_hi[1];
   double phi[NE][NC], dphi[NE][NC][3], hphi[NE][NC][6];
   for (int i = 0; i < N; ++i) mo_channels<double, NC>(wf, g, rt[i], wf.atom_xyz, ncol, phi[i], dphi[i], hphi[i], kinetic);
@@ -606,14 +734,16 @@ __device__ void eval_walker_md(const WfDev& wf, const GenShared& g, const double
         for (int a = 0; a < n; ++a) {
           const int i = i0 + a;
           double j1[3], j2[3];
-          backflow_rows<NE>(r, P, N, w, i, kk, e, j1, j2);
+          backflow_rows_t<NE>(BT, i, kk, e, j1, j2);
+          const double cq[6] = {j1[0] * j1[0], j1[1] * j1[1], j1[2] * j1[2],
+                                2.0 * j1[0] * j1[1], 2.0 * j1[0] * j1[2], 2.0 * j1[1] * j1[2]};
           for (int c = 0; c < wf.p_hi[s]; ++c) {
             double v1 = 0.0, v2 = 0.0;
             for (int dd = 0; dd < 3; ++dd) {
               v1 += j1[dd] * dphi[i][c][dd];
               v2 += j2[dd] * dphi[i][c][dd];
-              for (int f = 0; f < 3; ++f) v2 += (j1[dd] * j1[f]) * hphi[i][c][hidx(dd, f)];
             }
+            for (int q = 0; q < 6; ++q) v2 += cq[q] * hphi[i][c][q];
             dA[a][c] = v1;
             d2A[a][c] = v2;
           }

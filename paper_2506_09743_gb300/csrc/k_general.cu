@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(128) k_eloc_md(WfDev wf, const double* __restr
 }
 
 template <int NE, int NO>
-__global__ void __launch_bounds__(128) k_eloc_general(WfDev wf, const double* __restrict__ walkers, int64_t W,
+__global__ void __launch_bounds__(128, 4) k_eloc_general(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                       int64_t ldw, bool kinetic, double* __restrict__ e_loc,
                                                       double* __restrict__ log_psi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
