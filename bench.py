@@ -103,6 +103,22 @@ def x2_stage_ops(mol) -> float:
     return float(mol.n_elec * per_row)
 
 
+def oz_stage_alu_ops(mol) -> float:
+    """Algorithmic FP32/ALU operations per walker of k_ao_mo_oz, the FP32X2
+    AO stage with the contraction on the tensor cores: the AO evaluation of
+    x2_stage_ops (everything but its multiply-accumulates), per AO value and
+    channel the digit slicing (oz_digits: 26 FP32 operations, 2 for the row
+    scale, 6 BF16 packs), per MO and channel the recombination of the six
+    classes (oz_combine: 44).  The contraction itself runs on the tensor
+    pipe (BF16 digit products, exact FP32 sums) and is not counted here;
+    row-scale bounds, addressing and stores are not counted either."""
+    o = X2_OPS
+    contraction = 2 * mol.n_ao * mol.n_mo * o["mac"]
+    ao_eval = x2_stage_ops(mol) / mol.n_elec - contraction
+    per_row = ao_eval + 2 * mol.n_ao * (26 + 2 + 6) + 2 * mol.n_mo * 44
+    return float(mol.n_elec * per_row)
+
+
 # GB300 issue rates from the unit counts and the maximum SM clock (152 SMs,
 # 2.07 GHz): FP32 128 lanes per SM; FP64 2 FMA lanes per SM (4 flop/clk)
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12  # 40.3 T FP32 operations/s
@@ -449,6 +465,47 @@ def rank_walker_seed(rank: int) -> int:
     return qi.SEED_WALKERS + rank
 
 
+PROFILE_CASES = ("co_fp32x2", "co_mixed_tf32", "co_fp64", "li2_eloc", "li2_energy_grad", "li2_sample")
+
+
+def run_only(case: str, W: int, steps: int, warmup: int, device: int = 0) -> dict:
+    """One workload alone (the small cases the ncu captures run): `warmup`
+    untimed calls, then `steps` calls timed with CUDA events.  CO cases time
+    qmc_local_energy in the named form; li2_eloc the backflow E_L (FP64),
+    li2_energy_grad qmc_energy_grad, li2_sample ten Metropolis steps."""
+    import torch
+
+    from paper_2506_09743_gb300 import Wavefunction
+
+    mol = qi.make_co() if case.startswith("co_") else qi.make_li2()
+    form = case[3:] if case.startswith("co_") else "fp64"
+    x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
+    wf = Wavefunction(mol, precision=form, device=device)
+    e = torch.empty(W, dtype=torch.float64, device="cuda")
+
+    def call():
+        if case == "li2_energy_grad":
+            wf.energy_grad(x)
+        elif case == "li2_sample":
+            wf.sample(x, n_steps=10, step=0.05, seed=0x5EED)
+        else:
+            wf.local_energy(x, e_loc=e, want_log_psi=False)
+
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        call()
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    wf.close()
+    return {"case": case, "walkers": W, "steps": steps, "ms_per_call": ms}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -464,6 +521,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the other molecules' measurements")
     ap.add_argument("--manybody-jastrow", action="store_true",
                     help="time CO with the many-body Jastrow of App. D (K_en + 5 K_een terms) instead")
+    ap.add_argument("--only", choices=PROFILE_CASES,
+                    help="run one workload alone and print its time per call (the cases the ncu captures use)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -482,6 +541,9 @@ def main():
     from paper_2506_09743_gb300 import Wavefunction
 
     torch.cuda.set_device(local)
+    if args.only:
+        print(json.dumps(run_only(args.only, args.walkers, args.steps, args.warmup, local)), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -607,18 +669,26 @@ def main():
                 "note": "against the FP64 form on the same walkers; the walkers beyond 2e-4 Ha are at nodes "
                         "(|E| of 1e4..1e7 Ha), outside the parity tests' conditioning cut"}
 
-    # rooflines: FP32-issue-bound AO stages, FP64-pipe-bound determinant stage
-    x2_ops = x2_stage_ops(mol) * W
+    # rooflines: the FP32X2 AO stage (k_ao_mo_oz) is bound by FP32/ALU issue
+    # (its contraction runs on the tensor pipe), the determinant stage by the
+    # FP64 pipe
+    oz_ops = oz_stage_alu_ops(mol) * W
     x2_ms = float(stage_x2[1])
-    x2_rate = x2_ops / (x2_ms / 1e3) / 1e12
+    oz_rate = oz_ops / (x2_ms / 1e3) / 1e12
+    x2_equiv = x2_stage_ops(mol) * W / (x2_ms / 1e3) / 1e12
     flops_det = det_stage_flops(mol) * W
     det_ms = float(stage_x2[2])
     det_rate = flops_det / (det_ms / 1e3) / 1e12
-    roofline = {"kernel": "k_ao_mo_x2 (AOs + AO->MO contraction in pairs of FP32; FP32X2 form)", "bound": "alu",
-                "achieved": x2_rate, "peak": FP32_PEAK_TOPS, "unit": "T FP32 ops/s", "frac": x2_rate / FP32_PEAK_TOPS,
-                "traffic": None,
+    roofline = {"kernel": "k_ao_mo_oz (AOs in pairs of FP32, exact digit-sliced contraction on tcgen05; FP32X2 form)",
+                "bound": "alu", "achieved": oz_rate, "peak": FP32_PEAK_TOPS, "unit": "T FP32 ops/s",
+                "frac": oz_rate / FP32_PEAK_TOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (no measured FP32 peak on this pool)",
-                "ops_per_launch": x2_ops, "ops_model": "bench.x2_stage_ops (pair-arithmetic operation counts)",
+                "ops_per_launch": oz_ops,
+                "ops_model": "bench.oz_stage_alu_ops: AO evaluation in pair arithmetic + digit slicing + class "
+                             "recombination; the contraction runs on the tensor pipe",
+                "simt_equivalent_tops": x2_equiv,
+                "simt_equivalent_note": "the whole stage (bench.x2_stage_ops, contraction as pair multiply-"
+                                        "accumulates) per second: what the SIMT pair kernel would have to issue",
                 "kernel_ms": x2_ms}
     rooflines = {
         "k_det": {"bound": "alu", "achieved": det_rate, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
@@ -632,7 +702,7 @@ def main():
     }
     # whole step: the FP32X2 step cannot beat its AO stage at the FP32 issue
     # rate plus its determinant stage at the FP64 rate (the two run in turn)
-    bound_ms = x2_ops / (FP32_PEAK_TOPS * 1e12) * 1e3 + flops_det / (FP64_PEAK_TFLOPS * 1e12) * 1e3
+    bound_ms = oz_ops / (FP32_PEAK_TOPS * 1e12) * 1e3 + flops_det / (FP64_PEAK_TFLOPS * 1e12) * 1e3
     whole_step = {"ms_per_step": ms_step, "bound_ms": bound_ms, "frac": bound_ms / ms_step,
                   "note": "AO stage at the FP32 issue rate + determinant stage at the FP64 rate, in sequence"}
     line = {
@@ -644,7 +714,7 @@ def main():
                    "walkers_per_gpu": W, "precision": "fp32x2",
                    "l2": "flushed (256 MB write) between timed steps, outside the timed events",
                    "parallelism": f"walker shards x{world}, no data-path collective"},
-        "stage_ms": {"jastrow_coulomb": float(stage_x2[0]), "ao_mo_x2": float(stage_x2[1]),
+        "stage_ms": {"jastrow_coulomb": float(stage_x2[0]), "ao_mo_oz": float(stage_x2[1]),
                      "det_eloc": float(stage_x2[2])},
         "finite_frac": fin_x2,
         "accuracy": accuracy(e_x2),

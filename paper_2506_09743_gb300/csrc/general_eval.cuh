@@ -585,21 +585,28 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
   }
   logpsi = J + logdet;
   if (!kinetic) return;
-  // Tr(A^-1 d_k^2 A) = sum_a [sum_q cq_a(k) Hc[a][q] + sum_d J2_a(k)_d Gc[a][d]] with
-  // the orbital gradients and Hessians of each row contracted with A^-1 once
-  // per walker: Gc[i][d] = sum_m (A^-1)_{m a} d_d phi_m(r~_i), Hc likewise
-  T Gc[NE][3], Hc[NE][6];
-  for (int i = 0; i < N; ++i) {
-    const int s = i < nu ? 0 : 1, n = s == 0 ? nu : wf.n_down, a = s == 0 ? i : i - nu;
-    for (int d = 0; d < 3; ++d) {
-      T acc = T(0.0);
-      for (int m = 0; m < n; ++m) acc += ainv[s][m][a] * dphi[i][m][d];
-      Gc[i][d] = acc;
-    }
-    for (int q = 0; q < 6; ++q) {
-      T acc = T(0.0);
-      for (int m = 0; m < n; ++m) acc += ainv[s][m][a] * hphi[i][m][q];
-      Hc[i][q] = acc;
+  // Per spin, the orbital gradients and Hessians of each row contracted with
+  // A^-1 once per walker:
+  //   M_d[a][b] = sum_m d_d phi_m(r~_{i_a}) (A^-1)_{m b},   Hc[i_a][q] = sum_m (A^-1)_{m a} H_q phi_m(r~_{i_a}).
+  // Per coordinate x_k, with Y = (d_k A) A^-1, Y[a][b] = sum_d J1_a(k)_d M_d[a][b]:
+  //   Tr(A^-1 d_k A) = Tr Y,  Tr((A^-1 d_k A)^2) = Tr(Y^2),
+  //   Tr(A^-1 d_k^2 A) = sum_a [sum_q cq_a(k) Hc[i_a][q] + sum_d J2_a(k)_d M_d[a][a]].
+  T Md[2][3][NO][NO], Hc[NE][6];
+  for (int s = 0; s < 2; ++s) {
+    const int n = s == 0 ? nu : wf.n_down, i0 = s == 0 ? 0 : nu;
+    for (int a = 0; a < n; ++a) {
+      const int i = i0 + a;
+      for (int d = 0; d < 3; ++d)
+        for (int b = 0; b < n; ++b) {
+          T acc = T(0.0);
+          for (int m = 0; m < n; ++m) acc += dphi[i][m][d] * ainv[s][m][b];
+          Md[s][d][a][b] = acc;
+        }
+      for (int q = 0; q < 6; ++q) {
+        T acc = T(0.0);
+        for (int m = 0; m < n; ++m) acc += ainv[s][m][a] * hphi[i][m][q];
+        Hc[i][q] = acc;
+      }
     }
   }
   T kin = T(lapJ);
@@ -610,12 +617,12 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
       for (int s = 0; s < 2; ++s) {
         const int n = s == 0 ? nu : wf.n_down, i0 = s == 0 ? 0 : nu;
         if (n == 0 || (w == 0.0 && s != sk)) continue;
-        T dA[NO][NO];
+        T Y[NO][NO];
         T tr2 = T(0.0);
         for (int a = 0; a < n; ++a) {
           const int i = i0 + a;
           if (w == 0.0 && i != kk) {
-            for (int m = 0; m < n; ++m) dA[a][m] = T(0.0);
+            for (int b = 0; b < n; ++b) Y[a][b] = T(0.0);
             continue;
           }
           double j1[3], j2[3];
@@ -629,24 +636,17 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
           const double cq[6] = {j1[0] * j1[0], j1[1] * j1[1], j1[2] * j1[2],
                                 2.0 * j1[0] * j1[1], 2.0 * j1[0] * j1[2], 2.0 * j1[1] * j1[2]};
           for (int q = 0; q < 6; ++q) tr2 += cq[q] * Hc[i][q];
-          for (int d = 0; d < 3; ++d) tr2 += j2[d] * Gc[i][d];
-          for (int m = 0; m < n; ++m) {
+          for (int d = 0; d < 3; ++d) tr2 += j2[d] * Md[s][d][a][a];
+          for (int b = 0; b < n; ++b) {
             T v1 = T(0.0);
-            for (int d = 0; d < 3; ++d) v1 += j1[d] * dphi[i][m][d];
-            dA[a][m] = v1;
+            for (int d = 0; d < 3; ++d) v1 += j1[d] * Md[s][d][a][b];
+            Y[a][b] = v1;
           }
         }
-        T X1[NO][NO];
-        for (int m = 0; m < n; ++m)
-          for (int q = 0; q < n; ++q) {
-            T acc = T(0.0);
-            for (int a = 0; a < n; ++a) acc += ainv[s][m][a] * dA[a][q];
-            X1[m][q] = acc;
-          }
         T tr1 = T(0.0), trsq = T(0.0);
-        for (int m = 0; m < n; ++m) {
-          tr1 += X1[m][m];
-          for (int q = 0; q < n; ++q) trsq += X1[m][q] * X1[q][m];
+        for (int a = 0; a < n; ++a) {
+          tr1 += Y[a][a];
+          for (int b = 0; b < n; ++b) trsq += Y[a][b] * Y[b][a];
         }
         a_s[s] = tr1;
         b_s[s] = tr2 + tr1 * tr1 - trsq;
