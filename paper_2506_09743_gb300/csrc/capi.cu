@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <string>
@@ -167,6 +168,82 @@ int tc_canonical_index(int l, int a, int b, int c) {
   if (a == 1) return b ? 1 : 2;
   if (b == 2) return 3;
   return b ? 4 : 5;
+}
+
+// Row-scale tables of the FP32X2 tensor-core AO stage: for every atom and
+// bin [r_lo^2, r_hi^2] of the squared electron-nucleus distance, upper bounds
+// over the AOs of the atom's shells of |AO value| (bv) and of the kinetic
+// channel, |lap phi + 2 grad J . grad phi| <= bk0 + |grad J| bk1.  Per shell
+// (radial sums at rho_lo, powers of rho at rho_hi, the terms of the bound
+// the kernel's shells would give one by one):
+//   R0 >= sum |c| e^(-a rho^2), R1 >= |f'/rho|, R2 >= |f''|,
+//   bv  = R0 rho^l,
+//   bk0 = R0 l (l - 1) rho^(l-2) + rho^l (R2 + 2 (l + 1) R1),
+//   bk1 = 2 R1 rho^(l+1) + 2 R0 l rho^(l-1).
+// The last bin (rho >= 256) takes rho_lo for every factor, valid once each
+// radial factor times rho^(l+2) decreases beyond 256 bohr (checked: else no
+// table).  Bins are widened by 1e-6 on both sides and the bounds rounded up,
+// so FP32 rounding of r^2 on the device cannot leave a bin's bound.
+bool oz_bound_table(const std::vector<ShellDev>& shells, int n_atom, std::vector<float>& tab) {
+  for (const ShellDev& sh : shells) {
+    if (sh.kind == 0) {
+      if (sh.expo[0] * 256.0 < sh.kn + sh.l + 3) return false;
+    } else {
+      for (int p = 0; p < sh.n_prim; ++p)
+        if (2.0 * sh.expo[p] * 65536.0 < sh.l + 3) return false;
+    }
+  }
+  std::vector<double> acc((size_t)n_atom * kOzBoundBins * 3, 0.0);
+  for (int k = 1; k < kOzBoundBins; ++k) {
+    double rlo, rhi;
+    if (k == kOzBoundBins - 1) {
+      rlo = 256.0 * (1.0 - 1e-6);
+      rhi = rlo;
+    } else {
+      const uint32_t u0 = (uint32_t)(k - 1 + kOzBoundBase) << 19, u1 = (uint32_t)(k + kOzBoundBase) << 19;
+      float f0, f1;
+      std::memcpy(&f0, &u0, 4);
+      std::memcpy(&f1, &u1, 4);
+      rlo = std::sqrt((double)f0) * (1.0 - 1e-6);
+      rhi = std::sqrt((double)f1) * (1.0 + 1e-6);
+    }
+    for (const ShellDev& sh : shells) {
+      double R0 = 0.0, R1 = 0.0, R2 = 0.0;
+      if (sh.kind == 0) {
+        const double F = std::fabs(sh.coef[0]) * std::pow(rhi, sh.kn) * std::exp(-sh.expo[0] * rlo);
+        const double Q = sh.kn / rlo + sh.expo[0];
+        R0 = F;
+        R1 = Q * F / rlo;
+        R2 = (Q * Q + sh.kn / (rlo * rlo)) * F;
+      } else {
+        for (int p = 0; p < sh.n_prim; ++p) {
+          const double a = sh.expo[p], ce = std::fabs(sh.coef[p]) * std::exp(-a * rlo * rlo);
+          R0 += ce;
+          R1 += 2.0 * a * ce;
+          R2 += (4.0 * a * a * rhi * rhi + 2.0 * a) * ce;
+        }
+      }
+      const int l = sh.l;
+      const double rl = std::pow(rhi, l), rl1 = l >= 1 ? std::pow(rhi, l - 1) : 0.0,
+                   rl2 = l >= 2 ? std::pow(rhi, l - 2) : 0.0;
+      const double bv = R0 * rl;
+      const double bk0 = R0 * l * (l - 1) * rl2 + rl * (R2 + 2.0 * (l + 1) * R1);
+      const double bk1 = 2.0 * R1 * rhi * rl + 2.0 * R0 * l * rl1;
+      double* t = &acc[((size_t)sh.atom * kOzBoundBins + k) * 3];
+      t[0] = std::max(t[0], bv);
+      t[1] = std::max(t[1], bk0);
+      t[2] = std::max(t[2], bk1);
+    }
+  }
+  tab.assign((size_t)n_atom * kOzBoundBins * 4, 0.0f);
+  for (size_t i = 0; i < (size_t)n_atom * kOzBoundBins; ++i)
+    for (int c = 0; c < 3; ++c) {
+      const double v = acc[i * 3 + c] * (1.0 + 1e-6);
+      float f = (float)v;
+      if ((double)f < v) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+      tab[i * 4 + c] = f;
+    }
+  return true;
 }
 
 qmc_status launch_status(cudaError_t e, const char* where) {
@@ -372,7 +449,10 @@ qmc_status build_tables(qmc_wf* wf) {
       std::vector<int> by_cost;
       for (int s = 0; s < d.n_shell; ++s)
         if (shell_pass[s] == p) by_cost.push_back(s);
-      auto cost = [&](int s) { return 3 * shells[s].n_prim + 4 * shells[s].n_ao + 2; };
+      // issue cost of a shell in the pair kernels: ~140 FP32 operations per
+      // primitive (exponential, radial sums), ~100 per AO (angular factor,
+      // kinetic channel, digits of both channels), ~40 per shell
+      auto cost = [&](int s) { return 14 * shells[s].n_prim + 10 * shells[s].n_ao + 4; };
       std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return cost(a) > cost(b); });
       std::vector<std::vector<int>> part(4);
       int load[4] = {0, 0, 0, 0};
@@ -537,6 +617,8 @@ qmc_status build_tables(qmc_wf* wf) {
     }
     d.oz = 1;  // confirmed by oz_supported below, once the other tables are known
   }
+  std::vector<float> oz_bnd;
+  const bool have_bnd = d.oz && oz_bound_table(shells, d.n_atom, oz_bnd);
 
   // ---- upload everything in one blob
   DeviceGuard guard(wf->device);
@@ -549,7 +631,7 @@ qmc_status build_tables(qmc_wf* wf) {
       {h.prim_start.data(), sizeof(int) * (nao + 1)}, {ao_col.data(), sizeof(int) * nao},
       {tc_shells.data(), sizeof(int) * tc_shells.size()}, {det_tab.data(), sizeof(int) * det_tab.size()},
       {mo_x2.data(), sizeof(float) * mo_x2.size()},      {exp_tab.data(), sizeof(float) * exp_tab.size()},
-      {mo_oz.data(), sizeof(uint16_t) * mo_oz.size()}};
+      {mo_oz.data(), sizeof(uint16_t) * mo_oz.size()},  {oz_bnd.data(), sizeof(float) * oz_bnd.size()}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
   void* blob = nullptr;
@@ -588,6 +670,7 @@ qmc_status build_tables(qmc_wf* wf) {
   d.mo_x2 = reinterpret_cast<const float2*>(ptr[14]);
   d.exp_tab = reinterpret_cast<const float*>(ptr[15]);
   d.mo_oz = reinterpret_cast<const uint16_t*>(ptr[16]);
+  d.oz_bound = have_bnd ? reinterpret_cast<const float4*>(ptr[17]) : nullptr;
   if (d.oz && !oz_supported(d)) d.oz = 0;  // the SIMT pair kernel serves this wavefunction
   // the previous tables may still be read by work in flight on any stream
   if (wf->blob) {

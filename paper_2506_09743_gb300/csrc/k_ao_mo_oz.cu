@@ -115,6 +115,18 @@ __device__ __forceinline__ double widen_scaled(float f, int k) {
   return __longlong_as_double(__double_as_longlong(d) + ((long long)k << 52));
 }
 
+// The same for a normal float f when f 2^k is a normal double (always so in
+// the epilogue: f is zero or a multiple of 2^-40 below 2^25, |k| < 300): the
+// FP64 bit pattern is assembled by integer operations, so the epilogue
+// spends one FP64 instruction (the final add) per output instead of five.
+__device__ __forceinline__ double widen_scaled_int(float f, int k) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e32 = (u >> 23) & 0xffu;
+  if (e32 == 0u || e32 == 0xffu) return widen_scaled(f, k);  // zero, subnormal, inf, NaN
+  const uint32_t hi = (u & 0x80000000u) | ((e32 + 896u + (uint32_t)k) << 20) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // FP32 upper bounds of |AO value| and |kinetic value| over the AOs of a shell
 // at distance rho (r2 = rho^2) with |grad J| = gn
 __device__ __forceinline__ void shell_bounds(const ShellDev& sh, float r2, float rho, float irho, float gn,
@@ -168,8 +180,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
   int* col_s = pow_s + wf.n_ao;                                       // [n_ao]
   int* list_s = col_s + wf.n_ao;                                      // [n_shell]
   unsigned* rowb = reinterpret_cast<unsigned*>(pow_s + oz_int_words(wf));  // [2][128] bound bits
-  int* rowe = reinterpret_cast<int*>(rowb + 2 * kRows);              // [2][128] scale exponents
-  int* colf = rowe + 2 * kRows;                                       // [16] MO column exponents
+  int* rowe_buf = reinterpret_cast<int*>(rowb + 2 * kRows);          // [2 tiles][2][128] scale exponents
+  int* colf = rowe_buf + 4 * kRows;                                   // [16] MO column exponents
   uint64_t* mbar = reinterpret_cast<uint64_t*>(colf + kNPad);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
 
@@ -208,29 +220,89 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
   const uint32_t lbo = 128, sbo_a = 512, sbo_b = (uint32_t)(kp / 8) * 128;
   const int64_t n_wblk = (W + kRows - 1) / kRows;
   const int64_t n_tiles = n_wblk * wf.n_elec;
-  uint32_t commits = 0;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  uint32_t commits = 0, iter = 0;
+  // a row's electron position and Jastrow gradient, fetched one tile ahead
+  // (the loads of the next tile are in flight during this tile's epilogue)
+  double nrx, nry, nrz;
+  float ngx, ngy, ngz;
+  auto fetch = [&](int64_t t) {
+    nrx = nry = nrz = 0.0;
+    ngx = ngy = ngz = 0.f;
+    if (t >= n_tiles) return;
+    const int ti = (int)(t % wf.n_elec);
+    const int64_t tw = (t / wf.n_elec) * kRows + row;
+    if (tw >= W) return;
+    nrx = walkers[(int64_t)(3 * ti) * ldw + tw];
+    nry = walkers[(int64_t)(3 * ti + 1) * ldw + tw];
+    nrz = walkers[(int64_t)(3 * ti + 2) * ldw + tw];
+    if (NCH == 2) {
+      ngx = gradJ[(int64_t)(3 * ti) * ldm + tw];
+      ngy = gradJ[(int64_t)(3 * ti + 1) * ldm + tw];
+      ngz = gradJ[(int64_t)(3 * ti + 2) * ldm + tw];
+    }
+  };
+  fetch(blockIdx.x);
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
+    // scale exponents of this tile's rows: written before its passes, read by
+    // its epilogue; alternate buffers, so that the next tile may write its
+    // own while this epilogue still reads (the pass barrier of the tile after
+    // next orders the reuse)
+    int* rowe = rowe_buf + (iter & 1u) * 2 * kRows;
     const int i = (int)(tile % wf.n_elec);
     const int64_t wb = tile / wf.n_elec;
-    const int64_t w = wb * kRows + row;
-    const bool live = w < W;
-    double rx = 0.0, ry = 0.0, rz = 0.0;
-    float gjx = 0.f, gjy = 0.f, gjz = 0.f;
-    if (live) {
-      rx = walkers[(int64_t)(3 * i) * ldw + w];
-      ry = walkers[(int64_t)(3 * i + 1) * ldw + w];
-      rz = walkers[(int64_t)(3 * i + 2) * ldw + w];
-      if (NCH == 2) {
-        gjx = gradJ[(int64_t)(3 * i) * ldm + w];
-        gjy = gradJ[(int64_t)(3 * i + 1) * ldm + w];
-        gjz = gradJ[(int64_t)(3 * i + 2) * ldm + w];
+    const double rx = nrx, ry = nry, rz = nrz;
+    const float gjx = ngx, gjy = ngy, gjz = ngz;
+    // ---- 1. row scales from FP32 upper bounds of every AO of the row
+    const float gn = NCH == 2 ? sqrtf(gjx * gjx + gjy * gjy + gjz * gjz) : 0.f;
+    int e0 = 0, e1 = 0;
+    if (wf.oz_bound != nullptr) {
+      // per-atom tables of bounds over bins of r^2: each thread reads its
+      // row's bins (no reduction across the row's four parts, no barrier);
+      // an electron within 2^-12 bohr of a nucleus falls back to the shells
+      float bv = 0.f, bk = 0.f;
+      bool direct = false;
+      for (int a = 0; a < wf.n_atom; ++a) {
+        float dx, dy, dz;
+        displacement(rx, ry, rz, wf.atom_xyz[a], dx, dy, dz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const int idx = oz_bound_bin(r2);
+        if (idx == 0) {
+          direct = true;
+          continue;
+        }
+        const float4 t = __ldg(wf.oz_bound + (size_t)a * kOzBoundBins + idx);
+        bv = fmaxf(bv, t.x);
+        bk = fmaxf(bk, fmaf(gn, t.z, t.y));
       }
-    }
-    // ---- 1. row scales from FP32 bounds of every AO of the row
-    if (tid < 2 * kRows) rowb[tid] = 0u;
-    __syncthreads();
-    {
-      const float gn = sqrtf(gjx * gjx + gjy * gjy + gjz * gjz);
+      if (direct) {
+        int cur_atom = -1;
+        float r2 = 0.f, rho = 0.f, irho = 0.f;
+        for (int q = 0; q < wf.n_shell; ++q) {
+          const ShellDev& sh = sh_s[q];
+          if (sh.atom != cur_atom) {
+            cur_atom = sh.atom;
+            float dx, dy, dz;
+            displacement(rx, ry, rz, wf.atom_xyz[cur_atom], dx, dy, dz);
+            r2 = dx * dx + dy * dy + dz * dz;
+            irho = rsqrtf(r2);
+            rho = r2 * irho;
+          }
+          float sv, sk;
+          shell_bounds(sh, r2, rho, irho, gn, sv, sk);
+          bv = fmaxf(bv, sv);
+          bk = fmaxf(bk, sk);
+        }
+      }
+      e0 = scale_exponent(__float_as_uint(bv));
+      e1 = scale_exponent(__float_as_uint(bk));
+      if (part == 0) {
+        rowe[row] = e0;
+        rowe[kRows + row] = e1;
+      }
+    } else {
+      // the four parts of a row bound their own shells and meet in shared memory
+      if (tid < 2 * kRows) rowb[tid] = 0u;
+      __syncthreads();
       float bv = 0.f, bk = 0.f;
       int cur_atom = -1;
       float r2 = 0.f, rho = 0.f, irho = 0.f;
@@ -254,12 +326,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
       // (a NaN bound, from an electron on a nucleus, orders above all)
       atomicMax(&rowb[row], __float_as_uint(bv));
       if (NCH == 2) atomicMax(&rowb[kRows + row], __float_as_uint(bk));
+      __syncthreads();
+      if (tid < 2 * kRows) rowe[tid] = scale_exponent(rowb[tid]);
+      __syncthreads();
+      e0 = rowe[row];
+      e1 = rowe[kRows + row];
     }
-    __syncthreads();
-    if (tid < 2 * kRows) rowe[tid] = scale_exponent(rowb[tid]);
-    __syncthreads();
-    const float sc0 = __uint_as_float((unsigned)(127 - rowe[row]) << 23);
-    const float sc1 = NCH == 2 ? __uint_as_float((unsigned)(127 - rowe[kRows + row]) << 23) : 0.f;
+    const float sc0 = __uint_as_float((unsigned)(127 - e0) << 23);
+    const float sc1 = NCH == 2 ? __uint_as_float((unsigned)(127 - e1) << 23) : 0.f;
 
     // digits of one, two (k even) or four (k = 0 mod 4) columns of a channel,
     // written to the six digit tiles
@@ -346,15 +420,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
           }
         } else {
           f32x2 t1(0.f), t2(0.f);
-          for (int p = 0; p < sh.n_prim; ++p) {
-            const f32x2 al(sh.expo_f[p], sh.expo_lo[p]);
-            const f32x2 ce = f32x2(sh.coef_f[p], sh.coef_lo[p]) * exp_x2(-(al * r2), xtab);
+          auto prim = [&](const f32x2& al, const f32x2& ce) {
             f += ce;
             if (NCH == 2) {
               const f32x2 t = (al * ce) * 2.0f;
               t1 += t;
               t2 += (al * t) * 2.0f;
             }
+          };
+          // primitives two at a time: two independent exponentials in flight
+          // (the sums still take the primitives in order)
+          int p = 0;
+          for (; p + 1 < sh.n_prim; p += 2) {
+            const f32x2 al0(sh.expo_f[p], sh.expo_lo[p]), al1(sh.expo_f[p + 1], sh.expo_lo[p + 1]);
+            const f32x2 e0 = exp_x2(-(al0 * r2), xtab), e1 = exp_x2(-(al1 * r2), xtab);
+            const f32x2 ce0 = f32x2(sh.coef_f[p], sh.coef_lo[p]) * e0;
+            const f32x2 ce1 = f32x2(sh.coef_f[p + 1], sh.coef_lo[p + 1]) * e1;
+            prim(al0, ce0);
+            prim(al1, ce1);
+          }
+          if (p < sh.n_prim) {
+            const f32x2 al(sh.expo_f[p], sh.expo_lo[p]);
+            prim(al, f32x2(sh.coef_f[p], sh.coef_lo[p]) * exp_x2(-(al * r2), xtab));
           }
           if (NCH == 2) {
             g1 = -t1;
@@ -484,6 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
       }
       break;
     }
+    fetch(tile + gridDim.x);
     // ---- 3. epilogue: the six classes of 8 MO columns per thread, recombined
     {
       const int quad = warp & 3, role = warp >> 2, ch = role >> 1, half = role & 1;
@@ -513,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
               for (int g = 0; g < kOzClasses; ++g) acc[g] = __uint_as_float(v[g][c]);
               const f32x2 s = oz_combine(acc);
               const int k = er + colf[m] - 16;
-              dst[(size_t)m * ldm] = widen_scaled(s.hi, k) + widen_scaled(s.lo, k);
+              dst[(size_t)m * ldm] = widen_scaled_int(s.hi, k) + widen_scaled_int(s.lo, k);
             }
           }
         }
@@ -528,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
 size_t oz_smem_bytes(const WfDev& wf, int nch) {
   size_t b = (size_t)nch * kOzDigits * kTileBytes + (size_t)kStackBlocks * kNPad * wf.k_pad * 2;
   b += sizeof(ShellDev) * wf.n_shell + sizeof(float) * 128 + 4 * (size_t)oz_int_words(wf);
-  b += sizeof(int) * (4 * kRows + kNPad) + 16;
+  b += sizeof(int) * (6 * kRows + kNPad) + 16;
   return b;
 }
 

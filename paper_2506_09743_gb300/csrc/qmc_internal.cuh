@@ -49,6 +49,22 @@ struct ShellDev {
   float coef_lo[QMC_MAX_PRIM];  // pairs (hi, lo) of the FP32X2 form (2^-48)
 };
 
+// Bins of the squared electron-nucleus distance for the FP32X2 row-scale
+// tables, read off the FP32 bit pattern of r^2: bin 0 holds r^2 < 2^-24, bins
+// 1 .. 640 sixteen per octave of r^2 up to 2^16, bin 641 everything beyond.
+constexpr int kOzBoundBins = 642;
+constexpr int kOzBoundBase = (127 - 24) << 4;  // (biased exponent of 2^-24) x 16
+__host__ __device__ inline int oz_bound_bin(float r2) {
+#if defined(__CUDA_ARCH__)
+  const uint32_t u = __float_as_uint(r2);
+#else
+  uint32_t u;
+  __builtin_memcpy(&u, &r2, 4);
+#endif
+  const int idx = (int)(u >> 19) - kOzBoundBase + 1;
+  return idx < 0 ? 0 : (idx > kOzBoundBins - 1 ? kOzBoundBins - 1 : idx);
+}
+
 // Everything a kernel needs, passed by value (pointers are device memory).
 struct WfDev {
   int n_atom, n_up, n_down, n_elec;
@@ -80,6 +96,10 @@ struct WfDev {
   const uint16_t* mo_oz;
   int oz_colexp[16];
   int oz;                  // 1: the FP32X2 form contracts on the tensor cores
+  // per-atom upper bounds for the row scales of k_ao_mo_oz, [n_atom][kOzBoundBins]
+  // {|AO value|, |kinetic value| = x + |grad J| y} over bins of r^2 (oz_bound_bin);
+  // nullptr: the kernel bounds every shell instead
+  const float4* oz_bound;
   int tc_value;            // 1: the FP32X2 form's Metropolis value path runs k_ao_mo_tc (FP32 AOs)
   const float* exp_tab;    // [64][2] 2^(j/64) as pairs: exp of the FP32X2 form
   const int* exc;          // [2][kMaxExc][5] rank, h1, h2, p1, p2
