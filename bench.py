@@ -337,6 +337,21 @@ def run_secondary(device, stream, barrier, flush):
                 out["li2_energy_grad_note"] = ("131,072 walkers: E_L, mean/variance, gradient of 83 parameters "
                                                "and forces on both nuclei, host-timed (synchronous call)")
             wf.close()
+    # CO energy gradient (Eq. nabla_loss) with the 100-determinant expansion:
+    # 1,008 parameters (exponents, MO coefficients, CI weights, b, w), FP64
+    mol = qi.make_co()
+    W = 131072
+    x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
+    wf = Wavefunction(mol, precision="fp64", device=device)
+    wf.energy_grad(x, want_forces=False)
+    barrier()
+    t0 = time.perf_counter()
+    wf.energy_grad(x, want_forces=False)
+    out["co_energy_grad_ms"] = 1e3 * (time.perf_counter() - t0)
+    out["co_energy_grad_note"] = ("131,072 walkers, 100 determinants: E_L (FP64 form), mean/variance and the gradient "
+                                  "of 1,008 parameters through tables of the reference inverse; host-timed")
+    wf.close()
+    del x
     # CO with the many-body Jastrow of App. D (K_en + 5 K_een terms), mixed form
     mol = qi.with_manybody_jastrow(qi.make_co())
     W = qi.WORKLOAD_WALKERS["co"]

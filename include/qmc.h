@@ -276,7 +276,16 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
  * stored); the nuclear derivatives of E_L and log|Psi| by forward-mode
  * tangents through the whole local-energy evaluation.  Sums run in a fixed
  * order (results are bitwise reproducible).
- * Scope: FP64 form, one determinant, <= 8 electrons, <= 4 per spin
+ * Several determinants (Eq. psimol with the CI sum): d log|Psi| / d Phi_{a m}
+ * from tables of the reference inverse (Eq. table): with T = A0^-1 Phi,
+ * R_X = det T[h, p], S = sum_n d_n R_n^up R_n^dn and Y_{p h} = (dS/dT_{h p}) / S,
+ *   d log|Psi| / d Phi_{a m} = [m occupied] (A0^-1)_{m a} + [(I - P T) Y A0^-1]_{m a},
+ * contracted with the AOs for the MO coefficients and exponents;
+ * d log|Psi| / d d_n = R_n^up R_n^dn / S.
+ * Scope: FP64 form and either (a) one determinant, <= 8 electrons, <= 4 per
+ * spin (gradient and forces; backflow allowed) or (b) no backflow, <= 8
+ * electrons per spin, <= 16 orbitals, <= 128 distinct excitations per spin
+ * (gradient only: forces must be NULL); no many-body Jastrow
  * (QMC_ERR_UNSUPPORTED otherwise).
  * walkers: device [3N][ldw].  e_stats: host [2] (mean, variance).  grad:
  * device [n_param] in qmc_param_layout order, or NULL.  forces: device
@@ -298,7 +307,8 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
  *   [3 + P, 3 + 2P)     sum E_L d log|Psi| / d theta_p
  *   then three blocks of 3 n_atom (atom-major, x y z):
  *                       sum d E_L / d R,  sum d ln rho / d R,  sum E_L d ln rho / d R.
- * Same scope as qmc_energy_grad (QMC_ERR_UNSUPPORTED otherwise).  Sums run in
+ * Scope (a) of qmc_energy_grad: the sums include the forces
+ * (QMC_ERR_UNSUPPORTED otherwise).  Sums run in
  * a fixed order (bitwise reproducible).  qmc_assemble_energy_grad is the host
  * arithmetic above on the (reduced) sums, copied to the host: e_stats [2],
  * grad [n_param] (or NULL), forces [n_atom][3] (or NULL); QMC_ERR_ARG when
@@ -359,9 +369,8 @@ typedef enum { QMC_DET_TABLE = 0, QMC_DET_EXPLICIT = 1 } qmc_det_method;
 qmc_status qmc_set_det_method(qmc_wf* wf, int32_t method);
 
 /* ---- Wavefunction optimisation (App. B) and batched forces (Sec. 3.3) ----
- * qmc_optimize runs the optimisation loop of App. B on the FP64 form (the
- * energy gradient's precondition: one determinant, at most 8 electrons and
- * 4 per spin): n_equil Metropolis steps, then per optimisation step t = 1 ..
+ * qmc_optimize runs the optimisation loop of App. B on the FP64 form (within
+ * the scope of qmc_energy_grad's gradient): n_equil Metropolis steps, then per optimisation step t = 1 ..
  * n_iter the energy gradient of Eq. nabla_loss at the current walkers, one
  * ADAM update of the optimised parameters (Kingma and Ba 2015, Algorithm 1;
  * App. B: lr 1e-2), the new parameters installed as by qmc_set_params, and
@@ -399,7 +408,7 @@ qmc_status qmc_optimize(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t 
  * slice is joined by the images of its samples under x -> -x, y -> -y and
  * both (all electrons together; the symmetry of a molecule on the z axis),
  * before Eq. force is evaluated with that slice's mean energy.  FP64 form,
- * same precondition as qmc_energy_grad.  walkers: device [3N][ldw].
+ * scope (a) of qmc_energy_grad (forces).  walkers: device [3N][ldw].
  * e_mean: host [n_batches] or NULL.  forces: host [n_batches][n_atom][3].
  * Synchronous; QMC_ERR_ARG unless 1 <= n_batches <= n_walkers. */
 qmc_status qmc_force_batches(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, int32_t n_batches,

@@ -631,7 +631,8 @@ qmc_status build_tables(qmc_wf* wf) {
       {h.prim_start.data(), sizeof(int) * (nao + 1)}, {ao_col.data(), sizeof(int) * nao},
       {tc_shells.data(), sizeof(int) * tc_shells.size()}, {det_tab.data(), sizeof(int) * det_tab.size()},
       {mo_x2.data(), sizeof(float) * mo_x2.size()},      {exp_tab.data(), sizeof(float) * exp_tab.size()},
-      {mo_oz.data(), sizeof(uint16_t) * mo_oz.size()},  {oz_bnd.data(), sizeof(float) * oz_bnd.size()}};
+      {mo_oz.data(), sizeof(uint16_t) * mo_oz.size()},  {oz_bnd.data(), sizeof(float) * oz_bnd.size()},
+      {order.data(), sizeof(int) * order.size()}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
   void* blob = nullptr;
@@ -671,6 +672,7 @@ qmc_status build_tables(qmc_wf* wf) {
   d.exp_tab = reinterpret_cast<const float*>(ptr[15]);
   d.mo_oz = reinterpret_cast<const uint16_t*>(ptr[16]);
   d.oz_bound = have_bnd ? reinterpret_cast<const float4*>(ptr[17]) : nullptr;
+  d.det_orig = reinterpret_cast<const int*>(ptr[18]);
   if (d.oz && !oz_supported(d)) d.oz = 0;  // the SIMT pair kernel serves this wavefunction
   // the previous tables may still be read by work in flight on any stream
   if (wf->blob) {
@@ -1195,27 +1197,38 @@ qmc_status qmc_set_params(qmc_wf* wf, const double* params) {
 // Preconditions and scratch of the energy-gradient calls: the library-owned
 // workspace, and in the gradient scratch e_loc [W], stats [4] and the block
 // partial sums (rows x blocks, rows up to max(n_param, 9 n_atom)).
+// The energy-gradient path of a wavefunction: the general kernels (one
+// determinant, <= 8 electrons, <= 4 per spin; gradient and forces) or the
+// multi-determinant kernels (no backflow; gradient only).
 static qmc_status grad_setup(qmc_wf* wf, const double* walkers, int64_t n_walkers, int64_t ldw, bool want_grad,
                              int64_t* n_param, Workspace* ws, int** err_flag, double** e_loc, double** stats,
-                             double** partial) {
+                             double** partial, bool* md) {
   if (!wf) return fail(QMC_ERR_ARG, "null wavefunction");
   if (n_walkers < 1 || ldw < n_walkers) return fail(QMC_ERR_ARG, "need n_walkers >= 1 and ldw >= n_walkers");
   if (!walkers) return fail(QMC_ERR_ARG, "null walkers");
   if (wf->precision != QMC_FP64) return fail(QMC_ERR_UNSUPPORTED, "energy gradients are computed in the FP64 form");
-  if (!general_supported(wf->dev))
-    return fail(QMC_ERR_UNSUPPORTED, "energy gradients need one determinant, <= 8 electrons, <= 4 per spin");
   if (wf->dev.mb_en || wf->dev.n_een)
     return fail(QMC_ERR_UNSUPPORTED, "energy gradients do not cover the many-body Jastrow");
+  *md = !general_supported(wf->dev);
+  if (*md && !md_grad_supported(wf->dev))
+    return fail(QMC_ERR_UNSUPPORTED,
+                "energy gradients need one determinant with <= 8 electrons (<= 4 per spin), or no backflow with "
+                "<= 8 electrons per spin, <= 16 orbitals and <= 128 distinct excitations per spin");
   qmc_param_layout(wf, n_param, nullptr);
-  if (want_grad && grad_smem_bytes(wf->dev, (int)*n_param) > 227 * 1024)
+  const size_t smem = *md ? md_grad_smem_bytes(wf->dev, (int)*n_param) : grad_smem_bytes(wf->dev, (int)*n_param);
+  if (want_grad && smem > 227 * 1024)
     return fail(QMC_ERR_UNSUPPORTED, "too many parameters for the gradient kernel's shared memory");
   void* base;
   qmc_status s = get_workspace(wf, n_walkers, nullptr, 0, &base);
   if (s) return s;
   *ws = carve(wf, base, n_walkers, err_flag);
   const int64_t nb = general_blocks(n_walkers);
-  const size_t need = align256(sizeof(double) * n_walkers) + align256(sizeof(double) * 4) +
-                      align256(sizeof(double) * nb * std::max<int64_t>(*n_param, 9 * wf->dev.n_atom));
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t part = *md ? md_grad_scratch_bytes(wf->dev, ws->ldm, (int)*n_param, n_sm)
+                          : sizeof(double) * nb * std::max<int64_t>(*n_param, 9 * wf->dev.n_atom);
+  const size_t need = align256(sizeof(double) * n_walkers) + align256(sizeof(double) * 4) + align256(part);
   if (wf->gws_bytes < need) {
     if (wf->gws) cudaFree(wf->gws);
     wf->gws = nullptr;
@@ -1247,14 +1260,22 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
   Workspace ws;
   int* err_flag;
   double *e_loc, *stats, *partial;
+  bool md = false;
   qmc_status s = grad_setup(wf, walkers, n_walkers, ldw, grad != nullptr, &n_param, &ws, &err_flag, &e_loc, &stats,
-                            &partial);
+                            &partial, &md);
   if (s) return s;
+  if (md && forces)
+    return fail(QMC_ERR_UNSUPPORTED, "forces need one determinant with <= 8 electrons (pass forces = NULL)");
   s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, nullptr, st);
   if (s) return s;
   s = launch_status(launch_mean_var(e_loc, n_walkers, stats, st), "mean/variance");
   if (s) return s;
-  if (grad) {
+  if (grad && md) {
+    s = launch_status(launch_md_grad(wf->dev, walkers, n_walkers, ldw, ws, e_loc, stats, wf->spec.prim_start[wf->dev.n_ao],
+                                     (int)n_param, partial, grad, st),
+                      "parameter gradient (several determinants)");
+    if (s) return s;
+  } else if (grad) {
     s = launch_status(launch_grad(wf->dev, walkers, n_walkers, ldw, e_loc, stats, wf->dev.ao_ang, wf->dev.ao_prim,
                                   (int)n_param, partial, grad, st),
                       "parameter gradient");
@@ -1287,9 +1308,11 @@ qmc_status qmc_energy_grad_sums(qmc_wf* wf, const double* walkers, int64_t n_wal
   Workspace ws;
   int* err_flag;
   double *e_loc, *stats, *partial;
+  bool md = false;
   qmc_status s =
-      grad_setup(wf, walkers, n_walkers, ldw, true, &n_param, &ws, &err_flag, &e_loc, &stats, &partial);
+      grad_setup(wf, walkers, n_walkers, ldw, true, &n_param, &ws, &err_flag, &e_loc, &stats, &partial, &md);
   if (s) return s;
+  if (md) return fail(QMC_ERR_UNSUPPORTED, "the per-batch sums include forces: one determinant, <= 8 electrons");
   s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, nullptr, st);
   if (s) return s;
   s = launch_status(launch_energy_sums(e_loc, n_walkers, sums, st), "energy sums");

@@ -192,6 +192,11 @@ __global__ void k_row_sums(const double* __restrict__ partial, int n_rows, int n
   out[k] = s;
 }
 
+cudaError_t launch_row_sums(const double* partial, int n_rows, int n_cols, double* out, cudaStream_t st) {
+  k_row_sums<<<(n_rows + 127) / 128, 128, 0, st>>>(partial, n_rows, n_cols, out);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------------------
 // launchers
 

@@ -104,6 +104,7 @@ struct WfDev {
   const float* exp_tab;    // [64][2] 2^(j/64) as pairs: exp of the FP32X2 form
   const int* exc;          // [2][kMaxExc][5] rank, h1, h2, p1, p2
   const int* det_idx;      // [n_det][2] excitation index per spin
+  const int* det_orig;     // [n_det] index of each (sorted) determinant in the caller's order
   const double* det_w;     // [n_det]
   // [n_det] {packed offsets up, rank up, packed offsets down, rank down}:
   // table offsets (h_a - h_lo) nv + (p_b - n_s) of the k x k block, 8 bits
@@ -262,6 +263,14 @@ bool general_supported(const WfDev& wf);
 bool bf_multidet_supported(const WfDev& wf);
 int general_blocks(int64_t W);
 size_t grad_smem_bytes(const WfDev& wf, int n_param);
+// multi-determinant parameter gradient (no backflow; k_md_grad.cu)
+bool md_grad_supported(const WfDev& wf);
+size_t md_grad_smem_bytes(const WfDev& wf, int n_param);
+size_t md_grad_scratch_bytes(const WfDev& wf, int64_t ldm, int n_param, int n_sm);
+cudaError_t launch_row_sums(const double* partial, int n_rows, int n_cols, double* out, cudaStream_t st);
+cudaError_t launch_md_grad(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                           const double* e_loc, const double* stats, int n_prim, int n_param, double* scratch,
+                           double* grad, cudaStream_t st, int weight = 0);
 cudaError_t launch_eloc_general(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, bool kinetic,
                                 double* e_loc, double* log_psi, cudaStream_t st);
 cudaError_t launch_mean_var(const double* x, int64_t W, double* stats, cudaStream_t st);

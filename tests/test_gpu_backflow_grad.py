@@ -80,7 +80,7 @@ def test_backflow_rejected_outside_its_scope(pkg):
     mol.backflow_w = 0.1
     with pytest.raises(QmcError):
         pkg.Wavefunction(mol, precision="fp64")
-    # gradients and forces are single-determinant only
+    # with backflow, gradients and forces are single-determinant only
     wf = pkg.Wavefunction(qi.make_li2(n_mo=6, n_det=5), precision="fp64")
     with pytest.raises(QmcError):
         wf.energy_grad(_x(qi.walkers(qi.make_li2(), 16, seed=1)))

@@ -399,8 +399,12 @@ def test_rotation_invariance_s_basis():
 # gradient and force estimators against finite differences
 
 
-def test_grad_log_psi_finite_difference():
-    mol = qi.make_li2()
+@pytest.mark.parametrize("name", ["li2", "co_sd20"])
+def test_grad_log_psi_finite_difference(name):
+    """The oracle's autograd d log|Psi| / d theta against central
+    differences, for the backflow single determinant (Li2) and a 20-determinant
+    CO expansion (CI weights, occupied and virtual MO columns)."""
+    mol = qi.make_li2() if name == "li2" else qi.make_co(n_det=20)
     wf = O.Wavefunction(mol, requires_grad=True)
     r = _walkers(mol, 3)
     G = O.grad_log_psi(wf, r)
@@ -408,18 +412,23 @@ def test_grad_log_psi_finite_difference():
     h = 1e-5
     off = 0
     rng = np.random.default_rng(0)
-    for p in params:
+    extra = {"mo_coeff": [3 * mol.n_mo + 2, 5 * mol.n_mo + 10, 40 * mol.n_mo + 12], "det_weight": [1, 2, 7]}
+    for key, p in zip(wf.params().keys(), params):
         n = p.numel()
-        for j in sorted(set([0, n - 1] + list(rng.integers(0, n, size=4)))):
-            with torch.no_grad():
-                flat = p.view(-1)
-                old = flat[j].item()
-                flat[j] = old + h
-                lp_p = O.log_psi(wf, r)[0]
-                flat[j] = old - h
-                lp_m = O.log_psi(wf, r)[0]
-                flat[j] = old
-            fd = (lp_p - lp_m) / (2 * h)
+        picks = [0, n - 1] + list(rng.integers(0, n, size=4)) + [j for j in extra.get(key, []) if j < n]
+        for j in sorted(set(picks)):
+            def central(step):
+                with torch.no_grad():
+                    flat = p.view(-1)
+                    old = flat[j].item()
+                    flat[j] = old + step
+                    lp_p = O.log_psi(wf, r)[0]
+                    flat[j] = old - step
+                    lp_m = O.log_psi(wf, r)[0]
+                    flat[j] = old
+                return (lp_p - lp_m) / (2 * step)
+
+            fd = (4.0 * central(h / 2) - central(h)) / 3.0  # Richardson: O(h^4)
             assert torch.allclose(G[:, off + j], fd, rtol=1e-6, atol=1e-7), (off, j)
         off += n
 
