@@ -103,6 +103,76 @@ def x2_stage_ops(mol) -> float:
     return float(mol.n_elec * per_row)
 
 
+def fp64_ao_stage_ops(mol) -> dict:
+    """Algorithmic FP64 work per walker of k_ao_mo_simt<double> (FP64 form):
+    per electron and Gaussian primitive -alpha rho^2, c e and the value and
+    kinetic radial sums (11 flops) and one exponential; per AO its value and
+    kinetic channel (12 flops); the contraction (ao_mo_stage_flops)."""
+    n_shell_prim = 0
+    shells = set()
+    for b in range(mol.n_ao):
+        key = (int(mol.ao_atom[b]), int(sum(mol.ao_pow[b][:3])),
+               tuple(mol.prim_exp[mol.ao_prim_start[b]:mol.ao_prim_start[b + 1]]))
+        if key not in shells:
+            shells.add(key)
+            n_shell_prim += int(mol.ao_prim_start[b + 1] - mol.ao_prim_start[b])
+    flops = mol.n_elec * (11 * n_shell_prim + 12 * mol.n_ao) + ao_mo_stage_flops(mol)
+    return {"flops": float(flops), "exp": mol.n_elec * n_shell_prim}
+
+
+def general_eloc_ops(mol) -> dict:
+    """Algorithmic FP64 work per walker of the general kernel's local energy
+    (k_eloc_general: one determinant, backflow), counted from its formulas:
+    flops (an FMA counts 2) and the special functions separately.
+      pairs:      geometry 8 flops, 1 sqrt, 1 division; Pade J, grad J, lap J
+                  and 1/r_ij 31 flops, 2 divisions; backflow Jacobian blocks
+                  G1, G2 and their row sums 110 flops (w != 0)
+      e-n terms:  10 flops, 1 sqrt, 1 division per (electron, atom)
+      backflow positions: 4 flops per (electron, coordinate, partner)
+      orbitals per electron: per atom 9 flops, 1 sqrt, 1 division; per shell
+                  the radial factor (STO 12 + kn flops + 1 exp; GTO 12 flops +
+                  1 exp per primitive) and the closed-form s/p derivative set
+                  (20); per AO 2 x 10 channels x n_occ flops (+ 15 for p)
+      reference inverses: 2 n^3 + n^2 flops, n divisions, 1 log per spin
+      contractions against A^-1: 6 n^3 (gradients) + 12 n per electron (Hessians)
+      per coordinate and spin: per row 45 flops (Jacobian row, cq, Tr(A^-1 d^2 A)
+                  terms, Y row), then Tr Y, Tr Y^2 and the second derivative 24"""
+    N, nu, nd = int(mol.n_elec), int(mol.n_up), int(mol.n_down)
+    n_occ = max(nu, nd)
+    A = int(mol.n_atom)
+    P = N * (N - 1) // 2
+    bf = float(mol.backflow_w) != 0.0
+    flops = P * (8 + 31 + (110 if bf else 0)) + N * A * 10 + (N * 3 * (N - 1) * 4)
+    n_sqrt = P + N * A + N * A
+    n_div = P + 2 * P + N * A + N * A
+    n_exp = 0
+    shells = {}
+    for b in range(mol.n_ao):
+        key = (int(mol.ao_atom[b]), int(sum(mol.ao_pow[b][:3])), int(mol.ao_kind[b]), int(mol.ao_pow[b][3]),
+               tuple(mol.prim_exp[mol.ao_prim_start[b]:mol.ao_prim_start[b + 1]]))
+        shells.setdefault(key, 0)
+        shells[key] += 1
+    per_elec = A * 9
+    for (atom, l, kind, kn, ex), n_ao in shells.items():
+        if kind == 0:
+            per_elec += 12 + kn + 20
+            n_exp += N
+        else:
+            per_elec += 12 * len(ex) + 20
+            n_exp += N * len(ex)
+        per_elec += n_ao * (2 * 10 * n_occ + (15 if l == 1 else 0))
+    flops += N * per_elec
+    for n in (nu, nd):
+        if n:
+            flops += 2 * n ** 3 + n * n + 6 * n ** 3
+            n_div += n
+    flops += N * 12 * n_occ
+    for n in (nu, nd):
+        if n:
+            flops += 3 * N * (n * 45 + 24)
+    return {"flops": float(flops), "exp": n_exp, "sqrt": n_sqrt, "div": n_div, "log": 2}
+
+
 def oz_stage_alu_ops(mol) -> float:
     """Algorithmic FP32/ALU operations per walker of k_ao_mo_oz, the FP32X2
     AO stage with the contraction on the tensor cores: the AO evaluation of
@@ -268,7 +338,7 @@ def run_serving(n_requests: int, with_fp64: bool, device: int, n_requests_fp64: 
     from paper_2506_09743_gb300 import serving
 
     out = {"n_steps": 50, "walker_choices": [4096, 16384, 65536, 262144], "molecules": ["h2", "lih", "li2", "co"],
-           "note": "Li2 (backflow) requests run in the FP64 form in both mixes",
+           "note": "Li2 (backflow) requests run in the FP32X2 form in the FP32X2 mix",
            "policy": "large (>= 65,536 walkers) requests ordered, at most 2 in flight, low stream priority"}
     forms = ["fp32x2"] + (["fp64"] if with_fp64 else [])
     for form in forms:
@@ -294,7 +364,7 @@ def run_serving(n_requests: int, with_fp64: bool, device: int, n_requests_fp64: 
     return out
 
 
-def run_secondary(device, stream, barrier, flush):
+def run_secondary(device, stream, barrier, flush, rates=None):
     """The other workloads: E_L throughput of H2 (1,024 walkers), LiH
     (65,536) and Li2 with backflow (131,072), and the Li2 energy gradient +
     forces (Eq. nabla_loss, Eq. force) on 131,072 walkers."""
@@ -324,11 +394,30 @@ def run_secondary(device, stream, barrier, flush):
         mol = qi.make_molecule(name)
         W = qi.WORKLOAD_WALKERS[name]
         x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
-        forms = ("fp64",) if mol.backflow_w != 0.0 else ("fp64", "fp32x2", "mixed_tf32")
+        forms = ("fp64", "fp32x2") if mol.backflow_w != 0.0 else ("fp64", "fp32x2", "mixed_tf32")
         for form in forms:
             wf = Wavefunction(mol, precision=form, device=device)
             out[f"{name}_{form}_walker_evals_per_s"] = rate(wf, x, W)
-            if name == "li2":
+            if name == "li2" and form == "fp64":
+                # the general kernel's FP64 roofline: formula flops, and with
+                # the special functions at their measured FMA equivalents
+                ops = general_eloc_ops(mol)
+                ms = 1e3 * W / out[f"{name}_{form}_walker_evals_per_s"]
+                fl = ops["flops"] * W / (ms / 1e3) / 1e12
+                eq = None
+                if rates:
+                    f = rates["fp64_fma_per_s"]
+                    sp = (ops["exp"] * f / rates["fp64_exp_per_s"] + ops["sqrt"] * f / rates["fp64_sqrt_per_s"]
+                          + ops["div"] * f / rates["fp64_recip_per_s"])
+                    eq = (ops["flops"] + 2.0 * sp) * W / (ms / 1e3) / 1e12
+                out["li2_eloc_roofline"] = {
+                    "kernel": "k_eloc_general<6, 3>", "bound": "alu", "kernel_ms": ms, "unit": "TFLOP/s (FP64)",
+                    "flops_per_walker": ops["flops"], "exp_per_walker": ops["exp"], "sqrt_per_walker": ops["sqrt"],
+                    "div_per_walker": ops["div"], "achieved": fl, "peak": FP64_PEAK_TFLOPS,
+                    "frac": fl / FP64_PEAK_TFLOPS, "achieved_with_special": eq,
+                    "frac_with_special": None if eq is None else eq / FP64_PEAK_TFLOPS,
+                    "ops_model": "bench.general_eloc_ops; exp, sqrt and division at the measured FMA equivalents"}
+            if name == "li2" and form == "fp64":
                 wf.energy_grad(x)
                 barrier()
                 t0 = time.perf_counter()
@@ -480,20 +569,23 @@ def rank_walker_seed(rank: int) -> int:
     return qi.SEED_WALKERS + rank
 
 
-PROFILE_CASES = ("co_fp32x2", "co_mixed_tf32", "co_fp64", "li2_eloc", "li2_energy_grad", "li2_sample")
+PROFILE_CASES = ("co_fp32x2", "co_mixed_tf32", "co_fp64", "co_energy_grad", "li2_eloc", "li2_eloc_fp32x2",
+                 "li2_energy_grad", "li2_sample")
 
 
 def run_only(case: str, W: int, steps: int, warmup: int, device: int = 0) -> dict:
     """One workload alone (the small cases the ncu captures run): `warmup`
     untimed calls, then `steps` calls timed with CUDA events.  CO cases time
-    qmc_local_energy in the named form; li2_eloc the backflow E_L (FP64),
+    qmc_local_energy in the named form (co_energy_grad: the FP64 gradient of
+    the 100-determinant expansion); li2_eloc the backflow E_L (FP64),
     li2_energy_grad qmc_energy_grad, li2_sample ten Metropolis steps."""
     import torch
 
     from paper_2506_09743_gb300 import Wavefunction
 
     mol = qi.make_co() if case.startswith("co_") else qi.make_li2()
-    form = case[3:] if case.startswith("co_") else "fp64"
+    form = (case[3:] if case.startswith("co_") and case != "co_energy_grad"
+            else "fp32x2" if case.endswith("_fp32x2") else "fp64")
     x = torch.tensor(qi.to_soa(qi.walkers(mol, W, seed=qi.SEED_WALKERS)), device="cuda")
     wf = Wavefunction(mol, precision=form, device=device)
     e = torch.empty(W, dtype=torch.float64, device="cuda")
@@ -501,6 +593,8 @@ def run_only(case: str, W: int, steps: int, warmup: int, device: int = 0) -> dic
     def call():
         if case == "li2_energy_grad":
             wf.energy_grad(x)
+        elif case == "co_energy_grad":
+            wf.energy_grad(x, want_forces=False)
         elif case == "li2_sample":
             wf.sample(x, n_steps=10, step=0.05, seed=0x5EED)
         else:
@@ -559,6 +653,9 @@ def main():
     if args.only:
         print(json.dumps(run_only(args.only, args.walkers, args.steps, args.warmup, local)), flush=True)
         return
+    from paper_2506_09743_gb300 import _lib as qlib
+
+    rates = qlib.measure_rates()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -665,7 +762,8 @@ def main():
     mh_mixed = mh_rate(wf_mixed)
 
     sharded = run_sharded_energy_grad(local, rank, world, dist, barrier)
-    secondary = run_secondary(local, stream, barrier, flush) if world == 1 and not args.no_secondary else None
+    secondary = (run_secondary(local, stream, barrier, flush, rates)
+                 if world == 1 and not args.no_secondary else None)
     det_sweep = run_det_sweep(local, stream, barrier, flush) if world == 1 and not args.no_det_sweep else None
 
     serving_out = None
@@ -684,6 +782,10 @@ def main():
                 "note": "against the FP64 form on the same walkers; the walkers beyond 2e-4 Ha are at nodes "
                         "(|E| of 1e4..1e7 Ha), outside the parity tests' conditioning cut"}
 
+    # measured FP64 FMA and FP32 instruction rates of this GPU (probe kernels
+    # of the library): beside the nominal peaks derived from the unit counts
+    fp64_meas = 2.0 * rates["fp64_fma_per_s"] / 1e12 if rates else None
+    fp32_meas = rates["fp32_fma_per_s"] / 1e12 if rates else None
     # rooflines: the FP32X2 AO stage (k_ao_mo_oz) is bound by FP32/ALU issue
     # (its contraction runs on the tensor pipe), the determinant stage by the
     # FP64 pipe
@@ -697,7 +799,8 @@ def main():
     roofline = {"kernel": "k_ao_mo_oz (AOs in pairs of FP32, exact digit-sliced contraction on tcgen05; FP32X2 form)",
                 "bound": "alu", "achieved": oz_rate, "peak": FP32_PEAK_TOPS, "unit": "T FP32 ops/s",
                 "frac": oz_rate / FP32_PEAK_TOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (no measured FP32 peak on this pool)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (no FP32 figure in the measured peaks)",
+                "peak_measured": fp32_meas, "frac_of_measured": oz_rate / fp32_meas if fp32_meas else None,
                 "ops_per_launch": oz_ops,
                 "ops_model": "bench.oz_stage_alu_ops: AO evaluation in pair arithmetic + digit slicing + class "
                              "recombination; the contraction runs on the tensor pipe",
@@ -705,14 +808,28 @@ def main():
                 "simt_equivalent_note": "the whole stage (bench.x2_stage_ops, contraction as pair multiply-"
                                         "accumulates) per second: what the SIMT pair kernel would have to issue",
                 "kernel_ms": x2_ms}
+    # the FP64 form's AO stage: contraction flops + AO flops + exponentials
+    # (in FMA equivalents from the measured exp rate)
+    fp64_ao = fp64_ao_stage_ops(mol)
+    simt_ms = float(stage_fp64[1])
+    exp_fma = rates["fp64_fma_per_s"] / rates["fp64_exp_per_s"] if rates else None
+    simt_flops = fp64_ao["flops"] * W
+    simt_equiv = simt_flops + (2.0 * exp_fma * fp64_ao["exp"] * W if exp_fma else 0.0)
     rooflines = {
         "k_det": {"bound": "alu", "achieved": det_rate, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
                   "frac": det_rate / FP64_PEAK_TFLOPS, "kernel_ms": det_ms, "flops_per_launch": flops_det,
                   "traffic": None if DET_TRAFFIC_BYTES_PER_WALKER is None else DET_TRAFFIC_BYTES_PER_WALKER * W,
-                  "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal)"},
-        "k_ao_mo_simt_fp64": {"bound": "alu", "kernel_ms": float(stage_fp64[1]),
-                              "achieved": ao_mo_stage_flops(mol) * W / (float(stage_fp64[1]) / 1e3) / 1e12,
-                              "unit": "TFLOP/s (FP64, contraction flops only)", "peak": FP64_PEAK_TFLOPS},
+                  "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal)",
+                  "peak_measured": fp64_meas, "frac_of_measured": det_rate / fp64_meas if fp64_meas else None},
+        "k_ao_mo_simt_fp64": {"bound": "alu", "kernel_ms": simt_ms, "unit": "TFLOP/s (FP64)",
+                              "peak": FP64_PEAK_TFLOPS, "flops_per_launch": simt_flops,
+                              "exp_per_launch": fp64_ao["exp"] * W,
+                              "achieved": simt_flops / (simt_ms / 1e3) / 1e12,
+                              "achieved_with_exp": simt_equiv / (simt_ms / 1e3) / 1e12,
+                              "frac_with_exp": simt_equiv / (simt_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                              "exp_cost_fma": exp_fma,
+                              "ops_model": "bench.fp64_ao_stage_ops: AO values and kinetic channels, contraction; "
+                                           "each exponential as the measured FMA equivalents"},
         "k_ao_mo_tc": {"kernel_ms": float(stage_mixed[1]), "note": "FP32 AO stage + tcgen05 TF32x3 contraction"},
     }
     # whole step: the FP32X2 step cannot beat its AO stage at the FP32 issue
@@ -743,6 +860,7 @@ def main():
         "fp32x2_vs_fp64": value / value_fp64,
         "roofline": roofline,
         "rooflines": rooflines,
+        "measured_rates": rates,
         "whole_step": whole_step,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(soa.nbytes),
                 "d2h_bytes_per_step": int(2 * 8 * W), "api": "qmc_local_energy_host (pinned host buffers), FP32X2 form"},

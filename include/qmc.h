@@ -77,7 +77,11 @@ typedef enum {
  * Jastrow terms are FP64 in QMC_FP64 and use FP32 pair arithmetic with
  * compensated sums in the other forms; the Coulomb potential is FP64 in
  * QMC_FP64, pairs of FP32 in QMC_FP32X2 and FP32 terms with compensated
- * sums otherwise.  Backflow wavefunctions run in QMC_FP64 only. */
+ * sums otherwise.  Backflow wavefunctions run in QMC_FP64 and QMC_FP32X2; in
+ * QMC_FP32X2 only their orbitals (AO values, derivatives and the AO->MO
+ * contraction, s and p shells) are in pairs of FP32, while the Jastrow
+ * factor, the backflow map, the potential, the determinants and the
+ * Laplacian stay FP64 (and so does the value path). */
 typedef enum {
   QMC_FP64 = 0,
   QMC_FP32 = 1,
@@ -517,6 +521,15 @@ const char* qmc_server_last_error(void);
 /* Message of the last failed call on this thread ("" if none yet).  The
  * pointer stays valid until the next library call on the same thread. */
 const char* qmc_last_error(void);
+
+/* Measured arithmetic rates of the current device, the denominators of the
+ * FP64- and FP32-bound rooflines: rates[0] FP64 FMA/s, [1] FP32 FMA
+ * instructions/s, [2] FP64 exp/s, [3] FP64 sqrt/s, [4] FP64 reciprocal (1/x)/s.
+ * Each is timed with CUDA events over a probe kernel of eight independent
+ * dependency chains per thread, 8 x 256 threads per SM (contractive maps:
+ * every value stays finite).  Synchronous on `stream` (about 0.3 s); rates:
+ * host [5].  QMC_ERR_ARG for NULL rates, QMC_ERR_OOM, QMC_ERR_CUDA. */
+qmc_status qmc_measure_rates(double rates[5], void* stream);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ EXPORTED = (
     "qmc_server_progress", "qmc_server_results", "qmc_server_cancel", "qmc_server_set_policy", "qmc_server_free_bytes", "qmc_server_clock",
     "qmc_server_last_error", "qmc_set_timing", "qmc_last_stage_ms", "qmc_set_det_method", "qmc_optimize", "qmc_force_batches", "qmc_set_manybody_jastrow",
     "qmc_check_status", "qmc_set_wait_limit", "qmc_energy_grad_sums_size", "qmc_energy_grad_sums",
-    "qmc_assemble_energy_grad", "qmc_last_error",
+    "qmc_assemble_energy_grad", "qmc_measure_rates", "qmc_last_error",
 )
 
 PD = POINTER(c_double)
@@ -164,6 +164,8 @@ def load(path: str = LIB_PATH):
     lib.qmc_energy_grad_sums.restype = c_int32
     lib.qmc_assemble_energy_grad.argtypes = [c_int64, c_int32, PD, PD, PD, PD]
     lib.qmc_assemble_energy_grad.restype = c_int32
+    lib.qmc_measure_rates.argtypes = [PD, c_void_p]
+    lib.qmc_measure_rates.restype = c_int32
     lib.qmc_last_error.argtypes = []
     lib.qmc_last_error.restype = c_char_p
     _lib = lib
@@ -195,3 +197,16 @@ def assemble_energy_grad(sums, n_param: int, n_atom: int):
     check(lib.qmc_assemble_energy_grad(int(n_param), int(n_atom), s.ctypes.data_as(PD), e.ctypes.data_as(PD),
                                        g.ctypes.data_as(PD), f.ctypes.data_as(PD)))
     return float(e[0]), float(e[1]), g[:n_param], f
+
+
+def measure_rates(stream=None) -> dict:
+    """qmc_measure_rates: the GPU's FP64 FMA, FP32 FMA and FP64 exp / sqrt /
+    reciprocal rates per second, measured by the library's probe kernels."""
+    import numpy as np
+
+    lib = load()
+    out = np.zeros(5, dtype=np.float64)
+    h = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    check(lib.qmc_measure_rates(out.ctypes.data_as(PD), h))
+    keys = ("fp64_fma_per_s", "fp32_fma_per_s", "fp64_exp_per_s", "fp64_sqrt_per_s", "fp64_recip_per_s")
+    return {k: float(v) for k, v in zip(keys, out)}

@@ -280,8 +280,10 @@ qmc_status build_tables(qmc_wf* wf) {
   }
   d.vnn = vnn_of(d);
   d.wait_cycles = wf->wait_cycles;
-  if (h.w != 0.0 && prec != QMC_FP64)
-    return fail(QMC_ERR_UNSUPPORTED, "backflow wavefunctions run in the FP64 form only");
+  if (h.w != 0.0 && prec != QMC_FP64 && prec != QMC_FP32X2)
+    return fail(QMC_ERR_UNSUPPORTED, "backflow wavefunctions run in the FP64 and FP32X2 forms only");
+  // FP32X2 with backflow: the general kernels take the orbitals in pairs of FP32
+  d.gen_x2 = (h.w != 0.0 && prec == QMC_FP32X2) ? 1 : 0;
   d.mb_en = h.jen.empty() ? 0 : 1;
   d.n_een = (int)(h.jeen.size() / 7);
   for (int k = 0; k < 3; ++k) {
@@ -469,9 +471,13 @@ qmc_status build_tables(qmc_wf* wf) {
       d.part_off[p][4] = (int)tc_shells.size();
     }
   }
+  if (d.gen_x2)
+    for (const ShellDev& q : shells)
+      if (q.l > 1) return fail(QMC_ERR_UNSUPPORTED, "the FP32X2 form with backflow covers s and p shells");
   std::vector<double> mo64((size_t)nao * nmo);
   std::vector<float> mo32((size_t)nao * nmo);
   std::vector<float> mo_x2((size_t)nao * nmo * 2);  // rows in x2_row order, (hi, lo)
+  std::vector<float> mo_x2n((size_t)nao * nmo * 2);  // rows in AO order, (hi, lo)
   for (int b = 0; b < nao; ++b)
     for (int m = 0; m < nmo; ++m) {
       const double c = h.mo[(size_t)b * nmo + m] * ang[b];
@@ -480,6 +486,8 @@ qmc_status build_tables(qmc_wf* wf) {
       const size_t o = 2 * ((size_t)x2_row[b] * nmo + m);
       mo_x2[o] = (float)c;
       mo_x2[o + 1] = (float)(c - (double)(float)c);
+      mo_x2n[2 * ((size_t)b * nmo + m)] = (float)c;
+      mo_x2n[2 * ((size_t)b * nmo + m) + 1] = (float)(c - (double)(float)c);
     }
   // 2^(j/64), j = 0..63, as pairs of FP32 for the FP32X2 exponential
   std::vector<float> exp_tab(128);
@@ -632,7 +640,7 @@ qmc_status build_tables(qmc_wf* wf) {
       {tc_shells.data(), sizeof(int) * tc_shells.size()}, {det_tab.data(), sizeof(int) * det_tab.size()},
       {mo_x2.data(), sizeof(float) * mo_x2.size()},      {exp_tab.data(), sizeof(float) * exp_tab.size()},
       {mo_oz.data(), sizeof(uint16_t) * mo_oz.size()},  {oz_bnd.data(), sizeof(float) * oz_bnd.size()},
-      {order.data(), sizeof(int) * order.size()}};
+      {order.data(), sizeof(int) * order.size()},        {mo_x2n.data(), sizeof(float) * mo_x2n.size()}};
   size_t total = 0;
   for (auto& p : parts) total += align256(p.second);
   void* blob = nullptr;
@@ -673,6 +681,7 @@ qmc_status build_tables(qmc_wf* wf) {
   d.mo_oz = reinterpret_cast<const uint16_t*>(ptr[16]);
   d.oz_bound = have_bnd ? reinterpret_cast<const float4*>(ptr[17]) : nullptr;
   d.det_orig = reinterpret_cast<const int*>(ptr[18]);
+  d.mo_x2n = reinterpret_cast<const float2*>(ptr[19]);
   if (d.oz && !oz_supported(d)) d.oz = 0;  // the SIMT pair kernel serves this wavefunction
   // the previous tables may still be read by work in flight on any stream
   if (wf->blob) {

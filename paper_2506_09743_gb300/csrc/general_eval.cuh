@@ -25,6 +25,7 @@
 
 #include <type_traits>
 
+#include "ao_eval.cuh"
 #include "dual.cuh"
 #include "qmc_internal.cuh"
 
@@ -79,7 +80,8 @@ __device__ __forceinline__ int hidx(int d, int f) {
 struct GenShared {
   const ShellDev* sh;
   const int* pw;
-  const double* C;  // [n_ao][n_mo] (angular factors folded in)
+  const double* C;     // [n_ao][n_mo] (angular factors folded in)
+  const float2* Cx2;   // the same as pairs of FP32 (FP32X2 form), or null
 };
 
 // One shell's AO value, gradient and Hessian channels at displacement
@@ -229,6 +231,111 @@ __device__ void mo_channels(const WfDev& wf, const GenShared& g, const double p[
       shell_channels<double, T, NO>(wf, g, sh, xd, yd, zd, r2d, rhod, ir2d, irhod, n_occ, phi, dphi, hphi, deriv);
     else
       shell_channels<T, T, NO>(wf, g, sh, dx, dy, dz, r2, rho, ir2, irho, n_occ, phi, dphi, hphi, deriv);
+  }
+}
+
+// The FP32X2 form of mo_channels (shells with l <= 1): displacements, radial
+// factors, the closed-form derivative set and the contraction in pairs of
+// FP32 (f32x2.cuh: error-free products and sums, table-driven exponential),
+// widened to FP64 once per channel.  C is the pair table g.Cx2 [n_ao][n_mo]
+// (angular factors folded in).  dphi / hphi may be null when !deriv.
+template <int NO>
+__device__ void mo_channels_x2(const WfDev& wf, const GenShared& g, const double p[3], int n_occ, double* phi,
+                               double (*dphi)[3], double (*hphi)[6], bool deriv) {
+  f32x2 aphi[NO], adphi[NO][3], ahphi[NO][6];
+  for (int m = 0; m < NO; ++m) {
+    aphi[m] = f32x2(0.f);
+    for (int d = 0; d < 3; ++d) adphi[m][d] = f32x2(0.f);
+    for (int q = 0; q < 6; ++q) ahphi[m][q] = f32x2(0.f);
+  }
+  int cur_atom = -1;
+  f32x2 dv[3], r2(0.f), rho(0.f), irho(0.f), ir2(0.f);
+  for (int s = 0; s < wf.n_shell; ++s) {
+    const ShellDev& sh = g.sh[s];
+    if (sh.atom != cur_atom) {
+      cur_atom = sh.atom;
+      for (int d = 0; d < 3; ++d) dv[d] = diff_x2(p[d], wf.atom_xyz[cur_atom][d]);
+      r2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+      rho = sqrt_x2(r2);
+      irho = recip_x2(rho);
+      ir2 = irho * irho;
+    }
+    f32x2 f(0.f), g1(0.f), f2(0.f);
+    if (sh.kind == 0) {
+      const f32x2 z(sh.expo_f[0], sh.expo_lo[0]);
+      f32x2 rk(1.f);
+      for (int k = 0; k < sh.kn; ++k) rk = rk * rho;
+      f = f32x2(sh.coef_f[0], sh.coef_lo[0]) * rk * exp_x2(-(z * rho), wf.exp_tab);
+      if (deriv) {
+        const f32x2 q = irho * (float)sh.kn - z;
+        g1 = q * f * irho;
+        f2 = (q * q - ir2 * (float)sh.kn) * f;
+      }
+    } else {
+      for (int k = 0; k < sh.n_prim; ++k) {
+        const f32x2 al(sh.expo_f[k], sh.expo_lo[k]);
+        const f32x2 ce = f32x2(sh.coef_f[k], sh.coef_lo[k]) * exp_x2(-(al * r2), wf.exp_tab);
+        f = f + ce;
+        if (deriv) {
+          const f32x2 t = (al * ce) * 2.0f;
+          g1 = g1 - t;
+          f2 = f2 + ((al * r2) * 2.0f - 1.0f) * t;
+        }
+      }
+    }
+    // closed forms as in shell_channels: q = (f2 - g1) / rho^2
+    f32x2 gs[3], hs[6];
+    if (deriv) {
+      const f32x2 q = (f2 - g1) * ir2;
+      for (int d = 0; d < 3; ++d) gs[d] = g1 * dv[d];
+      hs[0] = g1 + q * dv[0] * dv[0];
+      hs[1] = g1 + q * dv[1] * dv[1];
+      hs[2] = g1 + q * dv[2] * dv[2];
+      hs[3] = q * dv[0] * dv[1];
+      hs[4] = q * dv[0] * dv[2];
+      hs[5] = q * dv[1] * dv[2];
+    }
+    for (int k = 0; k < sh.n_ao; ++k) {
+      const int b = sh.ao_first + k;
+      f32x2 val = f, grad[3], hess[6];
+      if (deriv)
+        for (int d = 0; d < 3; ++d) grad[d] = gs[d];
+      if (deriv)
+        for (int q = 0; q < 6; ++q) hess[q] = hs[q];
+      if (sh.l == 1) {
+        const int pw = g.pw[b];
+        const int c = (pw & 15) ? 0 : ((pw >> 4) & 15) ? 1 : 2;
+        const f32x2 x = dv[c];
+        val = x * f;
+        if (deriv) {
+          for (int d = 0; d < 3; ++d) grad[d] = x * gs[d];
+          grad[c] = grad[c] + f;
+          for (int q = 0; q < 6; ++q) hess[q] = x * hs[q];
+          hess[c] = hess[c] + gs[c] * 2.0f;
+          for (int e = 0; e < 3; ++e)
+            if (e != c) hess[hidx(c, e)] = hess[hidx(c, e)] + gs[e];
+        }
+      }
+      const float2* Cb = g.Cx2 + (size_t)b * wf.n_mo;
+      for (int m = 0; m < NO; ++m) {
+        if (m < n_occ) {
+          const float2 cc = Cb[m];
+          const f32x2 c(cc.x, cc.y);
+          mac_x2(aphi[m], c, val);
+          if (deriv) {
+            for (int d = 0; d < 3; ++d) mac_x2(adphi[m][d], c, grad[d]);
+            for (int q = 0; q < 6; ++q) mac_x2(ahphi[m][q], c, hess[q]);
+          }
+        }
+      }
+    }
+  }
+  for (int m = 0; m < NO; ++m) {
+    phi[m] = widen(normalize_x2(aphi[m]));
+    if (deriv) {
+      for (int d = 0; d < 3; ++d) dphi[m][d] = widen(normalize_x2(adphi[m][d]));
+      for (int q = 0; q < 6; ++q) hphi[m][q] = widen(normalize_x2(ahphi[m][q]));
+    }
   }
 }
 
@@ -493,7 +600,7 @@ __device__ __forceinline__ double det_pivots(double (&a)[NO][NO], int n) {
 // electron-count bracket are unrolled (guards on the actual counts) so that
 // every array stays in registers; the pair terms are visited in eval_walker's
 // order.
-template <int NE, int NO>
+template <int NE, int NO, bool X2 = false>
 __device__ __forceinline__ double logpsi_walker(const WfDev& wf, const GenShared& g, const double (&r)[NE][3]) {
   const int N = wf.n_elec, nu = wf.n_up, nd = wf.n_down;
   const double w = wf.bf_w;
@@ -522,7 +629,10 @@ __device__ __forceinline__ double logpsi_walker(const WfDev& wf, const GenShared
   double phi[NE][NO];
 #pragma unroll
   for (int q = 0; q < NE; ++q) {
-    if (q < N) mo_values<NO>(wf, g, rt[q], n_occ, phi[q]);
+    if (q < N) {
+      if constexpr (X2) mo_channels_x2<NO>(wf, g, rt[q], n_occ, phi[q], nullptr, nullptr, false);
+      else mo_values<NO>(wf, g, rt[q], n_occ, phi[q]);
+    }
     else
 #pragma unroll
       for (int m = 0; m < NO; ++m) phi[q][m] = 0.0;
@@ -554,7 +664,7 @@ __device__ __forceinline__ double logpsi_walker(const WfDev& wf, const GenShared
 // Local energy and log|Psi| of one walker.  T = double, or Dual<K> with the
 // nuclear coordinates R seeded for forces.  NE >= n_elec, NO >= occupied
 // orbitals per spin.
-template <typename T, int NE, int NO>
+template <typename T, int NE, int NO, bool X2 = false>
 __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&r)[NE][3], const T (*R)[3],
                             bool kinetic, T& eloc, T& logpsi, int seeded = -1) {
   const int N = wf.n_elec, nu = wf.n_up;
@@ -570,8 +680,10 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
   BackflowTables<NE> BT;
   if (kinetic && w != 0.0) backflow_tables<NE>(r, P, N, w, BT);
   T phi[NE][NO], dphi[NE][NO][3], hphi[NE][NO][6];
-  for (int i = 0; i < N; ++i)
-    mo_channels<T, NO>(wf, g, rt[i], R, n_occ, phi[i], dphi[i], hphi[i], kinetic, seeded);
+  for (int i = 0; i < N; ++i) {
+    if constexpr (X2) mo_channels_x2<NO>(wf, g, rt[i], n_occ, phi[i], dphi[i], hphi[i], kinetic);
+    else mo_channels<T, NO>(wf, g, rt[i], R, n_occ, phi[i], dphi[i], hphi[i], kinetic, seeded);
+  }
   // reference determinants (the expansion holds one determinant)
   T ainv[2][NO][NO];
   T logdet = T(log(fabs(wf.det_w[0])));
@@ -677,7 +789,7 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
 // Z = S^-1 PMP collapse to 2 det(PMP) / R; for k = 1 they cancel), where
 // tr1 = Tr X1_occ, trsq = Tr(X1_occ^2), tr2 = Tr X2_occ.  Then
 // Eqs. nabla_sigma / delta_sigma with the up-down cross term.
-template <int NE, int NC>
+template <int NE, int NC, bool X2 = false>
 __device__ void eval_walker_md(const WfDev& wf, const GenShared& g, const double (&r)[NE][3], bool kinetic,
                                double& eloc, double& logpsi) {
   constexpr int NS = 4;  // occupied orbitals per spin
@@ -692,7 +804,10 @@ __device__ void eval_walker_md(const WfDev& wf, const GenShared& g, const double
   if (kinetic) backflow_tables<NE>(r, P, N, w, BT);
   const int ncol = wf.p_hi[0] > wf.p_hi[1] ? wf.p_hi[0] : wf.p_hi[1];
   double phi[NE][NC], dphi[NE][NC][3], hphi[NE][NC][6];
-  for (int i = 0; i < N; ++i) mo_channels<double, NC>(wf, g, rt[i], wf.atom_xyz, ncol, phi[i], dphi[i], hphi[i], kinetic);
+  for (int i = 0; i < N; ++i) {
+    if constexpr (X2) mo_channels_x2<NC>(wf, g, rt[i], ncol, phi[i], dphi[i], hphi[i], kinetic);
+    else mo_channels<double, NC>(wf, g, rt[i], wf.atom_xyz, ncol, phi[i], dphi[i], hphi[i], kinetic);
+  }
   // reference inverses and the value tables t_p
   double ainv[2][NS][NS], tv[2][NS][NC], det0 = 1.0;
   for (int s = 0; s < 2; ++s) {
@@ -844,6 +959,7 @@ __device__ __forceinline__ void stage_tables(const WfDev& wf, GenShared& g, unsi
   g.sh = sh;
   g.pw = pw;
   g.C = wf.mo64;
+  g.Cx2 = wf.mo_x2n;
 }
 
 inline size_t gen_table_bytes(const WfDev& wf) {

@@ -102,6 +102,8 @@ struct WfDev {
   const float4* oz_bound;
   int tc_value;            // 1: the FP32X2 form's Metropolis value path runs k_ao_mo_tc (FP32 AOs)
   const float* exp_tab;    // [64][2] 2^(j/64) as pairs: exp of the FP32X2 form
+  const float2* mo_x2n;    // [n_ao][n_mo] MO table (angular factors folded in) as pairs, AO order
+  int gen_x2;              // 1: the general (backflow) kernels evaluate the orbitals in pairs of FP32
   const int* exc;          // [2][kMaxExc][5] rank, h1, h2, p1, p2
   const int* det_idx;      // [n_det][2] excitation index per spin
   const int* det_orig;     // [n_det] index of each (sorted) determinant in the caller's order

@@ -99,14 +99,15 @@ class Server:
 
 def build_mix(precision: str, molecules=("h2", "lih", "li2", "co"), n_bonds: int = 20, device: int = 0):
     """Wavefunctions of the serving mix: each molecule at n_bonds bond lengths
-    from 0.6x to 2.5x equilibrium.  Backflow (Li2) runs in the FP64 form."""
+    from 0.6x to 2.5x equilibrium.  Backflow (Li2) has the FP64 and FP32X2
+    forms only: it runs in FP32X2 in the FP32X2 mix and in FP64 otherwise."""
     import qmc_inputs as qi
 
     wfs = {}
     for name in molecules:
         base = qi.make_molecule(name)
         for k, s in enumerate(np.linspace(0.6, 2.5, n_bonds)):
-            prec = "fp64" if base.backflow_w != 0.0 else precision
+            prec = precision if base.backflow_w == 0.0 or precision in ("fp64", "fp32x2") else "fp64"
             wfs[(name, k)] = Wavefunction(base.with_bond_scale(float(s)), precision=prec, device=device)
     return wfs
 

@@ -8,7 +8,7 @@ import torch
 import qmc_inputs as qi
 from oracle import qmc_oracle as O
 
-from gpu_common import fp64_check, oracle_reference
+from gpu_common import fp64_check, gated_check, oracle_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +37,23 @@ def test_li2_backflow_local_energy_parity(pkg):
     st = fp64_check(e.cpu().numpy(), E_ref, sens)
     assert np.all(np.abs(lp.cpu().numpy() - lp_ref) <= 1e-10 * np.maximum(1.0, np.abs(lp_ref)))
     print("li2 backflow fp64", st)
+
+
+@pytest.mark.parametrize("n_det,W", [(1, 700), (20, 300)])
+def test_backflow_fp32x2_local_energy_parity(pkg, n_det, W):
+    """Backflow in the FP32X2 form (orbitals in pairs of FP32, everything
+    else FP64): |dE| <= 2e-4 Ha on every walker inside the conditioning cut,
+    log|Psi| within the pairs' rounding of the FP64 value."""
+    mol = qi.make_li2() if n_det == 1 else qi.make_li2(n_mo=6, n_det=n_det)
+    r = qi.walkers(mol, W, seed=41 + n_det)
+    E_ref, lp_ref, sens = oracle_reference(mol, r)
+    wf = pkg.Wavefunction(mol, precision="fp32x2")
+    e, lp = wf.local_energy(_x(r))
+    torch.cuda.synchronize()
+    st = gated_check(e.cpu().numpy(), E_ref, sens)
+    assert np.all(np.abs(lp.cpu().numpy() - lp_ref) <= 1e-9 * np.maximum(1.0, np.abs(lp_ref)) * np.maximum(1.0, sens))
+    print(f"li2 backflow {n_det} det fp32x2", st)
+    wf.close()
 
 
 @pytest.mark.parametrize("n_det", [5, 20, 118])
@@ -76,6 +93,11 @@ def test_backflow_rejected_outside_its_scope(pkg):
 
     with pytest.raises(QmcError):
         pkg.Wavefunction(qi.make_li2(), precision="mixed_tf32")
+    # the FP32X2 form has backflow, but gradients stay FP64
+    wf = pkg.Wavefunction(qi.make_li2(), precision="fp32x2")
+    with pytest.raises(QmcError):
+        wf.energy_grad(_x(qi.walkers(qi.make_li2(), 16, seed=1)))
+    wf.close()
     mol = qi.make_co(n_det=3)
     mol.backflow_w = 0.1
     with pytest.raises(QmcError):

@@ -171,8 +171,8 @@ def test_proposal_gaussians_match_library_box_muller(pkg):
     wf.close()
 
 
-@pytest.mark.parametrize("name", ["lih", "co"])
-@pytest.mark.parametrize("precision", ["fp32x2", "mixed_tf32"])
+@pytest.mark.parametrize("name,precision", [("lih", "fp32x2"), ("lih", "mixed_tf32"), ("co", "fp32x2"),
+                                            ("co", "mixed_tf32"), ("li2", "fp32x2")])
 def test_reduced_precision_chain_mean_matches_fp64_chain(pkg, name, precision):
     """The Metropolis chain of a reduced-precision form samples the same
     |Psi|^2 as the FP64 form: from the same walkers and Philox key, its mean
