@@ -41,9 +41,9 @@ METRIC = "walker local-energy evals/s (CO, 14 e-) vs FP64 plain; p99 request lat
 UNIT = "walker-evals/s"
 WORKLOAD = "CO 14e- 58 GTO 14 MO 100 det, 262144 walkers"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.26 TF)
-# DRAM bytes (read + write) per walker of the mixed-form k_det launch, from an ncu capture of that
-# kernel on 131,072 CO walkers (419.6 MB); set to None whenever the kernel changes.
-DET_TRAFFIC_BYTES_PER_WALKER = (414.371072e6 + 5.260032e6) / 131072  # ncu dram read+write of k_det (131,072 walkers)
+# DRAM bytes (read + write) per walker of the k_det launch, from an ncu capture of that kernel in the
+# FP32X2 form on 131,072 CO walkers (418.6 MB per launch); set to None whenever the kernel changes.
+DET_TRAFFIC_BYTES_PER_WALKER = (414.384128e6 + 4.216064e6) / 131072
 
 
 def det_stage_flops(mol) -> float:
