@@ -367,6 +367,13 @@ qmc_status build_tables(qmc_wf* wf) {
     for (int p = 0; p < q.n_prim; ++p) {
       q.expo_lo[p] = (float)(q.expo[p] - (double)q.expo_f[p]);
       q.coef_lo[p] = (float)(q.coef[p] - (double)q.coef_f[p]);
+      // 2 alpha c and 4 alpha^2 c: the GTO kinetic radial sums as pair
+      // multiply-accumulates with e^(-alpha r^2)
+      const double c2 = 2.0 * q.expo[p] * q.coef[p], c4 = 4.0 * q.expo[p] * q.expo[p] * q.coef[p];
+      q.c2a_f[p] = (float)c2;
+      q.c2a_lo[p] = (float)(c2 - (double)q.c2a_f[p]);
+      q.c4a_f[p] = (float)c4;
+      q.c4a_lo[p] = (float)(c4 - (double)q.c4a_f[p]);
     }
     std::vector<int> canon(q.n_ao, -1);
     bool complete = q.l <= 2 && q.n_ao == (q.l + 1) * (q.l + 2) / 2;

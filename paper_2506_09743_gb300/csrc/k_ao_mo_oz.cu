@@ -419,30 +419,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
             f2 = (qq * qq - irho * irho * (float)sh.kn) * f;
           }
         } else {
+          // per primitive e = e^(-alpha r^2) and, as pair multiply-accumulates
+          // (normalised once per shell), f = sum c e, t1 = sum 2 alpha c e,
+          // t2 = sum 4 alpha^2 c e
           f32x2 t1(0.f), t2(0.f);
-          auto prim = [&](const f32x2& al, const f32x2& ce) {
-            f += ce;
+          for (int p = 0; p < sh.n_prim; ++p) {
+            const f32x2 e = exp_x2(-(f32x2(sh.expo_f[p], sh.expo_lo[p]) * r2), xtab);
+            mac_x2(f, f32x2(sh.coef_f[p], sh.coef_lo[p]), e);
             if (NCH == 2) {
-              const f32x2 t = (al * ce) * 2.0f;
-              t1 += t;
-              t2 += (al * t) * 2.0f;
+              mac_x2(t1, f32x2(sh.c2a_f[p], sh.c2a_lo[p]), e);
+              mac_x2(t2, f32x2(sh.c4a_f[p], sh.c4a_lo[p]), e);
             }
-          };
-          // primitives two at a time: two independent exponentials in flight
-          // (the sums still take the primitives in order)
-          int p = 0;
-          for (; p + 1 < sh.n_prim; p += 2) {
-            const f32x2 al0(sh.expo_f[p], sh.expo_lo[p]), al1(sh.expo_f[p + 1], sh.expo_lo[p + 1]);
-            const f32x2 e0 = exp_x2(-(al0 * r2), xtab), e1 = exp_x2(-(al1 * r2), xtab);
-            const f32x2 ce0 = f32x2(sh.coef_f[p], sh.coef_lo[p]) * e0;
-            const f32x2 ce1 = f32x2(sh.coef_f[p + 1], sh.coef_lo[p + 1]) * e1;
-            prim(al0, ce0);
-            prim(al1, ce1);
           }
-          if (p < sh.n_prim) {
-            const f32x2 al(sh.expo_f[p], sh.expo_lo[p]);
-            prim(al, f32x2(sh.coef_f[p], sh.coef_lo[p]) * exp_x2(-(al * r2), xtab));
-          }
+          f = normalize_x2(f);
+          t1 = normalize_x2(t1);
+          t2 = normalize_x2(t2);
           if (NCH == 2) {
             g1 = -t1;
             f2 = r2 * t2 - t1;

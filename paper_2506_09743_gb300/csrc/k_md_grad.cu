@@ -30,8 +30,9 @@
 // scratch; k_md_rows (one thread per electron row) evaluates the AOs and
 // adds the coefficient, exponent and backflow terms.  Per-walker values are
 // weighted (estimator 2 (E_L - E_v) / M, one, or E_L) and summed per warp by
-// shuffles in a fixed order, per block over the warps in order, and over the
-// blocks by k_row_sums: the result is bitwise reproducible.
+// shuffles in a fixed order (a butterfly reduce-scatter for the outputs of
+// two AOs at a time), per block over the warps in order, and over the blocks
+// by k_row_sums: the result is bitwise reproducible.
 #include "general_eval.cuh"
 
 namespace qmc {
@@ -187,6 +188,24 @@ __global__ void __launch_bounds__(kMdThreads) k_md_gamma(WfDev wf, const double*
   flush_acc(acc, n_param, partial, ld_partial, blockIdx.x);
 }
 
+// Sum over the warp's lanes of 32 values per lane: afterwards lane L holds the
+// sum of every lane's v[L].  Butterfly reduce-scatter in five exchange
+// stages (31 adds per lane for 32 outputs, instead of five per output for a
+// per-output tree); the order of the additions is fixed.
+__device__ __forceinline__ double reduce_scatter32(double (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      const double send = upper ? v[k] : v[k + s];
+      const double keep = upper ? v[k + s] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
 __global__ void __launch_bounds__(kMdThreads) k_md_rows(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                          int64_t ldw, const double* __restrict__ gam, int64_t ldm,
                                                          const double* __restrict__ e_loc,
@@ -234,45 +253,80 @@ __global__ void __launch_bounds__(kMdThreads) k_md_rows(WfDev wf, const double* 
       const double dx = r[0] - wf.atom_xyz[sh.atom][0], dy = r[1] - wf.atom_xyz[sh.atom][1],
                    dz = r[2] - wf.atom_xyz[sh.atom][2];
       const double r2 = dx * dx + dy * dy + dz * dz, rho = sqrt(r2);
-      double f, g1, f2;
-      radial(sh, r2, rho, f, g1, f2);
+      // radial factor, f'/rho, and per primitive the exponent derivative of
+      // its normalised term: d(N_p e^(-alpha r^2)) / d alpha = term ((3/4 + l/2)/alpha - r^2)
+      double f = 0.0, g1 = 0.0, dexp[QMC_MAX_PRIM];
+      if (sh.kind == 0) {
+        double rk = 1.0;
+        for (int k = 0; k < sh.kn; ++k) rk *= rho;
+        f = sh.coef[0] * rk * exp(-sh.expo[0] * rho);
+        g1 = (sh.kn / rho - sh.expo[0]) * f / rho;
+        const int nq = sh.kn + sh.l + 1;
+        dexp[0] = f * ((nq + 0.5) / sh.expo[0] - rho);
+      } else {
+        for (int p = 0; p < sh.n_prim; ++p) {
+          const double al = sh.expo[p];
+          const double term = sh.coef[p] * exp(-al * r2);
+          f += term;
+          g1 -= 2.0 * al * term;
+          dexp[p] = term * ((0.75 + 0.5 * sh.l) / al - r2);
+        }
+      }
       const double dv[3] = {dx, dy, dz};
-      for (int k = 0; k < sh.n_ao; ++k) {
-        const int b = sh.ao_first + k;
-        const int pw = g.pw[b];
-        const int pa[3] = {pw & 15, (pw >> 4) & 15, (pw >> 8) & 15};
-        const double Pm = mono(dx, dy, dz, pa[0], pa[1], pa[2]);
-        const double* Cb = g.C + (size_t)b * nmo;  // angular factor folded in
-        double ub = 0.0;
-        for (int m = 0; m < nmo; ++m) {
-          ub += Cb[m] * G[m];
-          const double v = warp_sum(wt * ang[b] * Pm * f * G[m]);
-          if (lane == 0) my[off_c + b * nmo + m] += v;
-        }
-        const int p0 = prim_start[b];
-        if (sh.kind == 0) {
-          const int nq = sh.kn + pa[0] + pa[1] + pa[2] + 1;
-          const double v = warp_sum(wt * ub * Pm * f * ((nq + 0.5) / sh.expo[0] - rho));
-          if (lane == 0) my[p0] += v;
-        } else {
-          for (int p = 0; p < sh.n_prim; ++p) {
-            const double al = sh.expo[p];
-            const double term = sh.coef[p] * exp(-al * r2);
-            const double v = warp_sum(wt * ub * Pm * term * ((0.75 + 0.5 * sh.l) / al - r2));
-            if (lane == 0) my[p0 + p] += v;
+      // AOs two at a time: MO-coefficient terms of AO k in slots [16 (k & 1), +16)
+      for (int k0 = 0; k0 < sh.n_ao; k0 += 2) {
+        double vc[32];
+        double ub[2] = {0.0, 0.0}, Pm[2] = {0.0, 0.0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = k0 + h;
+          const bool has = k < sh.n_ao;
+          const int b = has ? sh.ao_first + k : sh.ao_first;
+          const int pw = g.pw[b];
+          const int pa[3] = {pw & 15, (pw >> 4) & 15, (pw >> 8) & 15};
+          Pm[h] = has ? mono(dx, dy, dz, pa[0], pa[1], pa[2]) : 0.0;
+          const double sb = wt * ang[b] * Pm[h] * f;
+          const double* Cb = g.C + (size_t)b * nmo;  // angular factor folded in
+          double u = 0.0;
+#pragma unroll
+          for (int m = 0; m < kMdNM; ++m) {
+            vc[16 * h + m] = sb * G[m];
+            if (m < nmo) u += Cb[m] * G[m];
+          }
+          ub[h] = has ? u : 0.0;
+          // grad (P f) . sum_j (r_a - r_j) / r_aj
+          if (has) {
+            double gd = 0.0;
+            for (int d = 0; d < 3; ++d) {
+              double dP = 0.0;
+              if (pa[d] > 0) {
+                const int e[3] = {pa[0] - (d == 0), pa[1] - (d == 1), pa[2] - (d == 2)};
+                dP = pa[d] * mono(dx, dy, dz, e[0], e[1], e[2]);
+              }
+              gd += (f * dP + Pm[h] * g1 * dv[d]) * drt[d];
+            }
+            gw += u * gd;
           }
         }
-        // grad (P f) . sum_j (r_a - r_j) / r_aj
-        double gd = 0.0;
-        for (int d = 0; d < 3; ++d) {
-          double dP = 0.0;
-          if (pa[d] > 0) {
-            const int e[3] = {pa[0] - (d == 0), pa[1] - (d == 1), pa[2] - (d == 2)};
-            dP = pa[d] * mono(dx, dy, dz, e[0], e[1], e[2]);
-          }
-          gd += (f * dP + Pm * g1 * dv[d]) * drt[d];
+        const double oc = reduce_scatter32(vc, lane);
+        {
+          const int k = k0 + (lane >> 4), m = lane & 15;
+          if (k < sh.n_ao && m < nmo) my[off_c + (sh.ao_first + k) * nmo + m] += oc;
         }
-        gw += ub * gd;
+        // exponent terms of the same two AOs: slots [8 h + p]
+        double ve[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) ve[t] = 0.0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const double qb = wt * ub[h] * Pm[h];
+          for (int p = 0; p < sh.n_prim && p < QMC_MAX_PRIM; ++p) ve[8 * h + p] = qb * dexp[p];
+        }
+        const double oe = reduce_scatter32(ve, lane);
+        {
+          const int h = lane >> 3, p = lane & 7, k = k0 + h;
+          if (h < 2 && k < sh.n_ao && p < (sh.kind == 0 ? 1 : sh.n_prim)) my[prim_start[sh.ao_first + k] + p] += oe;
+        }
       }
     }
     const double v = warp_sum(wt * gw);

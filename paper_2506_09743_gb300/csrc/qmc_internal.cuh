@@ -47,6 +47,8 @@ struct ShellDev {
   float coef_f[QMC_MAX_PRIM];  // (double->float runs on the FP64 pipe)
   float expo_lo[QMC_MAX_PRIM];  // expo - expo_f and coef - coef_f as floats: the
   float coef_lo[QMC_MAX_PRIM];  // pairs (hi, lo) of the FP32X2 form (2^-48)
+  float c2a_f[QMC_MAX_PRIM], c2a_lo[QMC_MAX_PRIM];  // 2 alpha c as pairs (GTO kinetic sums)
+  float c4a_f[QMC_MAX_PRIM], c4a_lo[QMC_MAX_PRIM];  // 4 alpha^2 c as pairs
 };
 
 // Bins of the squared electron-nucleus distance for the FP32X2 row-scale
