@@ -44,6 +44,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.
 # DRAM bytes (read + write) per walker of the k_det launch, from an ncu capture of that kernel in the
 # FP32X2 form on 131,072 CO walkers (418.6 MB per launch); set to None whenever the kernel changes.
 DET_TRAFFIC_BYTES_PER_WALKER = (414.384128e6 + 4.216064e6) / 131072
+# DRAM bytes (read + write) per walker of the k_ao_mo_oz launch, from an ncu capture of that kernel on
+# 131,072 CO walkers (66.5 MB read, 408.6 MB written per launch); None whenever the kernel changes.
+OZ_TRAFFIC_BYTES_PER_WALKER = (66.5216e6 + 408.638976e6) / 131072
 
 
 def det_stage_flops(mol) -> float:
@@ -175,17 +178,26 @@ def general_eloc_ops(mol) -> dict:
 
 def oz_stage_alu_ops(mol) -> float:
     """Algorithmic FP32/ALU operations per walker of k_ao_mo_oz, the FP32X2
-    AO stage with the contraction on the tensor cores: the AO evaluation of
-    x2_stage_ops (everything but its multiply-accumulates), per AO value and
-    channel the digit slicing (oz_digits: 26 FP32 operations, 2 for the row
-    scale, 6 BF16 packs), per MO and channel the recombination of the six
-    classes (oz_combine: 44).  The contraction itself runs on the tensor
-    pipe (BF16 digit products, exact FP32 sums) and is not counted here;
-    row-scale bounds, addressing and stores are not counted either."""
+    AO stage with the contraction on the tensor cores.  Per electron: per
+    Gaussian primitive of each shell -alpha rho^2 (7), the exponential (69)
+    and three pair multiply-accumulates for the value and the two kinetic
+    radial sums (3 x 12, coefficients 2 alpha c and 4 alpha^2 c folded on the
+    host); per shell their three normalisations (3 x 3); per AO its value and
+    kinetic channel (32, as x2_stage_ops); per AO value and channel the digit
+    slicing (oz_digits: 26 FP32 operations, 2 for the row scale, 6 BF16
+    packs); per MO and channel the recombination of the six classes
+    (oz_combine: 44).  The contraction itself runs on the tensor pipe (BF16
+    digit products, exact FP32 sums) and is not counted here; row-scale
+    bounds, addressing and stores are not counted either."""
     o = X2_OPS
-    contraction = 2 * mol.n_ao * mol.n_mo * o["mac"]
-    ao_eval = x2_stage_ops(mol) / mol.n_elec - contraction
-    per_row = ao_eval + 2 * mol.n_ao * (26 + 2 + 6) + 2 * mol.n_mo * 44
+    shells = {}
+    for b in range(mol.n_ao):
+        key = (int(mol.ao_atom[b]), int(sum(mol.ao_pow[b][:3])), tuple(mol.prim_exp[mol.ao_prim_start[b]:mol.ao_prim_start[b + 1]]))
+        shells[key] = int(mol.ao_prim_start[b + 1] - mol.ao_prim_start[b])
+    per_prim = o["mul"] + o["exp"] + 3 * o["mac"]
+    per_ao = o["mul"] + 2 * o["mul"] + o["add"]
+    per_row = (sum(shells.values()) * per_prim + len(shells) * 9 + mol.n_ao * per_ao
+               + 2 * mol.n_ao * (26 + 2 + 6) + 2 * mol.n_mo * 44)
     return float(mol.n_elec * per_row)
 
 
@@ -798,7 +810,9 @@ def main():
     det_rate = flops_det / (det_ms / 1e3) / 1e12
     roofline = {"kernel": "k_ao_mo_oz (AOs in pairs of FP32, exact digit-sliced contraction on tcgen05; FP32X2 form)",
                 "bound": "alu", "achieved": oz_rate, "peak": FP32_PEAK_TOPS, "unit": "T FP32 ops/s",
-                "frac": oz_rate / FP32_PEAK_TOPS, "traffic": None,
+                "frac": oz_rate / FP32_PEAK_TOPS,
+                "traffic": None if OZ_TRAFFIC_BYTES_PER_WALKER is None else OZ_TRAFFIC_BYTES_PER_WALKER * W,
+                "traffic_note": "ncu dram read + write of one launch on 131,072 walkers, scaled by walkers",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (no FP32 figure in the measured peaks)",
                 "peak_measured": fp32_meas, "frac_of_measured": oz_rate / fp32_meas if fp32_meas else None,
                 "ops_per_launch": oz_ops,

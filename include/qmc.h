@@ -289,7 +289,8 @@ qmc_status qmc_sample(qmc_wf* wf, double* walkers, int64_t n_walkers, int64_t ld
  * Scope: FP64 form and either (a) one determinant, <= 8 electrons, <= 4 per
  * spin (gradient and forces; backflow allowed) or (b) no backflow, <= 8
  * electrons per spin, <= 16 orbitals, <= 128 distinct excitations per spin
- * (gradient only: forces must be NULL); no many-body Jastrow
+ * (gradient only: forces must be NULL).  A many-body Jastrow takes path (b)
+ * (its parameters are in the gradient; forces must be NULL)
  * (QMC_ERR_UNSUPPORTED otherwise).
  * walkers: device [3N][ldw].  e_stats: host [2] (mean, variance).  grad:
  * device [n_param] in qmc_param_layout order, or NULL.  forces: device
@@ -324,7 +325,8 @@ qmc_status qmc_assemble_energy_grad(int64_t n_param, int32_t n_atom, const doubl
                                     double* grad, double* forces);
 
 /* Replace the variational parameters (host [n_param] in qmc_param_layout
- * order: exponents, MO coefficients, CI weights, Jastrow b, backflow w) and
+ * order: exponents, MO coefficients, CI weights, Jastrow b, backflow w, then
+ * the many-body Jastrow's when it is set) and
  * rebuild the device tables.  Waits for work in flight on the device.
  * Exponents must be positive; on error the previous parameters stay. */
 qmc_status qmc_set_params(qmc_wf* wf, const double* params);
@@ -332,7 +334,10 @@ qmc_status qmc_set_params(qmc_wf* wf, const double* params);
 /* Number of variational parameters and the offsets of the gradient blocks:
  * offsets[0] exponents (one per primitive, prim_exp order), [1] MO
  * coefficients (row-major n_ao x n_mo), [2] CI weights, [3] Jastrow b,
- * [4] backflow w, [5] = n_param.  offsets may be NULL. */
+ * [4] backflow w, [5] = n_param.  With a many-body Jastrow (App. D) its
+ * parameters follow the backflow weight, from offsets[4] + 1 to n_param:
+ * K_en (w0, w1, w2) if set, then per K_een term (c, a1, b1, a2, b2, a3, b3).
+ * offsets may be NULL. */
 qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[6]);
 
 /* Many-body Jastrow factor (App. D), added to the Pade electron-electron
@@ -350,8 +355,8 @@ qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[
  * QMC_ERR_UNSUPPORTED with backflow, or when the electron-electron-nucleus
  * tables (per walker: n_elec x n_atom x (6 + 6 n_een) values plus
  * 8 x n_elec (n_elec - 1) / 2 pair terms, four walkers per block) exceed the
- * 227 KB of shared memory of a block; qmc_energy_grad / qmc_optimize refuse a
- * wavefunction that has it (its parameters are not in the gradient layout).
+ * 227 KB of shared memory of a block.  Its parameters join the gradient
+ * layout (qmc_param_layout) and qmc_energy_grad's gradient (no forces).
  * On error the previous Jastrow stays.  Synchronous (rebuilds the device
  * tables). */
 qmc_status qmc_set_manybody_jastrow(qmc_wf* wf, const double* en, int32_t n_een, const double* een);

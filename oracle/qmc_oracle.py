@@ -95,14 +95,21 @@ class Wavefunction:
             self.atom_xyz.requires_grad_(True)
 
     def params(self) -> dict:
-        """Variational parameters in the library's gradient layout order."""
-        return {
+        """Variational parameters in the library's gradient layout order; the
+        many-body Jastrow's (App. D), when present, after the backflow weight:
+        K_en (w0, w1, w2), then the K_een terms row by row."""
+        p = {
             "exponents": self.prim_exp,
             "mo_coeff": self.mo,
             "det_weight": self.det_weight,
             "jastrow_b": self.jastrow_b,
             "backflow_w": self.backflow_w,
         }
+        if self.jastrow_en is not None:
+            p["jastrow_en"] = self.jastrow_en
+        if self.jastrow_een is not None:
+            p["jastrow_een"] = self.jastrow_een
+        return p
 
     @property
     def n_ao(self):

@@ -819,7 +819,9 @@ qmc_status qmc_param_layout(const qmc_wf* wf, int64_t* n_param, int64_t offsets[
   o[2] = o[1] + (int64_t)wf->dev.n_ao * wf->dev.n_mo;
   o[3] = o[2] + wf->dev.n_det;
   o[4] = o[3] + 1;
-  o[5] = o[4] + 1;
+  // with a many-body Jastrow its parameters follow the backflow weight:
+  // K_en (w0, w1, w2), then per K_een term (c, a1, b1, a2, b2, a3, b3)
+  o[5] = o[4] + 1 + (wf->dev.mb_en ? 3 : 0) + 7 * (int64_t)wf->dev.n_een;
   *n_param = o[5];
   if (offsets)
     for (int k = 0; k < 6; ++k) offsets[k] = o[k];
@@ -1198,6 +1200,8 @@ qmc_status qmc_set_params(qmc_wf* wf, const double* params) {
   for (auto& v : h.det_w) v = params[k++];
   h.b = params[k++];
   h.w = params[k++];
+  for (auto& v : h.jen) v = params[k++];
+  for (auto& v : h.jeen) v = params[k++];
   for (size_t q = 0; q < k; ++q)
     if (!std::isfinite(params[q])) {
       wf->spec = old;
@@ -1223,9 +1227,8 @@ static qmc_status grad_setup(qmc_wf* wf, const double* walkers, int64_t n_walker
   if (n_walkers < 1 || ldw < n_walkers) return fail(QMC_ERR_ARG, "need n_walkers >= 1 and ldw >= n_walkers");
   if (!walkers) return fail(QMC_ERR_ARG, "null walkers");
   if (wf->precision != QMC_FP64) return fail(QMC_ERR_UNSUPPORTED, "energy gradients are computed in the FP64 form");
-  if (wf->dev.mb_en || wf->dev.n_een)
-    return fail(QMC_ERR_UNSUPPORTED, "energy gradients do not cover the many-body Jastrow");
-  *md = !general_supported(wf->dev);
+  // the many-body Jastrow's parameters are in the multi-determinant kernels
+  *md = !general_supported(wf->dev) || wf->dev.mb_en || wf->dev.n_een;
   if (*md && !md_grad_supported(wf->dev))
     return fail(QMC_ERR_UNSUPPORTED,
                 "energy gradients need one determinant with <= 8 electrons (<= 4 per spin), or no backflow with "
@@ -1281,7 +1284,8 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
                             &partial, &md);
   if (s) return s;
   if (md && forces)
-    return fail(QMC_ERR_UNSUPPORTED, "forces need one determinant with <= 8 electrons (pass forces = NULL)");
+    return fail(QMC_ERR_UNSUPPORTED,
+                "forces need one determinant with <= 8 electrons and no many-body Jastrow (pass forces = NULL)");
   s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, nullptr, st);
   if (s) return s;
   s = launch_status(launch_mean_var(e_loc, n_walkers, stats, st), "mean/variance");

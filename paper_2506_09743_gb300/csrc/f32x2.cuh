@@ -175,7 +175,12 @@ QMC_HD f32x2 exp_x2(f32x2 x, const float* tab) {
   const int j = n & 63, m = n >> 6;  // floor division for negative n too
   const f32x2 t(tab[2 * j], tab[2 * j + 1]);
   f32x2 v = er * t;
-  // 2^m, m >= -126 here; two factors keep 2^m representable for m = -127 .. -126
+  // times 2^m: one normal factor for m in [-126, 127] (x >= -87 keeps m >= -126);
+  // two factors outside that range
+  if (m >= -126 && m <= 127) {
+    const float sc = x2_bits_f((uint32_t)(m + 127) << 23);
+    return f32x2(x2_mul_rn(v.hi, sc), x2_mul_rn(v.lo, sc));
+  }
   const int m1 = m / 2, m2 = m - m1;
   const float s1 = x2_bits_f((uint32_t)(m1 + 127) << 23), s2 = x2_bits_f((uint32_t)(m2 + 127) << 23);
   v = f32x2(x2_mul_rn(x2_mul_rn(v.hi, s1), s2), x2_mul_rn(x2_mul_rn(v.lo, s1), s2));

@@ -600,7 +600,7 @@ __device__ __forceinline__ double det_pivots(double (&a)[NO][NO], int n) {
 // electron-count bracket are unrolled (guards on the actual counts) so that
 // every array stays in registers; the pair terms are visited in eval_walker's
 // order.
-template <int NE, int NO, bool X2 = false>
+template <int NE, int NO, bool PAIRS = false>
 __device__ __forceinline__ double logpsi_walker(const WfDev& wf, const GenShared& g, const double (&r)[NE][3]) {
   const int N = wf.n_elec, nu = wf.n_up, nd = wf.n_down;
   const double w = wf.bf_w;
@@ -630,7 +630,7 @@ __device__ __forceinline__ double logpsi_walker(const WfDev& wf, const GenShared
 #pragma unroll
   for (int q = 0; q < NE; ++q) {
     if (q < N) {
-      if constexpr (X2) mo_channels_x2<NO>(wf, g, rt[q], n_occ, phi[q], nullptr, nullptr, false);
+      if constexpr (PAIRS) mo_channels_x2<NO>(wf, g, rt[q], n_occ, phi[q], nullptr, nullptr, false);
       else mo_values<NO>(wf, g, rt[q], n_occ, phi[q]);
     }
     else
@@ -664,7 +664,7 @@ __device__ __forceinline__ double logpsi_walker(const WfDev& wf, const GenShared
 // Local energy and log|Psi| of one walker.  T = double, or Dual<K> with the
 // nuclear coordinates R seeded for forces.  NE >= n_elec, NO >= occupied
 // orbitals per spin.
-template <typename T, int NE, int NO, bool X2 = false>
+template <typename T, int NE, int NO, bool PAIRS = false>
 __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&r)[NE][3], const T (*R)[3],
                             bool kinetic, T& eloc, T& logpsi, int seeded = -1) {
   const int N = wf.n_elec, nu = wf.n_up;
@@ -681,7 +681,7 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
   if (kinetic && w != 0.0) backflow_tables<NE>(r, P, N, w, BT);
   T phi[NE][NO], dphi[NE][NO][3], hphi[NE][NO][6];
   for (int i = 0; i < N; ++i) {
-    if constexpr (X2) mo_channels_x2<NO>(wf, g, rt[i], n_occ, phi[i], dphi[i], hphi[i], kinetic);
+    if constexpr (PAIRS) mo_channels_x2<NO>(wf, g, rt[i], n_occ, phi[i], dphi[i], hphi[i], kinetic);
     else mo_channels<T, NO>(wf, g, rt[i], R, n_occ, phi[i], dphi[i], hphi[i], kinetic, seeded);
   }
   // reference determinants (the expansion holds one determinant)
@@ -789,7 +789,7 @@ __device__ void eval_walker(const WfDev& wf, const GenShared& g, const double (&
 // Z = S^-1 PMP collapse to 2 det(PMP) / R; for k = 1 they cancel), where
 // tr1 = Tr X1_occ, trsq = Tr(X1_occ^2), tr2 = Tr X2_occ.  Then
 // Eqs. nabla_sigma / delta_sigma with the up-down cross term.
-template <int NE, int NC, bool X2 = false>
+template <int NE, int NC, bool PAIRS = false>
 __device__ void eval_walker_md(const WfDev& wf, const GenShared& g, const double (&r)[NE][3], bool kinetic,
                                double& eloc, double& logpsi) {
   constexpr int NS = 4;  // occupied orbitals per spin
@@ -805,7 +805,7 @@ __device__ void eval_walker_md(const WfDev& wf, const GenShared& g, const double
   const int ncol = wf.p_hi[0] > wf.p_hi[1] ? wf.p_hi[0] : wf.p_hi[1];
   double phi[NE][NC], dphi[NE][NC][3], hphi[NE][NC][6];
   for (int i = 0; i < N; ++i) {
-    if constexpr (X2) mo_channels_x2<NC>(wf, g, rt[i], ncol, phi[i], dphi[i], hphi[i], kinetic);
+    if constexpr (PAIRS) mo_channels_x2<NC>(wf, g, rt[i], ncol, phi[i], dphi[i], hphi[i], kinetic);
     else mo_channels<double, NC>(wf, g, rt[i], wf.atom_xyz, ncol, phi[i], dphi[i], hphi[i], kinetic);
   }
   // reference inverses and the value tables t_p

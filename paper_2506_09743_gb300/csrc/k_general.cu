@@ -5,7 +5,7 @@
 
 namespace qmc {
 
-template <int NE, int NC, bool X2>
+template <int NE, int NC, bool PAIRS>
 __global__ void __launch_bounds__(128) k_eloc_md(WfDev wf, const double* __restrict__ walkers, int64_t W, int64_t ldw,
                                                  bool kinetic, double* __restrict__ e_loc,
                                                  double* __restrict__ log_psi) {
@@ -17,12 +17,12 @@ __global__ void __launch_bounds__(128) k_eloc_md(WfDev wf, const double* __restr
   double r[NE][3];
   load_walker<NE>(walkers, ldw, w, wf.n_elec, r);
   double e = 0.0, lp = 0.0;
-  eval_walker_md<NE, NC, X2>(wf, g, r, kinetic, e, lp);
+  eval_walker_md<NE, NC, PAIRS>(wf, g, r, kinetic, e, lp);
   if (kinetic) e_loc[w] = e;
   if (log_psi) log_psi[w] = lp;
 }
 
-template <int NE, int NO, bool X2>
+template <int NE, int NO, bool PAIRS>
 __global__ void __launch_bounds__(128, 4) k_eloc_general(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                       int64_t ldw, bool kinetic, double* __restrict__ e_loc,
                                                       double* __restrict__ log_psi) {
@@ -34,12 +34,12 @@ __global__ void __launch_bounds__(128, 4) k_eloc_general(WfDev wf, const double*
   double r[NE][3];
   load_walker<NE>(walkers, ldw, w, wf.n_elec, r);
   double e = 0.0, lp = 0.0;
-  eval_walker<double, NE, NO, X2>(wf, g, r, wf.atom_xyz, kinetic, e, lp);
+  eval_walker<double, NE, NO, PAIRS>(wf, g, r, wf.atom_xyz, kinetic, e, lp);
   if (kinetic) e_loc[w] = e;
   if (log_psi) log_psi[w] = lp;
 }
 
-template <int NE, int NO, bool X2>
+template <int NE, int NO, bool PAIRS>
 __global__ void __launch_bounds__(128) k_logpsi_general(const __grid_constant__ WfDev wf,
                                                         const double* __restrict__ walkers, int64_t W,
                                                         int64_t ldw, double* __restrict__ log_psi) {
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(128) k_logpsi_general(const __grid_constant__ 
   if (w >= W) return;
   double r[NE][3];
   load_walker<NE>(walkers, ldw, w, wf.n_elec, r);
-  log_psi[w] = logpsi_walker<NE, NO, X2>(wf, g, r);
+  log_psi[w] = logpsi_walker<NE, NO, PAIRS>(wf, g, r);
 }
 
 // Sum of W values in a fixed order: [0] mean, [1] mean square deviation.
@@ -94,23 +94,23 @@ bool bf_multidet_supported(const WfDev& wf) {
   return wf.n_elec <= 8 && ns <= 4 && nc <= 8;
 }
 
-template <bool X2>
+template <bool PAIRS>
 static cudaError_t launch_eloc_general_t(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, bool kinetic,
                                          double* e_loc, double* log_psi, dim3 grid, size_t smem, cudaStream_t st) {
   if (wf.n_det > 1) {
     if (!bf_multidet_supported(wf)) return cudaErrorInvalidValue;
-    if (wf.n_elec <= 2) k_eloc_md<2, 8, X2><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
+    if (wf.n_elec <= 2) k_eloc_md<2, 8, PAIRS><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
     else if (wf.n_elec <= 4)
-      k_eloc_md<4, 8, X2><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
-    else k_eloc_md<8, 8, X2><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
+      k_eloc_md<4, 8, PAIRS><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
+    else k_eloc_md<8, 8, PAIRS><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi);
     return cudaGetLastError();
   }
   if (!kinetic && log_psi) {  // value path: log|Psi| alone
-    QMC_GEN_DISPATCH((k_logpsi_general<NE, NO, X2><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, log_psi)));
+    QMC_GEN_DISPATCH((k_logpsi_general<NE, NO, PAIRS><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, log_psi)));
     return cudaGetLastError();
   }
   QMC_GEN_DISPATCH(
-      (k_eloc_general<NE, NO, X2><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi)));
+      (k_eloc_general<NE, NO, PAIRS><<<grid, 128, smem, st>>>(wf, walkers, W, ldw, kinetic, e_loc, log_psi)));
   return cudaGetLastError();
 }
 

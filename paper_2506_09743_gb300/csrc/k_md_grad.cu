@@ -138,6 +138,70 @@ __global__ void __launch_bounds__(kMdThreads) k_md_gamma(WfDev wf, const double*
       const double v = warp_sum(wt * gb);
       if (lane == 0) acc[(size_t)warp * n_param + off_b] += v;
     }
+    // many-body Jastrow (App. D), after the backflow weight:
+    //   K_en = (w0 r + w1 r^2) / (1 + w2 r) over atoms and electrons:
+    //     d/dw0 = r / d, d/dw1 = r^2 / d, d/dw2 = -(w0 r + w1 r^2) r / d^2, d = 1 + w2 r;
+    //   K_een = 1/2 sum over atoms, ordered pairs i != j and terms of
+    //     c f(a1, b1; r_ai) f(a2, b2; r_aj) f(a3, b3; r_ij), f(a, b; r) = a r / (1 + b r):
+    //     df/da = r / (1 + b r), df/db = -a r^2 / (1 + b r)^2
+    if (wf.mb_en || wf.n_een) {
+      int k = off_b + 2;
+      if (wf.mb_en) {
+        double g3[3] = {0.0, 0.0, 0.0};
+        if (live)
+          for (int a = 0; a < wf.n_atom; ++a)
+            for (int i = 0; i < N; ++i) {
+              double d2 = 0.0;
+              for (int c = 0; c < 3; ++c) {
+                const double dd = walkers[(int64_t)(3 * i + c) * ldw + w] - wf.atom_xyz[a][c];
+                d2 += dd * dd;
+              }
+              const double r = sqrt(d2), d = 1.0 + wf.jen[2] * r;
+              g3[0] += r / d;
+              g3[1] += r * r / d;
+              g3[2] -= (wf.jen[0] * r + wf.jen[1] * r * r) * r / (d * d);
+            }
+        for (int q = 0; q < 3; ++q) {
+          const double v = warp_sum(wt * g3[q]);
+          if (lane == 0) acc[(size_t)warp * n_param + k + q] += v;
+        }
+        k += 3;
+      }
+      for (int t = 0; t < wf.n_een; ++t) {
+        const double c = wf.jeen[t][0], a1 = wf.jeen[t][1], b1 = wf.jeen[t][2], a2 = wf.jeen[t][3],
+                     b2 = wf.jeen[t][4], a3 = wf.jeen[t][5], b3 = wf.jeen[t][6];
+        double g7[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (live)
+          for (int a = 0; a < wf.n_atom; ++a)
+            for (int i = 0; i < N; ++i)
+              for (int j = 0; j < N; ++j) {
+                if (i == j) continue;
+                double x2 = 0.0, y2 = 0.0, z2 = 0.0;
+                for (int q = 0; q < 3; ++q) {
+                  const double ri = walkers[(int64_t)(3 * i + q) * ldw + w], rj = walkers[(int64_t)(3 * j + q) * ldw + w];
+                  x2 += (ri - wf.atom_xyz[a][q]) * (ri - wf.atom_xyz[a][q]);
+                  y2 += (rj - wf.atom_xyz[a][q]) * (rj - wf.atom_xyz[a][q]);
+                  z2 += (ri - rj) * (ri - rj);
+                }
+                const double x = sqrt(x2), y = sqrt(y2), z = sqrt(z2);
+                const double d1 = 1.0 + b1 * x, d2 = 1.0 + b2 * y, d3 = 1.0 + b3 * z;
+                const double h1 = x / d1, h2 = y / d2, h3 = z / d3;  // df/da
+                const double f1 = a1 * h1, f2 = a2 * h2, f3 = a3 * h3;
+                g7[0] += 0.5 * f1 * f2 * f3;
+                g7[1] += 0.5 * c * h1 * f2 * f3;
+                g7[2] -= 0.5 * c * a1 * h1 * h1 * f2 * f3;
+                g7[3] += 0.5 * c * f1 * h2 * f3;
+                g7[4] -= 0.5 * c * f1 * a2 * h2 * h2 * f3;
+                g7[5] += 0.5 * c * f1 * f2 * h3;
+                g7[6] -= 0.5 * c * f1 * f2 * a3 * h3 * h3;
+              }
+        for (int q = 0; q < 7; ++q) {
+          const double v = warp_sum(wt * g7[q]);
+          if (lane == 0) acc[(size_t)warp * n_param + k + q] += v;
+        }
+        k += 7;
+      }
+    }
     if (!live) continue;
     // Gamma per spin
     for (int s = 0; s < 2; ++s) {
@@ -336,7 +400,7 @@ __global__ void __launch_bounds__(kMdThreads) k_md_rows(WfDev wf, const double* 
 }
 
 bool md_grad_supported(const WfDev& wf) {
-  if (wf.bf_w != 0.0 || wf.mb_en || wf.n_een) return false;
+  if (wf.bf_w != 0.0) return false;
   const int ns = wf.n_up > wf.n_down ? wf.n_up : wf.n_down;
   if (ns > kMdNS || wf.n_mo > kMdNM || wf.n_exc[0] > 128 || wf.n_exc[1] > 128) return false;
   return true;

@@ -59,6 +59,8 @@ std::vector<double> current_params(const qmc_wf* wf) {
   p.insert(p.end(), h.det_w.begin(), h.det_w.end());
   p.push_back(h.b);
   p.push_back(h.w);
+  p.insert(p.end(), h.jen.begin(), h.jen.end());
+  p.insert(p.end(), h.jeen.begin(), h.jeen.end());
   return p;
 }
 

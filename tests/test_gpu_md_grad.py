@@ -103,3 +103,52 @@ def test_full_size_co_multidet_gradient_runs(pkg):
     ci = g[off[2]:off[3]]
     assert abs(float(np.dot(d, ci))) <= 1e-9 * max(1.0, float(np.abs(d * ci).sum())), float(np.dot(d, ci))
     wf.close()
+
+
+@pytest.mark.parametrize("name,n_det,W", [("co", 20, 40), ("lih", 1, 100)])
+def test_manybody_jastrow_gradient_matches_oracle(pkg, name, n_det, W):
+    """The many-body Jastrow's parameters (App. D: K_en and five K_een terms)
+    join the gradient after the backflow weight; the whole gradient matches
+    the oracle's autograd gradient at 1e-8 of its largest component, the
+    many-body block at 1e-7 of its own."""
+    base = qi.make_co(n_det=n_det) if name == "co" else qi.make_lih()
+    mol = qi.with_manybody_jastrow(base)
+    r = qi.walkers(mol, W, seed=69)
+    Ev, var, g_ref = _oracle(mol, r)
+    wf = pkg.Wavefunction(mol, precision="fp64")
+    n, off = wf.param_layout()
+    assert n == off[4] + 1 + 3 + 7 * 5 == g_ref.shape[0]
+    e_mean, _, grad, _ = wf.energy_grad(_x(r), want_forces=False)
+    g = grad.cpu().numpy()
+    assert abs(e_mean - Ev) <= 1e-10 * max(1.0, abs(Ev))
+    err = np.abs(g - g_ref)
+    assert err.max() <= 1e-8 * np.abs(g_ref).max(), (err.max(), int(err.argmax()))
+    mb = slice(off[4] + 1, n)
+    assert err[mb].max() <= 1e-7 * np.abs(g_ref[mb]).max(), (err[mb], g_ref[mb])
+    with pytest.raises(Exception):
+        wf.energy_grad(_x(r), want_forces=True)
+    wf.close()
+
+
+def test_set_params_covers_the_manybody_jastrow(pkg):
+    """qmc_set_params with changed many-body parameters gives the energies of
+    a wavefunction built with them (bitwise)."""
+    mol = qi.with_manybody_jastrow(qi.make_co(n_det=20))
+    r = qi.walkers(mol, 256, seed=70)
+    wf = pkg.Wavefunction(mol, precision="fp64")
+    n, off = wf.param_layout()
+    en, een = np.asarray(mol.jastrow_en), np.asarray(mol.jastrow_een)
+    p = np.concatenate([mol.prim_exp, mol.mo_coeff.reshape(-1), mol.det_weight, [mol.jastrow_b, mol.backflow_w],
+                        en, een.reshape(-1)])
+    assert p.shape[0] == n
+    en2, een2 = en * 1.1, een.copy()
+    een2[:, 0] *= -0.7
+    p[off[4] + 1:] = np.concatenate([en2, een2.reshape(-1)])
+    wf.set_params(p)
+    e1, _ = wf.local_energy(_x(r))
+    mol2 = qi.with_manybody_jastrow(qi.make_co(n_det=20))
+    mol2.jastrow_en, mol2.jastrow_een = en2, een2
+    e2, _ = pkg.Wavefunction(mol2, precision="fp64").local_energy(_x(r))
+    torch.cuda.synchronize()
+    assert torch.equal(e1, e2)
+    wf.close()

@@ -399,12 +399,14 @@ def test_rotation_invariance_s_basis():
 # gradient and force estimators against finite differences
 
 
-@pytest.mark.parametrize("name", ["li2", "co_sd20"])
+@pytest.mark.parametrize("name", ["li2", "co_sd20", "lih_mbj"])
 def test_grad_log_psi_finite_difference(name):
     """The oracle's autograd d log|Psi| / d theta against central
-    differences, for the backflow single determinant (Li2) and a 20-determinant
-    CO expansion (CI weights, occupied and virtual MO columns)."""
-    mol = qi.make_li2() if name == "li2" else qi.make_co(n_det=20)
+    differences, for the backflow single determinant (Li2), a 20-determinant
+    CO expansion (CI weights, occupied and virtual MO columns) and LiH with
+    the many-body Jastrow of App. D (its K_en and K_een parameters)."""
+    mol = (qi.make_li2() if name == "li2" else qi.make_co(n_det=20) if name == "co_sd20"
+           else qi.with_manybody_jastrow(qi.make_lih()))
     wf = O.Wavefunction(mol, requires_grad=True)
     r = _walkers(mol, 3)
     G = O.grad_log_psi(wf, r)
