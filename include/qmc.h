@@ -67,7 +67,8 @@ typedef enum {
  *                  48 significant bits, on the FP32 pipes), the AO->MO
  *                  contraction exact on the tcgen05 tensor cores (the pairs
  *                  cut into BF16 digits; SIMT pairs when n_mo > 16 or
- *                  n_ao > 96), Coulomb potential in pairs of FP32, FP64
+ *                  n_ao > 96), electron-nucleus potential in pairs of
+ *                  FP32 and electron-electron terms in compensated FP32, FP64
  *                  determinants: MO values within about 2^-43 of |AO||C|, so
  *                  that the local energy matches the FP64 form to 2e-4 Ha on
  *                  every walker away from the nodes (where FP32 AOs leave
@@ -76,8 +77,9 @@ typedef enum {
  *                  MIXED_TF32 stages: FP32-level log|Psi|.
  * Jastrow terms are FP64 in QMC_FP64 and use FP32 pair arithmetic with
  * compensated sums in the other forms; the Coulomb potential is FP64 in
- * QMC_FP64, pairs of FP32 in QMC_FP32X2 and FP32 terms with compensated
- * sums otherwise.  Backflow wavefunctions run in QMC_FP64 and QMC_FP32X2; in
+ * QMC_FP64; in QMC_FP32X2 its electron-nucleus terms are pairs of FP32 and
+ * its electron-electron terms refined FP32 reciprocals with compensated
+ * sums; FP32 terms with compensated sums otherwise.  Backflow wavefunctions run in QMC_FP64 and QMC_FP32X2; in
  * QMC_FP32X2 only their orbitals (AO values, derivatives and the AO->MO
  * contraction, s and p shells) are in pairs of FP32, while the Jastrow
  * factor, the backflow map, the potential, the determinants and the
