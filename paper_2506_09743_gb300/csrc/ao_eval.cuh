@@ -103,14 +103,14 @@ __device__ __forceinline__ void displacement(double rx, double ry, double rz, co
   split_f64(a[2], ah, al); dz = (zh - ah) + (zl - al);
 }
 
-// r - a for a position r and a nucleus a given in FP64, as a pair (both are
-// split into pairs first; the difference is exact to 2^-48 of max(|r|, |a|))
+// r - a for a position r and a nucleus a given in FP64, as a normalised pair:
+// one FP64 subtraction (exact when r is next to a, Sterbenz), then the split.
+// (Splitting r and a first keeps only 2^-48 of |r| in each, which is a
+// relative error of 2^-48 |r| / |r - a| in the difference.)
 __device__ __forceinline__ f32x2 diff_x2(double r, double a) {
-  float rh, rl, ah, al;
-  split_f64(r, rh, rl);
-  split_f64(a, ah, al);
-  const f32x2 s = two_sum(rh, -ah);
-  return two_sum(s.hi, x2_add_rn(s.lo, x2_sub_rn(rl, al)));
+  float h, l;
+  split_f64(r - a, h, l);
+  return fast_two_sum(h, l);
 }
 
 }  // namespace qmc

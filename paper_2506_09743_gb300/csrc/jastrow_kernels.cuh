@@ -28,6 +28,7 @@
 
 #include <type_traits>
 
+#include "ao_eval.cuh"
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -422,9 +423,14 @@ struct KahanF {
 };
 
 // r_i - r_j (d) of two positions held as float pairs, as a pair
+// (the low words' difference is formed exactly too: near a nucleus, where
+// |a - b| is far below |a|, rounding it would cost 2^-48 |a| absolute, a
+// relative error of 2^-48 |a| / |a - b| in 1 / |a - b|)
 __device__ __forceinline__ f32x2 pair_diff_x2(float ah, float al, float bh, float bl) {
   const f32x2 s = two_sum(ah, -bh);
-  return two_sum(s.hi, x2_add_rn(s.lo, x2_sub_rn(al, bl)));
+  const f32x2 t = two_sum(al, -bl);
+  const f32x2 u = two_sum(s.hi, t.hi);
+  return fast_two_sum(u.hi, x2_add_rn(u.lo, x2_add_rn(s.lo, t.lo)));
 }
 // 1 / |v| of a difference vector given as pairs
 __device__ __forceinline__ f32x2 inv_dist_x2(f32x2 x, f32x2 y, f32x2 z) { return rsqrt_x2(x * x + y * y + z * z); }
@@ -504,10 +510,15 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
     for (int i = 0; i < NMAX; ++i)
       if (i < n) {
         if (VX2) {
-          vx = vx - inv_dist_x2(pair_diff_x2(rh[i][0], rl[i][0], ah[0], al[0]),
-                                pair_diff_x2(rh[i][1], rl[i][1], ah[1], al[1]),
-                                pair_diff_x2(rh[i][2], rl[i][2], ah[2], al[2])) *
-                        f32x2(zh, zl);
+          // r_i - R_a from the FP64 coordinates (one FP64 subtraction each,
+          // exact for an electron next to the nucleus), then split: the float
+          // split of a coordinate alone keeps only 2^-48 of |r_i|, which is
+          // 2^-48 |r_i| / |r_i - R_a| of Z / |r_i - R_a|
+          const double* src = copy ? copy : walkers;
+          f32x2 dv[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) dv[d] = diff_x2(src[(int64_t)(3 * i + d) * ldw + w], wf.atom_xyz[a][d]);
+          vx = vx - inv_dist_x2(dv[0], dv[1], dv[2]) * f32x2(zh, zl);
         } else {
           const float dx = (rh[i][0] - ah[0]) + (rl[i][0] - al[0]);
           const float dy = (rh[i][1] - ah[1]) + (rl[i][1] - al[1]);

@@ -400,3 +400,23 @@ def test_set_geometry_matches_fresh_wavefunction(pkg):
     e2, _ = _run(pkg, stretched, r, "fp64")
     torch.cuda.synchronize()
     assert np.allclose(e1.cpu().numpy(), e2, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("name", ["co", "lih"])
+def test_fp32x2_near_a_nucleus(pkg, name):
+    """Electrons within 2^-12 bohr of a nucleus: the FP32X2 tensor-core AO
+    stage takes its row scales from the shells one by one there (outside the
+    per-atom bound tables); such walkers meet the same 2e-4 Ha gate."""
+    from gpu_common import gated_check
+
+    mol = MOLS[name]()
+    r = qi.walkers(mol, 200, seed=23)
+    rng = np.random.default_rng(5)
+    for w in range(0, 200, 2):  # every other walker: one electron next to a nucleus
+        a = w % mol.n_atom
+        i = (w // 2) % mol.n_elec
+        r[w, i] = mol.atom_xyz[a] + rng.uniform(-1e-5, 1e-5, size=3)
+    E_ref, _, sens = oracle_reference(mol, r)
+    E, _ = _run(pkg, mol, r, "fp32x2")
+    st = gated_check(E, E_ref, sens)
+    print(name, "near-nucleus fp32x2", st)
