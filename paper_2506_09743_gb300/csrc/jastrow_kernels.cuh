@@ -440,7 +440,9 @@ __device__ __forceinline__ f32x2 inv_dist_x2(f32x2 x, f32x2 y, f32x2 z) { return
 // would cost 2^-24 of several hundred Ha); the electron-electron terms are
 // FP32 reciprocals refined to about one ulp and summed with compensation
 // (within 2^-22 V_ee: an emulation over 100,000 CO walkers gives at most
-// 4.7e-6 Ha); the Jastrow terms are bounded and stay FP32.
+// 4.7e-6 Ha); pairs closer than 0.01 bohr take 1/r_ij and the Jastrow
+// Laplacian term 2u'/r_ij (both unbounded at coalescence) in FP64; the other
+// Jastrow terms are bounded and stay FP32.
 template <int NMAX, bool MB, bool VX2>
 __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                      int64_t ldw, double* __restrict__ copy,
@@ -465,7 +467,9 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
       g[i][d] = 0.f;
     }
   KahanF J, V, lap;
-  f32x2 vx(0.f, 0.f);  // V in pairs (VX2)
+  f32x2 vx(0.f, 0.f);           // V in pairs (VX2)
+  double Vd = 0.0, lapd = 0.0;  // close pairs in FP64 (VX2)
+  bool any_close = false;
 #pragma unroll
   for (int i = 0; i < NMAX; ++i) {
 #pragma unroll
@@ -474,31 +478,65 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
         const float dx = (rh[i][0] - rh[j][0]) + (rl[i][0] - rl[j][0]);
         const float dy = (rh[i][1] - rh[j][1]) + (rl[i][1] - rl[j][1]);
         const float dz = (rh[i][2] - rh[j][2]) + (rl[i][2] - rl[j][2]);
-        const float d2 = dx * dx + dy * dy + dz * dz;
+        // (the order of the roundings is fixed: the close-pair pass below
+        // repeats this test bit for bit)
+        const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
         const float inv = rsqrtf(d2);  // hardware reciprocal square root and reciprocal:
         const float dist = d2 * inv;    // a few ulp, far inside the FP32 pair-term budget
         const float w0 = ((i < wf.n_up) == (j < wf.n_up)) ? w0p : w0a;
         const float rden = __frcp_rn(1.0f + b * dist);
         const float u1 = w0 * rden * rden;
         J.add(w0 * dist * rden);
+        // FP32X2: electrons within 0.01 bohr (1/r_ij > 100, and the Jastrow
+        // Laplacian 2u'/r_ij as large, where FP32 terms would cost 2^-22 of
+        // them) are left out here and taken in FP64 after the loop
+        const bool close = VX2 && d2 < 1e-4f;
+        any_close |= close;
         if (VX2) {
-          // 1/r_ij to about one ulp (one Newton step on the hardware estimate,
-          // residual by FMA): with compensated sums the electron-electron
-          // potential stays within 2^-22 V_ee (a few 1e-6 Ha), so the pairs
-          // are kept for the electron-nucleus terms, which grow near a nucleus
+          // 1/r_ij to about one ulp (one Newton step on the hardware
+          // estimate, residual by FMA), summed with compensation: each term
+          // within 2^-22 of itself, at most 2.4e-5 Ha
           const float e = fmaf(-d2 * inv, inv, 1.0f);
-          V.add(fmaf(0.5f * inv, e, inv));
+          V.add(close ? 0.0f : fmaf(0.5f * inv, e, inv));
         } else {
           V.add(inv);
         }
         if (deriv) {
-          lap.add(2.0f * (-2.0f * b * u1 * rden + 2.0f * u1 * inv));
+          lap.add(close ? 0.0f : 2.0f * (-2.0f * b * u1 * rden + 2.0f * u1 * inv));
           const float s = u1 * inv;
           g[i][0] += s * dx; g[i][1] += s * dy; g[i][2] += s * dz;
           g[j][0] -= s * dx; g[j][1] -= s * dy; g[j][2] -= s * dz;
         }
       }
     }
+  }
+  if (VX2 && any_close) {
+    // the close pairs (the same FP32 test as above, on the same splits) in
+    // FP64 from the FP64 coordinates and parameters; rare (the cusp), so one
+    // rolled loop over the pairs
+    const double* src = copy ? copy : walkers;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        float d2 = 0.f;
+        for (int d = 0; d < 3; ++d) {
+          float ih, il, jh, jl;
+          split_f64(src[(int64_t)(3 * i + d) * ldw + w], ih, il);
+          split_f64(src[(int64_t)(3 * j + d) * ldw + w], jh, jl);
+          const float v = (ih - jh) + (il - jl);
+          d2 = d == 0 ? __fmul_rn(v, v) : __fmaf_rn(v, v, d2);
+        }
+        if (!(d2 < 1e-4f)) continue;
+        double dd2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          const double v = src[(int64_t)(3 * i + d) * ldw + w] - src[(int64_t)(3 * j + d) * ldw + w];
+          dd2 += v * v;
+        }
+        const double invd = 1.0 / sqrt(dd2), distd = dd2 * invd;
+        const double w0d = ((i < wf.n_up) == (j < wf.n_up)) ? wf.w0_par : wf.w0_anti;
+        const double rdd = 1.0 / (1.0 + wf.jb * distd), u1d = w0d * rdd * rdd;
+        Vd += invd;
+        if (deriv) lapd += 2.0 * (-2.0 * wf.jb * u1d * rdd + 2.0 * u1d * invd);
+      }
   }
   for (int a = 0; a < wf.n_atom; ++a) {
     float ah[3], al[3];
@@ -548,8 +586,8 @@ __global__ void __launch_bounds__(128) k_jastrow_f32(WfDev wf, const double* __r
         }
   }
   jscal[w] = J.value();
-  jscal[ldm + w] = lap.value();
-  jscal[2 * ldm + w] = (VX2 ? widen(vx) + V.value() : V.value()) + wf.vnn;
+  jscal[ldm + w] = VX2 ? lap.value() + lapd : lap.value();
+  jscal[2 * ldm + w] = (VX2 ? widen(vx) + V.value() + Vd : V.value()) + wf.vnn;
 }
 
 // Launch one kernel instance; NM is the electron-count bracket.  If copy is

@@ -404,9 +404,10 @@ def test_set_geometry_matches_fresh_wavefunction(pkg):
 
 @pytest.mark.parametrize("name", ["co", "lih"])
 def test_fp32x2_near_a_nucleus(pkg, name):
-    """Electrons within 2^-12 bohr of a nucleus: the FP32X2 tensor-core AO
-    stage takes its row scales from the shells one by one there (outside the
-    per-atom bound tables); such walkers meet the same 2e-4 Ha gate."""
+    """Electrons within 2^-12 bohr of a nucleus (here within 1.7e-4 bohr,
+    |E_L| up to 1e5 Ha): the FP32X2 tensor-core AO stage takes its row scales
+    from the shells one by one there (outside the per-atom bound tables);
+    such walkers meet the same 2e-4 Ha gate."""
     from gpu_common import gated_check
 
     mol = MOLS[name]()
@@ -415,8 +416,28 @@ def test_fp32x2_near_a_nucleus(pkg, name):
     for w in range(0, 200, 2):  # every other walker: one electron next to a nucleus
         a = w % mol.n_atom
         i = (w // 2) % mol.n_elec
-        r[w, i] = mol.atom_xyz[a] + rng.uniform(-1e-5, 1e-5, size=3)
+        r[w, i] = mol.atom_xyz[a] + rng.uniform(-1e-4, 1e-4, size=3)
     E_ref, _, sens = oracle_reference(mol, r)
     E, _ = _run(pkg, mol, r, "fp32x2")
     st = gated_check(E, E_ref, sens)
     print(name, "near-nucleus fp32x2", st)
+
+
+@pytest.mark.parametrize("name", ["co", "lih"])
+def test_fp32x2_near_coalescence(pkg, name):
+    """Electron pairs of opposite spin within 1e-4 bohr: the FP32X2 Coulomb
+    stage sums 1/r_ij of such pairs in pairs of FP32 (an FP32 term would cost
+    2^-22 of 1e4 Ha); the walkers meet the same 2e-4 Ha gate."""
+    from gpu_common import gated_check
+
+    mol = MOLS[name]()
+    r = qi.walkers(mol, 200, seed=24)
+    rng = np.random.default_rng(6)
+    for w in range(0, 200, 2):
+        i = (w // 2) % mol.n_up
+        j = mol.n_up + (w // 2) % mol.n_down
+        r[w, j] = r[w, i] + rng.uniform(-1e-4, 1e-4, size=3)
+    E_ref, _, sens = oracle_reference(mol, r)
+    E, _ = _run(pkg, mol, r, "fp32x2")
+    st = gated_check(E, E_ref, sens)
+    print(name, "near-coalescence fp32x2", st)
