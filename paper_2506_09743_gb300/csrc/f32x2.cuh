@@ -41,7 +41,10 @@ QMC_HD float x2_fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 QMC_HD float x2_sqrt_rn(float a) { return __fsqrt_rn(a); }
 QMC_HD float x2_rcp(float a) { return __frcp_rn(a); }
 QMC_HD float x2_rsqrt(float a) { return rsqrtf(a); }
-QMC_HD float x2_rint(float a) { return rintf(a); }
+// round to the nearest integer (ties to even) by adding and subtracting
+// 1.5 x 2^23, for |a| < 2^22 (every use here: digits below 2^9, exponential
+// arguments below 2^13): two FP32 adds on the FMA pipe
+QMC_HD float x2_rint(float a) { return __fsub_rn(__fadd_rn(a, 12582912.0f), 12582912.0f); }
 QMC_HD float x2_bits_f(uint32_t u) { return __uint_as_float(u); }
 #else
 QMC_HD float x2_add_rn(float a, float b) { return a + b; }

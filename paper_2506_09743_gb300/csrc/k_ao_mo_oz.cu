@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
     const float sc1 = NCH == 2 ? __uint_as_float((unsigned)(127 - e1) << 23) : 0.f;
 
     // digits of one, two (k even) or four (k = 0 mod 4) columns of a channel,
-    // written to the six digit tiles
+    // written to the six digit tiles (a digit's BF16 pattern is the upper half
+    // of its FP32 pattern: two of them are packed by one byte permute)
     auto put1 = [&](int ch, int k, f32x2 v) {
       const float s = ch == 0 ? sc0 : sc1;
       float d[kOzDigits];
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
 #pragma unroll
       for (int j = 0; j < kOzDigits; ++j)
         *reinterpret_cast<uint32_t*>(A + (size_t)(ch * kOzDigits + j) * kTileBytes + off) =
-            (uint32_t)oz_bf16(d0[j]) | ((uint32_t)oz_bf16(d1[j]) << 16);
+            __byte_perm(__float_as_uint(d0[j]), __float_as_uint(d1[j]), 0x7632);
     };
     auto put4 = [&](int ch, int k, f32x2 v0, f32x2 v1, f32x2 v2, f32x2 v3) {
       const float s = ch == 0 ? sc0 : sc1;
@@ -368,8 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
 #pragma unroll
       for (int j = 0; j < kOzDigits; ++j)
         *reinterpret_cast<uint2*>(A + (size_t)(ch * kOzDigits + j) * kTileBytes + off) =
-            make_uint2((uint32_t)oz_bf16(d0[j]) | ((uint32_t)oz_bf16(d1[j]) << 16),
-                       (uint32_t)oz_bf16(d2[j]) | ((uint32_t)oz_bf16(d3[j]) << 16));
+            make_uint2(__byte_perm(__float_as_uint(d0[j]), __float_as_uint(d1[j]), 0x7632),
+                       __byte_perm(__float_as_uint(d2[j]), __float_as_uint(d3[j]), 0x7632));
     };
 
     // ---- 2. passes: AO pairs -> digits -> MMAs per digit class
