@@ -314,8 +314,9 @@ qmc_status qmc_energy_grad(qmc_wf* wf, const double* walkers, int64_t n_walkers,
  *   [3 + P, 3 + 2P)     sum E_L d log|Psi| / d theta_p
  *   then three blocks of 3 n_atom (atom-major, x y z):
  *                       sum d E_L / d R,  sum d ln rho / d R,  sum E_L d ln rho / d R.
- * Scope (a) of qmc_energy_grad: the sums include the forces
- * (QMC_ERR_UNSUPPORTED otherwise).  Sums run in
+ * Scope of qmc_energy_grad; on its path (b) (several determinants, or the
+ * many-body Jastrow) the three force blocks are NaN (all bits set): the
+ * forces need path (a).  Sums run in
  * a fixed order (bitwise reproducible).  qmc_assemble_energy_grad is the host
  * arithmetic above on the (reduced) sums, copied to the host: e_stats [2],
  * grad [n_param] (or NULL), forces [n_atom][3] (or NULL); QMC_ERR_ARG when

@@ -1332,11 +1332,20 @@ qmc_status qmc_energy_grad_sums(qmc_wf* wf, const double* walkers, int64_t n_wal
   qmc_status s =
       grad_setup(wf, walkers, n_walkers, ldw, true, &n_param, &ws, &err_flag, &e_loc, &stats, &partial, &md);
   if (s) return s;
-  if (md) return fail(QMC_ERR_UNSUPPORTED, "the per-batch sums include forces: one determinant, <= 8 electrons");
   s = eval_path(wf, walkers, n_walkers, ldw, ws, err_flag, true, e_loc, nullptr, st);
   if (s) return s;
   s = launch_status(launch_energy_sums(e_loc, n_walkers, sums, st), "energy sums");
   if (s) return s;
+  if (md) {  // gradient sums; the force blocks are NaN (forces need path (a))
+    for (int weight = 1; weight <= 2 && !s; ++weight)
+      s = launch_status(launch_md_grad(wf->dev, walkers, n_walkers, ldw, ws, e_loc, stats,
+                                       wf->spec.prim_start[wf->dev.n_ao], (int)n_param, partial,
+                                       sums + 3 + (weight - 1) * n_param, st, weight),
+                        "parameter gradient sums (several determinants)");
+    if (s) return s;
+    return launch_status(cudaMemsetAsync(sums + 3 + 2 * n_param, 0xFF, sizeof(double) * 9 * wf->dev.n_atom, st),
+                         "force sums");
+  }
   for (int weight = 1; weight <= 2 && !s; ++weight)
     s = launch_status(launch_grad(wf->dev, walkers, n_walkers, ldw, e_loc, stats, wf->dev.ao_ang, wf->dev.ao_prim,
                                   (int)n_param, partial, sums + 3 + (weight - 1) * n_param, st, weight),

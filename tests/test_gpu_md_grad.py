@@ -73,7 +73,7 @@ def test_multidet_gradient_is_bitwise_reproducible(pkg):
     wf.close()
 
 
-def test_multidet_forces_and_sums_refused(pkg):
+def test_multidet_forces_refused(pkg):
     from paper_2506_09743_gb300 import QmcError
 
     mol = qi.make_co(n_det=20)
@@ -81,8 +81,6 @@ def test_multidet_forces_and_sums_refused(pkg):
     x = _x(qi.walkers(mol, 16, seed=67))
     with pytest.raises(QmcError):
         wf.energy_grad(x, want_forces=True)
-    with pytest.raises(QmcError):
-        wf.energy_grad_sums(x)
     wf.close()
 
 
@@ -151,4 +149,29 @@ def test_set_params_covers_the_manybody_jastrow(pkg):
     e2, _ = pkg.Wavefunction(mol2, precision="fp64").local_energy(_x(r))
     torch.cuda.synchronize()
     assert torch.equal(e1, e2)
+    wf.close()
+
+
+def test_multidet_gradient_sums_of_halves_match_the_whole(pkg):
+    """Per-batch sums (qmc_energy_grad_sums) of two halves of a CO-20 batch,
+    added and assembled, reproduce qmc_energy_grad on the whole batch; the
+    force blocks are NaN on this path."""
+    from paper_2506_09743_gb300 import _lib
+
+    mol = qi.make_co(n_det=20)
+    W = 300
+    r = qi.walkers(mol, W, seed=72)
+    wf = pkg.Wavefunction(mol, precision="fp64")
+    n, _ = wf.param_layout()
+    e_mean, e_var, grad, _ = wf.energy_grad(_x(r), want_forces=False)
+    s1 = wf.energy_grad_sums(_x(r[:131])).cpu().numpy()
+    s2 = wf.energy_grad_sums(_x(r[131:])).cpu().numpy()
+    assert np.isnan(s1[3 + 2 * n:]).all() and np.isnan(s2[3 + 2 * n:]).all()
+    tot = s1 + s2
+    tot[3 + 2 * n:] = 0.0
+    ev, var, g, _ = _lib.assemble_energy_grad(tot, n, mol.n_atom)
+    g_ref = grad.cpu().numpy()
+    assert abs(ev - e_mean) <= 1e-12 * abs(e_mean)
+    assert abs(var - e_var) <= 1e-10 * e_var
+    assert np.abs(np.asarray(g) - g_ref).max() <= 1e-10 * np.abs(g_ref).max()
     wf.close()
