@@ -6,7 +6,10 @@
 // 8 x 256 threads per SM, long enough (tens of milliseconds) for the launch
 // to vanish, and is timed with CUDA events on the caller's stream.  The
 // chains are contractive maps, so every value stays finite and normal.
+#include <string>
+
 #include "qmc_internal.cuh"
+#include "wf_internal.cuh"
 
 namespace qmc {
 
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(kRateThreads) k_rate_special(double* out, int 
 
 extern "C" qmc_status qmc_measure_rates(double rates[5], void* stream) {
   using namespace qmc;
-  if (!rates) return QMC_ERR_ARG;
+  if (!rates) return set_error(QMC_ERR_ARG, "null rates");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
@@ -68,7 +71,7 @@ extern "C" qmc_status qmc_measure_rates(double rates[5], void* stream) {
   double* out = nullptr;
   if (cudaMalloc(&out, sizeof(double) * blocks * kRateThreads) != cudaSuccess) {
     cudaGetLastError();
-    return QMC_ERR_OOM;
+    return set_error(QMC_ERR_OOM, "rate probe buffer");
   }
   cudaEvent_t a, b;
   cudaEventCreate(&a);
@@ -98,7 +101,7 @@ extern "C" qmc_status qmc_measure_rates(double rates[5], void* stream) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(out);
-  if (e != cudaSuccess) return QMC_ERR_CUDA;
+  if (e != cudaSuccess) return set_error(QMC_ERR_CUDA, std::string("rate probe: ") + cudaGetErrorString(e));
   rates[0] = threads * kChains * 8.0 * it_fma / t64;          // FP64 FMA / s
   rates[1] = threads * kChains * 8.0 * it_fma * 16 / t32;     // FP32 FMA instructions / s
   rates[2] = threads * kChains * (double)it_special / te;     // FP64 exp / s
