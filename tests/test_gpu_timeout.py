@@ -1,6 +1,6 @@
-"""The timeout path of the bounded device waits (tensor-core AO stage).
+"""The timeout path of the bounded device waits (tensor-core AO stages).
 
-With a wait budget of 0 cycles every mbarrier wait of k_ao_mo_tc gives up at
+With a wait budget of 0 cycles every mbarrier wait of k_ao_mo_tc or k_ao_mo_oz gives up at
 once on a healthy GPU: the block records the failure, drains the MMAs it
 issued (with the normal budget), writes NaN for its remaining MO values and
 frees its tensor memory.  The host must then see QMC_ERR_TIMEOUT wherever
@@ -27,9 +27,11 @@ def pkg():
     return p
 
 
-# CO: two K-passes (the wait between passes and the final wait); LiH: one
-@pytest.mark.parametrize("name", ["co", "lih"])
-def test_timeout_is_reported_and_poisons_outputs(pkg, name):
+# CO: two K-passes (the wait between passes and the final wait); LiH: one.
+# mixed_tf32 runs k_ao_mo_tc; fp32x2 runs k_ao_mo_oz (its value path k_ao_mo_tc)
+@pytest.mark.parametrize("name,precision", [("co", "mixed_tf32"), ("lih", "mixed_tf32"), ("co", "fp32x2"),
+                                            ("lih", "fp32x2")])
+def test_timeout_is_reported_and_poisons_outputs(pkg, name, precision):
     from paper_2506_09743_gb300 import QmcError
     from paper_2506_09743_gb300._lib import QMC_ERR_TIMEOUT
 
@@ -37,7 +39,7 @@ def test_timeout_is_reported_and_poisons_outputs(pkg, name):
     W = 1000
     soa = np.ascontiguousarray(qi.to_soa(qi.walkers(mol, W, seed=31)))
     x = torch.tensor(soa, device="cuda")
-    wf = pkg.Wavefunction(mol, precision="mixed_tf32")
+    wf = pkg.Wavefunction(mol, precision=precision)
     e_ok, lp_ok = wf.local_energy(x)
     wf.check_status()
 
