@@ -66,8 +66,8 @@ typedef enum {
  *  QMC_FP32X2      local energies with AOs in pairs of FP32 (hi + lo, about
  *                  48 significant bits, on the FP32 pipes), the AO->MO
  *                  contraction exact on the tcgen05 tensor cores (the pairs
- *                  cut into BF16 digits; SIMT pairs when n_mo > 16 or
- *                  n_ao > 96), electron-nucleus potential in pairs of
+ *                  cut into BF16 digits; SIMT pairs when n_mo > 16,
+ *                  n_ao > 96 or n_ao n_mo < 256), electron-nucleus potential in pairs of
  *                  FP32 and electron-electron terms in compensated FP32, FP64
  *                  determinants: MO values within about 2^-43 of |AO||C|, so
  *                  that the local energy matches the FP64 form to 2e-4 Ha on

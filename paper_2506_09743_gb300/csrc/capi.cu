@@ -689,7 +689,11 @@ qmc_status build_tables(qmc_wf* wf) {
   d.oz_bound = have_bnd ? reinterpret_cast<const float4*>(ptr[17]) : nullptr;
   d.det_orig = reinterpret_cast<const int*>(ptr[18]);
   d.mo_x2n = reinterpret_cast<const float2*>(ptr[19]);
-  if (d.oz && !oz_supported(d)) d.oz = 0;  // the SIMT pair kernel serves this wavefunction
+  // the SIMT pair kernel serves this wavefunction when the tensor-core stage
+  // does not fit, or when the contraction is too small to pay for it (H2 and
+  // LiH: n_ao x n_mo of 2 and 72, where k_ao_mo_x2 measured 1.1-2.1x faster at
+  // 1,024-65,536 walkers; CO, 812: k_ao_mo_oz 1.2x faster at every size)
+  if (d.oz && (!oz_supported(d) || nao * nmo < 256)) d.oz = 0;
   // the previous tables may still be read by work in flight on any stream
   if (wf->blob) {
     cudaDeviceSynchronize();
