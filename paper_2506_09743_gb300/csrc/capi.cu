@@ -452,6 +452,7 @@ qmc_status build_tables(qmc_wf* wf) {
     }
     pass_used.push_back(used);
     d.n_pass = (int)pass_used.size();
+    std::vector<int> lists, lists2;  // shell lists in four and in two parts per row
     if (d.n_pass > kMaxTcPass) return fail(QMC_ERR_UNSUPPORTED, "too many AO passes");
     for (int p = 0; p < d.n_pass; ++p) {
       d.pass_zero[p] = ~pass_used[p];
@@ -463,20 +464,32 @@ qmc_status build_tables(qmc_wf* wf) {
       // kinetic channel, digits of both channels), ~40 per shell
       auto cost = [&](int s) { return 14 * shells[s].n_prim + 10 * shells[s].n_ao + 4; };
       std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return cost(a) > cost(b); });
-      std::vector<std::vector<int>> part(4);
-      int load[4] = {0, 0, 0, 0};
-      for (int s : by_cost) {
-        const int q = (int)(std::min_element(load, load + 4) - load);
-        part[q].push_back(s);
-        load[q] += cost(s);
-      }
-      for (int q = 0; q < 4; ++q) {
-        std::sort(part[q].begin(), part[q].end());
-        d.part_off[p][q] = (int)tc_shells.size();
-        for (int s : part[q]) tc_shells.push_back(s | (shell_col[s] << 8) | (shell_type[s] << 16));
-      }
-      d.part_off[p][4] = (int)tc_shells.size();
+      // greedy split of the pass's shells over np parts, largest cost first
+      auto split = [&](int np, int* off) {
+        std::vector<std::vector<int>> part(np);
+        std::vector<int> load(np, 0);
+        for (int s : by_cost) {
+          const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+          part[q].push_back(s);
+          load[q] += cost(s);
+        }
+        for (int q = 0; q < np; ++q) {
+          std::sort(part[q].begin(), part[q].end());
+          off[q] = (int)lists.size();
+          for (int s : part[q]) lists.push_back(s | (shell_col[s] << 8) | (shell_type[s] << 16));
+        }
+        off[np] = (int)lists.size();
+      };
+      split(4, d.part_off[p]);
+      std::swap(lists, lists2);
+      split(2, d.part2_off[p]);
+      std::swap(lists, lists2);
     }
+    // the two-part lists follow the four-part ones
+    for (int p = 0; p < d.n_pass; ++p)
+      for (int q = 0; q < 3; ++q) d.part2_off[p][q] += d.n_shell;
+    tc_shells = lists;
+    tc_shells.insert(tc_shells.end(), lists2.begin(), lists2.end());
   }
   if (d.gen_x2)
     for (const ShellDev& q : shells)

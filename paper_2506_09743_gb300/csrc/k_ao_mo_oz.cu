@@ -8,11 +8,14 @@
 // written to shared memory as BF16, and contracted on the tensor cores:
 //     D[ch][g] += A[ch][k] B[l]   for every digit pair with k + l = g,
 //                                 g = 0..5   (kind::f16, BF16 in, FP32 out).
-// The six MO digit slices are stacked along N behind five zero blocks of 16
-// rows, [0 0 0 0 0 B_0 .. B_5]; the window of six blocks that starts at
-// block 5 - k holds B_{g-k} in block g (zero for g < k), so one MMA of
-// N = 96 per A digit k adds A_k B_{g-k} to all six class accumulators at
-// once: 6 MMAs per channel and K step instead of 21.
+// The six MO digit slices are stacked along N behind one zero block of 16
+// rows, [0 B_0 .. B_5], and the six class accumulators of a channel lie side
+// by side in tensor memory (16 columns each).  One MMA per A digit k adds
+// A_k B_{g-k} to every class g >= k at once: for even k the window B_0 ..
+// B_{5-k} (N = 16 (6 - k)) lands on classes k .. 5; for odd k the window
+// starts one block earlier, on the zero block (N = 16 (7 - k)), and lands on
+// classes k - 1 .. 5, so that every accumulator address stays a multiple of
+// 32 columns.  6 MMAs per channel and K step instead of 21.
 // Every product and every partial sum of a class is an integer below 2^24,
 // so the FP32 accumulation in tensor memory is exact; the epilogue
 // recombines the six classes as a pair of FP32 and writes FP64.
@@ -26,11 +29,16 @@
 // range.  MO columns are scaled by 2^f_m and sliced on the host.
 //
 // Layout as k_ao_mo_tc: persistent CTAs walk over tiles of 128 walkers x one
-// electron (MMA M = 128), 512 threads in four parts per row, AO columns in
-// K-passes of 32 (a shell never straddles a pass).  One CTA per SM (96 KB of
-// digit tiles per pass).  Tensor memory: 2 channels x 6 classes x 16 MO
-// columns.  Every mbarrier wait is bounded as in k_ao_mo_tc (error flags,
-// drain of the issued MMAs, NaN outputs, QMC_ERR_TIMEOUT on the host).
+// electron (MMA M = 128), AO columns in K-passes of 32 (a shell never
+// straddles a pass), one CTA of 512 threads per SM.  Where shared memory
+// holds two sets of digit tiles (96 KB each), the CTA runs as two groups of
+// eight warps on alternate tiles, each with its own digit tiles, mbarrier,
+// named barrier and half of tensor memory: while one group waits for its
+// MMAs or drains its accumulators, the other evaluates AOs.  Otherwise one
+// group of sixteen warps (four threads per row).  Tensor memory per group:
+// 2 channels x 6 classes x 16 MO columns.  Every mbarrier wait is bounded as
+// in k_ao_mo_tc (error flags, drain of the issued MMAs, NaN outputs,
+// QMC_ERR_TIMEOUT on the host).
 #include <algorithm>
 
 #include "ao_eval.cuh"
@@ -42,12 +50,11 @@ namespace {
 
 constexpr int kRows = 128;
 constexpr int kThreads = 512;
-constexpr int kParts = kThreads / kRows;
 constexpr int kNPad = 16;
 constexpr int kPass = kTcPass;
-constexpr uint32_t kTmemCols = 256;              // 2 x 6 x 16 = 192 used
-constexpr int kStackBlocks = 2 * kOzDigits - 1;   // zero blocks + digit slices of the B stack
-constexpr int kNMma = kOzClasses * kNPad;         // N of one MMA: the six class blocks
+constexpr uint32_t kTmemCols = 256;              // per group: 2 x 6 x 16 = 192 used
+constexpr int kStackBlocks = kOzDigits + 1;       // zero block + digit slices of the B stack
+constexpr int kChCols = kOzClasses * kNPad;       // accumulator columns of one channel
 constexpr int kTileBytes = kRows * kPass * 2;     // one digit slice of one channel (BF16)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -64,16 +71,45 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, N = 96, M = 128.
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNMma >> 3) << 17) |
-                                ((uint32_t)(kRows >> 4) << 24);
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = n
+// (a multiple of 16 up to 96 here).
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdescBf16), "r"(accumulate));
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// Barrier of one thread group: the whole CTA for one group, named barrier
+// 1 + group (n threads) for two
+template <int G>
+__device__ __forceinline__ void group_sync(int grp, int n) {
+  if (G == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(n) : "memory");
+  }
+}
+
+template <int G>
+__device__ __forceinline__ bool group_and(int grp, int n, bool v) {
+  if (G == 1) return __syncthreads_and(v) != 0;
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, %2, %3, q;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + grp), "r"(n)
+      : "memory");
+  return r != 0;
 }
 
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase, long long budget) {
@@ -161,42 +197,50 @@ __device__ __forceinline__ void shell_bounds(const ShellDev& sh, float r2, float
        2.f * rb0 * gn * (float)l * rl1;
 }
 
-__host__ __device__ inline int oz_int_words(const WfDev& wf) { return (2 * wf.n_ao + wf.n_shell + 3) & ~3; }
+// shared int words of the AO powers, AO columns and both shell lists (four
+// and two parts per row), padded to 16 bytes
+__host__ __device__ inline int oz_int_words(const WfDev& wf) { return (2 * wf.n_ao + 2 * wf.n_shell + 3) & ~3; }
 
 }  // namespace
 
-template <int NCH>
+template <int NCH, int NG>
 __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double* __restrict__ walkers, int64_t W,
                                                          int64_t ldw, const float* __restrict__ gradJ,
                                                          double* __restrict__ mo_out, int nmp, int64_t ldm,
                                                          int* __restrict__ err_flag, int* __restrict__ err_wf) {
+  constexpr int kGT = kThreads / NG;      // threads of a group
+  constexpr int kGP = kGT / kRows;       // threads (parts) per row
+  constexpr int kGWarps = kGT / 32;      // warps of a group
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int kp = wf.k_pad;
-  unsigned char* A = smem_raw;                                        // [NCH][6][128 x 32] BF16
-  unsigned char* B = A + (size_t)NCH * kOzDigits * kTileBytes;        // [11 x 16][kp] BF16 stack
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int grp = tid / kGT, gtid = tid % kGT;
+  unsigned char* A = smem_raw + (size_t)grp * NCH * kOzDigits * kTileBytes;  // [NCH][6][128 x 32] BF16
+  unsigned char* B = smem_raw + (size_t)NG * NCH * kOzDigits * kTileBytes;    // [7 x 16][kp] BF16 stack
   ShellDev* sh_s = reinterpret_cast<ShellDev*>(B + (size_t)kStackBlocks * kNPad * kp * 2);
   float* xtab = reinterpret_cast<float*>(sh_s + wf.n_shell);          // [64][2]
   int* pow_s = reinterpret_cast<int*>(xtab + 128);                    // [n_ao]
   int* col_s = pow_s + wf.n_ao;                                       // [n_ao]
-  int* list_s = col_s + wf.n_ao;                                      // [n_shell]
-  unsigned* rowb = reinterpret_cast<unsigned*>(pow_s + oz_int_words(wf));  // [2][128] bound bits
-  int* rowe_buf = reinterpret_cast<int*>(rowb + 2 * kRows);          // [2 tiles][2][128] scale exponents
-  int* colf = rowe_buf + 4 * kRows;                                   // [16] MO column exponents
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(colf + kNPad);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  int* list_s = col_s + wf.n_ao;                                      // [2][n_shell]
+  int* ints_end = pow_s + oz_int_words(wf);
+  unsigned* rowb = reinterpret_cast<unsigned*>(ints_end) + grp * 2 * kRows;  // [NG][2][128] bound bits
+  int* rowe_buf = ints_end + NG * 2 * kRows + grp * 4 * kRows;                // [NG][2 tiles][2][128] exponents
+  int* colf = ints_end + NG * 6 * kRows;                                      // [16] MO column exponents
+  uint64_t* mbar_all = reinterpret_cast<uint64_t*>(colf + kNPad);            // [NG]
+  uint64_t* mbar = mbar_all + grp;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar_all + NG);
 
-  const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols));
+                 "r"(kTmemCols * NG));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
-  if (tid == 0) {
+  if (gtid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  {  // the stack: five zero blocks, then the six digit slices of the MO table
+  {  // the stack: one zero block, then the six digit slices of the MO table
     const uint32_t* src = reinterpret_cast<const uint32_t*>(wf.mo_oz);
     uint32_t* dst = reinterpret_cast<uint32_t*>(B);
     const int zero_words = (kStackBlocks - kOzDigits) * kNPad * kp / 2;
@@ -210,13 +254,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
     pow_s[k] = wf.ao_pow[k];
     col_s[k] = wf.ao_col[k];
   }
-  for (int k = tid; k < wf.n_shell; k += kThreads) list_s[k] = wf.tc_shells[k];
+  for (int k = tid; k < 2 * wf.n_shell; k += kThreads) list_s[k] = wf.tc_shells[k];
   for (int k = tid; k < kNPad; k += kThreads) colf[k] = wf.oz_colexp[k];
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = *tmem_slot + (uint32_t)(grp * kTmemCols);  // this group's columns
 
-  const int row = tid & (kRows - 1), part = tid / kRows;
+  const int row = gtid & (kRows - 1), part = gtid / kRows;
+  // a row's shells of pass p: list_s[part_begin(p) .. part_end(p)), from the
+  // four-part lists for one group, from the two-part lists for two
+  auto part_begin = [&](int p) { return NG == 1 ? wf.part_off[p][part] : wf.part2_off[p][part]; };
+  auto part_end = [&](int p) { return NG == 1 ? wf.part_off[p][part + 1] : wf.part2_off[p][part + 1]; };
   const uint32_t lbo = 128, sbo_a = 512, sbo_b = (uint32_t)(kp / 8) * 128;
   const int64_t n_wblk = (W + kRows - 1) / kRows;
   const int64_t n_tiles = n_wblk * wf.n_elec;
@@ -241,12 +289,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
       ngz = gradJ[(int64_t)(3 * ti + 2) * ldm + tw];
     }
   };
-  fetch(blockIdx.x);
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
+  // group g takes tiles blockIdx.x + (NG j + g) gridDim.x
+  const int64_t tile_step = (int64_t)NG * gridDim.x;
+  fetch(blockIdx.x + (int64_t)grp * gridDim.x);
+  for (int64_t tile = blockIdx.x + (int64_t)grp * gridDim.x; tile < n_tiles; tile += tile_step, ++iter) {
     // scale exponents of this tile's rows: written before its passes, read by
     // its epilogue; alternate buffers, so that the next tile may write its
-    // own while this epilogue still reads (the pass barrier of the tile after
-    // next orders the reuse)
+    // own while this epilogue still reads (the group's pass barrier of the
+    // tile after next orders the reuse)
     int* rowe = rowe_buf + (iter & 1u) * 2 * kRows;
     const int i = (int)(tile % wf.n_elec);
     const int64_t wb = tile / wf.n_elec;
@@ -301,13 +351,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
       }
     } else {
       // the four parts of a row bound their own shells and meet in shared memory
-      if (tid < 2 * kRows) rowb[tid] = 0u;
-      __syncthreads();
+      for (int k = gtid; k < 2 * kRows; k += kGT) rowb[k] = 0u;
+      group_sync<NG>(grp, kGT);
       float bv = 0.f, bk = 0.f;
       int cur_atom = -1;
       float r2 = 0.f, rho = 0.f, irho = 0.f;
       for (int pass = 0; pass < wf.n_pass; ++pass)
-        for (int q = wf.part_off[pass][part]; q < wf.part_off[pass][part + 1]; ++q) {
+        for (int q = part_begin(pass); q < part_end(pass); ++q) {
           const ShellDev& sh = sh_s[list_s[q] & 0xff];
           if (sh.atom != cur_atom) {
             cur_atom = sh.atom;
@@ -326,9 +376,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
       // (a NaN bound, from an electron on a nucleus, orders above all)
       atomicMax(&rowb[row], __float_as_uint(bv));
       if (NCH == 2) atomicMax(&rowb[kRows + row], __float_as_uint(bk));
-      __syncthreads();
-      if (tid < 2 * kRows) rowe[tid] = scale_exponent(rowb[tid]);
-      __syncthreads();
+      group_sync<NG>(grp, kGT);
+      for (int k = gtid; k < 2 * kRows; k += kGT) rowe[k] = scale_exponent(rowb[k]);
+      group_sync<NG>(grp, kGT);
       e0 = rowe[row];
       e1 = rowe[kRows + row];
     }
@@ -379,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
     for (int pass = 0; pass < wf.n_pass; ++pass) {
       if (pass > 0) ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1, wf.wait_cycles) && ok;
       const unsigned zero_cols = wf.pass_zero[pass];
-      for (int k = part; k < kPass; k += kParts)
+      for (int k = part; k < kPass; k += kGP)
         if ((zero_cols >> k) & 1u)
 #pragma unroll
           for (int ch = 0; ch < NCH; ++ch)
@@ -390,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
       f32x2 dx(0.f), dy(0.f), dz(0.f), r2(0.f), G(0.f), rho(0.f), irho(0.f);
       bool have_rho = false;
       f32x2 px[5], py[5], pz[5];
-      for (int q = wf.part_off[pass][part]; q < wf.part_off[pass][part + 1]; ++q) {
+      for (int q = part_begin(pass); q < part_end(pass); ++q) {
         const int ent = list_s[q];
         const ShellDev& sh = sh_s[ent & 0xff];
         const int c0 = (ent >> 8) & 0xff, type = ent >> 16;
@@ -519,20 +569,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      ok = __syncthreads_and(ok) != 0;
+      ok = group_and<NG>(grp, kGT, ok);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) break;
-      if (tid == 0) {
+      if (gtid == 0) {
         const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
         for (int ch = 0; ch < NCH; ++ch)
           for (int ks = 0; ks < kPass / 16; ++ks)
             for (int k = 0; k < kOzDigits; ++k) {
               const uint32_t a = a0 + (uint32_t)(ch * kOzDigits + k) * kTileBytes + (uint32_t)ks * 256;
-              // window of six blocks starting at block 5 - k of the stack
-              const uint32_t b = b0 + (uint32_t)(kOzDigits - 1 - k) * (kNPad * kp * 2) +
+              // even k: window B_0 .. B_{5-k} (stack block 1 on) onto classes
+              // k .. 5; odd k: the zero block first, onto classes k - 1 .. 5.
+              // k = 0 comes first and writes all six classes of the channel.
+              const int odd = k & 1;
+              const int n = kNPad * (kOzDigits - k + odd);
+              const uint32_t b = b0 + (uint32_t)(1 - odd) * (kNPad * kp * 2) +
                                  (uint32_t)(pass * (kPass / 8) + 2 * ks) * 128;
+              const uint32_t d = tmem + (uint32_t)(ch * kChCols + kNPad * (k - odd));
               const uint32_t acc = (written >> ch) & 1u;
-              mma_bf16(tmem + (uint32_t)(ch * kNMma), smem_desc(a, lbo, sbo_a), smem_desc(b, lbo, sbo_b), acc);
+              mma_bf16(d, smem_desc(a, lbo, sbo_a), smem_desc(b, lbo, sbo_b), idesc_bf16(n), acc);
               written |= 1u << ch;
             }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -542,32 +597,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
       ++commits;
     }
     if (ok) ok = mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1, wf.wait_cycles);
-    ok = __syncthreads_and(ok) != 0;
+    ok = group_and<NG>(grp, kGT, ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {
       // record the failure, let the issued MMAs finish (at most one commit is
-      // outstanding), poison this CTA's remaining outputs and stop
-      if (tid == 0) {
+      // outstanding), poison this group's remaining outputs and stop
+      if (gtid == 0) {
         atomicExch(err_flag, 1);
         atomicExch(err_wf, 1);
       }
       if (commits > 0) mbar_wait_bounded(smem_u32(mbar), (commits - 1) & 1, kDrainCycles);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int ch = tid >> 7;
-      for (int64_t t = tile; t < n_tiles; t += gridDim.x) {
+      for (int64_t t = tile; t < n_tiles; t += tile_step) {
         const int ti = (int)(t % wf.n_elec);
         const int64_t tw = (t / wf.n_elec) * kRows + row;
-        if (ch < NCH && tw < W)
-          for (int m = 0; m < nmp; ++m)
-            mo_out[((size_t)(ti * NCH + ch) * nmp + m) * ldm + tw] = __longlong_as_double(0x7ff8000000000000ll);
+        if (tw < W)
+          for (int ch = part; ch < NCH; ch += kGP)
+            for (int m = 0; m < nmp; ++m)
+              mo_out[((size_t)(ti * NCH + ch) * nmp + m) * ldm + tw] = __longlong_as_double(0x7ff8000000000000ll);
       }
       break;
     }
-    fetch(tile + gridDim.x);
-    // ---- 3. epilogue: the six classes of 8 MO columns per thread, recombined
-    {
-      const int quad = warp & 3, role = warp >> 2, ch = role >> 1, half = role & 1;
-      if (ch < NCH) {
+    fetch(tile + tile_step);
+    // ---- 3. epilogue: the six classes of 8 MO columns per thread, recombined.
+    // A warp reads the tensor-memory lanes of its rank mod 4 (a group starts
+    // at a multiple of four warps); the jobs (channel, half of the 16 MO
+    // columns) go round the group's roles.
+    constexpr int kRoles = kGWarps / 4;
+    const int quad = warp & 3, role = (warp % kGWarps) >> 2;
+#pragma unroll
+    for (int job = role; job < 2 * NCH; job += kRoles) {
+      const int ch = job >> 1, half = job & 1;
+      {
         uint32_t v[kOzClasses][8];
 #pragma unroll
         for (int g = 0; g < kOzClasses; ++g) {
@@ -602,21 +663,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_ao_mo_oz(WfDev wf, const double
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(kTmemCols * NG));
 }
 
-size_t oz_smem_bytes(const WfDev& wf, int nch) {
-  size_t b = (size_t)nch * kOzDigits * kTileBytes + (size_t)kStackBlocks * kNPad * wf.k_pad * 2;
+size_t oz_smem_bytes(const WfDev& wf, int nch, int groups) {
+  size_t b = (size_t)groups * nch * kOzDigits * kTileBytes + (size_t)kStackBlocks * kNPad * wf.k_pad * 2;
   b += sizeof(ShellDev) * wf.n_shell + sizeof(float) * 128 + 4 * (size_t)oz_int_words(wf);
-  b += sizeof(int) * (6 * kRows + kNPad) + 16;
+  b += sizeof(int) * (groups * 6 * kRows + kNPad) + 8 * groups + 8;
   return b;
 }
 
 bool oz_supported(const WfDev& wf) {
   // N = 16 MO columns per MMA; the class sums stay below 2^24 for up to 110
   // AO terms (96 kept as the limit); the tiles must fit in shared memory
-  return wf.n_pass > 0 && wf.n_mo <= kNPad && wf.n_ao <= 96 && oz_smem_bytes(wf, 2) <= 227 * 1024;
+  return wf.n_pass > 0 && wf.n_mo <= kNPad && wf.n_ao <= 96 && oz_smem_bytes(wf, 2, 1) <= 227 * 1024;
 }
+
+int oz_groups(const WfDev& wf, int nch) { return oz_smem_bytes(wf, nch, 2) <= 227 * 1024 ? 2 : 1; }
+
+namespace {
+
+template <int NCH, int G>
+cudaError_t launch_oz_t(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
+                        int* err_flag, int* err_wf, dim3 grid, cudaStream_t st) {
+  const size_t smem = oz_smem_bytes(wf, NCH, G);
+  cudaFuncSetAttribute(k_ao_mo_oz<NCH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ao_mo_oz<NCH, G><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, static_cast<const float*>(ws.gradJ), ws.mo,
+                                                    ws.nmp, ws.ldm, err_flag, err_wf);
+  return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_ao_mo_oz(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                             int nch, int* err_flag, int* err_wf, cudaStream_t st) {
@@ -626,16 +704,12 @@ cudaError_t launch_ao_mo_oz(const WfDev& wf, const double* walkers, int64_t W, i
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   const int64_t n_tiles = ((W + kRows - 1) / kRows) * wf.n_elec;
   const dim3 grid((unsigned)std::min<int64_t>(n_tiles, std::max(n_sm, 1)));
-  const size_t smem = oz_smem_bytes(wf, nch);
-  const float* gj = static_cast<const float*>(ws.gradJ);
-  if (nch == 2) {
-    cudaFuncSetAttribute(k_ao_mo_oz<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ao_mo_oz<2><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, ws.mo, ws.nmp, ws.ldm, err_flag, err_wf);
-  } else {
-    cudaFuncSetAttribute(k_ao_mo_oz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ao_mo_oz<1><<<grid, kThreads, smem, st>>>(wf, walkers, W, ldw, gj, ws.mo, ws.nmp, ws.ldm, err_flag, err_wf);
-  }
-  return cudaGetLastError();
+  const bool two = oz_groups(wf, nch) == 2;
+  if (nch == 2)
+    return two ? launch_oz_t<2, 2>(wf, walkers, W, ldw, ws, err_flag, err_wf, grid, st)
+               : launch_oz_t<2, 1>(wf, walkers, W, ldw, ws, err_flag, err_wf, grid, st);
+  return two ? launch_oz_t<1, 2>(wf, walkers, W, ldw, ws, err_flag, err_wf, grid, st)
+             : launch_oz_t<1, 1>(wf, walkers, W, ldw, ws, err_flag, err_wf, grid, st);
 }
 
 }  // namespace qmc

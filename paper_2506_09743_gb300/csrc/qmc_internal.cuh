@@ -127,14 +127,18 @@ struct WfDev {
   // pass_zero[p] (bit k = column k) are unused (zero).  A list entry is
   // shell | first column within the pass << 8 | type << 16, type 1 + l for a
   // complete s, p or d shell whose AOs sit in canonical Cartesian order
-  // (x, y, z; xx, xy, xz, yy, yz, zz) from that column, 0 otherwise
+  // (x, y, z; xx, xy, xz, yy, yz, zz) from that column, 0 otherwise.  The
+  // same shells split into two parts per row follow in
+  // tc_shells[part2_off[p][q] .. part2_off[p][q+1]) (k_ao_mo_oz with two
+  // thread groups).
   const int* ao_col;     // [n_ao]
-  const int* tc_shells;  // [n_shell]
+  const int* tc_shells;  // [2][n_shell]
   long long wait_cycles; // budget of a bounded device wait, SM clock cycles (qmc_set_wait_limit)
   int k_pad;             // n_pass * kTcPass (0 when the form has no tensor-core stage)
   int n_pass;
   unsigned pass_zero[kMaxTcPass];
   int part_off[kMaxTcPass][5];
+  int part2_off[kMaxTcPass][3];
 };
 
 struct Workspace {
@@ -302,8 +306,9 @@ cudaError_t launch_ao_mo_simt(const WfDev& wf, int prec, const double* walkers, 
                               const Workspace& ws, int nch, cudaStream_t st);
 // pairs of FP32 (QMC_FP32X2 form): SIMT contraction, and the digit-sliced
 // tensor-core contraction where oz_supported
-size_t oz_smem_bytes(const WfDev& wf, int nch);
+size_t oz_smem_bytes(const WfDev& wf, int nch, int groups);
 bool oz_supported(const WfDev& wf);
+int oz_groups(const WfDev& wf, int nch);  // thread groups of k_ao_mo_oz (1 or 2)
 cudaError_t launch_ao_mo_oz(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
                             int nch, int* err_flag, int* err_wf, cudaStream_t st);
 cudaError_t launch_ao_mo_x2(const WfDev& wf, const double* walkers, int64_t W, int64_t ldw, const Workspace& ws,
