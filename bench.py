@@ -45,8 +45,8 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.
 # FP32X2 form on 131,072 CO walkers (418.6 MB per launch); set to None whenever the kernel changes.
 DET_TRAFFIC_BYTES_PER_WALKER = (414.384128e6 + 4.216064e6) / 131072
 # DRAM bytes (read + write) per walker of the k_ao_mo_oz launch, from an ncu capture of that kernel on
-# 131,072 CO walkers (67.3 MB read, 409.2 MB written per launch); None whenever the kernel changes.
-OZ_TRAFFIC_BYTES_PER_WALKER = (67.25888e6 + 409.163264e6) / 131072
+# 131,072 CO walkers (66.3 MB read, 408.5 MB written per launch); None whenever the kernel changes.
+OZ_TRAFFIC_BYTES_PER_WALKER = (66.331904e6 + 408.453376e6) / 131072
 
 
 def det_stage_flops(mol) -> float:
