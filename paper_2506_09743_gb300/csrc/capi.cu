@@ -464,14 +464,31 @@ qmc_status build_tables(qmc_wf* wf) {
       // kinetic channel, digits of both channels), ~40 per shell
       auto cost = [&](int s) { return 14 * shells[s].n_prim + 10 * shells[s].n_ao + 4; };
       std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return cost(a) > cost(b); });
-      // greedy split of the pass's shells over np parts, largest cost first
+      // split of the pass's shells over np parts: greedy, largest cost first;
+      // two parts of at most 20 shells take the best of all subsets instead
       auto split = [&](int np, int* off) {
         std::vector<std::vector<int>> part(np);
         std::vector<int> load(np, 0);
-        for (int s : by_cost) {
-          const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-          part[q].push_back(s);
-          load[q] += cost(s);
+        const int n = (int)by_cost.size();
+        if (np == 2 && n <= 20) {
+          int total = 0;
+          for (int s : by_cost) total += cost(s);
+          unsigned best = 0;
+          int best_max = total + 1;
+          for (unsigned m = 0; m < (1u << n); m += 2) {  // shell 0 (the costliest) stays in part 0
+            int a = 0;
+            for (int k = 0; k < n; ++k)
+              if ((m >> k) & 1u) a += cost(by_cost[k]);
+            const int mx = std::max(a, total - a);
+            if (mx < best_max) { best_max = mx; best = m; }
+          }
+          for (int k = 0; k < n; ++k) part[(best >> k) & 1u].push_back(by_cost[k]);
+        } else {
+          for (int s : by_cost) {
+            const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            part[q].push_back(s);
+            load[q] += cost(s);
+          }
         }
         for (int q = 0; q < np; ++q) {
           std::sort(part[q].begin(), part[q].end());
