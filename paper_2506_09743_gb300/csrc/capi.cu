@@ -603,7 +603,7 @@ qmc_status build_tables(qmc_wf* wf) {
   if (h.w != 0.0 && !general_supported(d) && !bf_multidet_supported(d))
     return fail(QMC_ERR_UNSUPPORTED,
                 "backflow needs <= 8 electrons, <= 4 per spin and (several determinants) <= 8 orbital columns");
-  if (det_smem_bytes(d, true) > 227 * 1024)
+  if (det_smem_bytes(d, true) > 227 * 1024 || (prec == QMC_FP32X2 && det_x2_smem_bytes(d, true) > 227 * 1024))
     return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
 
   // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
@@ -918,7 +918,8 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   mark(wf, 4, st);
   s = launch_status(wf->det_method == QMC_DET_EXPLICIT
                         ? launch_det_explicit(d, wf->precision, W, v, kinetic, e_loc, log_psi, st)
-                        : launch_det(d, wf->precision, W, v, kinetic, e_loc, log_psi, st),
+                        : x2 ? launch_det_x2(d, W, v, kinetic, e_loc, log_psi, st)
+                             : launch_det(d, wf->precision, W, v, kinetic, e_loc, log_psi, st),
                     "det");
   if (s) return s;
   mark(wf, 5, st);

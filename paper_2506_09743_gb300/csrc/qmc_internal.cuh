@@ -255,6 +255,7 @@ __device__ __forceinline__ double team_sum(double v) {
 
 size_t tc_smem_bytes(const WfDev& wf, int nch);
 size_t det_smem_bytes(const WfDev& wf, bool kin);
+size_t det_x2_smem_bytes(const WfDev& wf, bool kin);  // k_det_x2 (QMC_FP32X2 form)
 
 // initial walker positions for the serving loop: home nucleus per electron
 struct InitSpec {
@@ -317,6 +318,9 @@ cudaError_t launch_ao_mo_tc(const WfDev& wf, int prec, const double* walkers, in
                             const Workspace& ws, int nch, int* err_flag, int* err_wf, cudaStream_t st);
 cudaError_t launch_det(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,
                        double* e_loc, double* log_psi, cudaStream_t st);
+// the same in pairs of FP32 (QMC_FP32X2 form, table method)
+cudaError_t launch_det_x2(const WfDev& wf, int64_t W, const Workspace& ws, bool kinetic, double* e_loc,
+                          double* log_psi, cudaStream_t st);
 // explicit per-excitation determinants (the baseline of the table method)
 size_t det_explicit_smem_bytes(const WfDev& wf, bool kin);
 cudaError_t launch_det_explicit(const WfDev& wf, int prec, int64_t W, const Workspace& ws, bool kinetic,
