@@ -6,7 +6,7 @@ space, Pade Jastrow; 262,144 seeded synthetic walkers per GPU.  One step =
 one qmc_local_energy call over the whole batch (Jastrow + Coulomb, AO
 evaluation, AO->MO contraction, reference inverse, excited-determinant
 tables, E_L assembly).  The headline `value` is the FP32X2 form (AOs,
-contraction and Coulomb potential in pairs of FP32, FP64 determinants), the
+contraction, Coulomb potential and determinant stage in pairs of FP32), the
 form that meets 2e-4 Ha per walker against the FP64 oracle; the plain FP64
 form and the faster FP32-AO tensor-core form (mixed_tf32, which does not meet
 that gate on ill-conditioned walkers) are timed on the same walkers and
@@ -41,12 +41,17 @@ METRIC = "walker local-energy evals/s (CO, 14 e-) vs FP64 plain; p99 request lat
 UNIT = "walker-evals/s"
 WORKLOAD = "CO 14e- 58 GTO 14 MO 100 det, 262144 walkers"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.26 TF)
-# DRAM bytes (read + write) per walker of the k_det launch, from an ncu capture of that kernel in the
-# FP32X2 form on 131,072 CO walkers (418.6 MB per launch); set to None whenever the kernel changes.
+# DRAM bytes (read + write) per walker of the k_det launch (the FP64 determinant stage of the
+# mixed_tf32 and FP64 forms), from an ncu capture of that kernel on 131,072 CO walkers (418.6 MB per
+# launch); set to None whenever the kernel changes.
 DET_TRAFFIC_BYTES_PER_WALKER = (414.384128e6 + 4.216064e6) / 131072
 # DRAM bytes (read + write) per walker of the k_ao_mo_oz launch, from an ncu capture of that kernel on
-# 131,072 CO walkers (66.3 MB read, 408.5 MB written per launch); None whenever the kernel changes.
-OZ_TRAFFIC_BYTES_PER_WALKER = (66.331904e6 + 408.453376e6) / 131072
+# 131,072 CO walkers (66.3 MB read, 409.0 MB written per launch); None whenever the kernel changes.
+OZ_TRAFFIC_BYTES_PER_WALKER = (66.262016e6 + 408.966912e6) / 131072
+# DRAM bytes (read + write) per walker of the k_det_x2 launch (FP32X2 determinant stage), from an ncu
+# capture of that kernel on 131,072 CO walkers (414.3 MB read, 1.2 MB written: energies only, no
+# log|Psi|); None whenever the kernel changes.
+DETX2_TRAFFIC_BYTES_PER_WALKER = (414.282752e6 + 1.217024e6) / 131072
 
 
 def det_stage_flops(mol) -> float:
@@ -78,8 +83,9 @@ def ao_mo_stage_flops(mol) -> float:
 
 # FP32 operations of the pair-of-FP32 primitives (f32x2.cuh, as written):
 # two_prod 2, fast_two_sum 3, two_sum 6; product of pairs 7, pair times a
-# float 6, sum of pairs 11; multiply-accumulate into a pair 12; exponential 69
-X2_OPS = {"mac": 12, "mul": 7, "mulf": 6, "add": 11, "exp": 69}
+# float 6, sum of pairs 11; multiply-accumulate into a pair 12; c - a b as a
+# pair 15; reciprocal 10; renormalisation 3; exponential 69
+X2_OPS = {"mac": 12, "mul": 7, "mulf": 6, "add": 11, "fms": 15, "recip": 10, "norm": 3, "exp": 69}
 
 
 def x2_stage_ops(mol) -> float:
@@ -104,6 +110,46 @@ def x2_stage_ops(mol) -> float:
     per_row = n_shell_prim * per_prim + mol.n_ao * per_ao + 2 * mol.n_ao * mol.n_mo * o["mac"]
     del n_prim
     return float(mol.n_elec * per_row)
+
+
+def det_x2_stage_ops(mol) -> float:
+    """Algorithmic FP32 operations per walker of k_det_x2, the FP32X2
+    determinant stage (table method, kinetic channel), from its pair
+    primitives (X2_OPS).  Per spin with n electrons, nh holes, nv virtuals:
+      elimination: per pivot step one reciprocal, the pivot row's n - 1
+                   products, per other row one product and n - 1 updates
+                   c - a b, and the determinant's running product
+      Tr(A0^-1 B0): n^2 multiply-accumulates, n renormalisations, n - 1 sums
+      per virtual: t = A0^-1 Phi_p (n^2 multiply-accumulates), y = B_p - B0 t
+                   (n^2 updates), Top on the holes (nh n multiply-accumulates),
+                   n + nh renormalisations
+      per distinct rank-2 spin excitation: the 2 x 2 minor (a product and an
+                   update) and its kinetic numerator (4 multiply-accumulates
+                   and a renormalisation)
+      per determinant: two products and three multiply-accumulates (ratio and
+                   kinetic numerator);
+    plus, per FP64 input element (both channels of the occupied block and of
+    the virtual columns), its split into a pair (7 FP32 operations; the
+    integer bit operations are not counted), and the 16-lane reductions of the
+    two sums (8 pair sums)."""
+    o = X2_OPS
+    tot = 8 * o["add"]
+    dets = np.asarray(mol.det_exc)
+    for s, n in enumerate((mol.n_up, mol.n_down)):
+        if n == 0:
+            continue
+        ex = dets[:, s, :]
+        holes = [h for row in ex for h in row[1:1 + row[0]]]
+        parts = [p for row in ex for p in row[3:3 + row[0]]]
+        nh = n - min(holes) if holes else 0
+        nv = max(parts) + 1 - n if parts else 0
+        tot += n * (o["recip"] + (n - 1) * o["mul"] + (n - 1) * (o["mul"] + (n - 1) * o["fms"]) + o["mul"])
+        tot += n * n * o["mac"] + n * o["norm"] + (n - 1) * o["add"]
+        tot += nv * (n * n * o["mac"] + n * n * o["fms"] + nh * n * o["mac"] + (n + nh) * o["norm"])
+        uniq = {tuple(row) for row in ex}
+        tot += sum(o["mul"] + o["fms"] + 4 * o["mac"] + o["norm"] for r in uniq if r[0] == 2)
+        tot += 7 * 2 * n * (n + nv)
+    return float(tot + len(dets) * (2 * o["mul"] + 3 * o["mac"]))
 
 
 def fp64_ao_stage_ops(mol) -> dict:
@@ -798,15 +844,19 @@ def main():
     # of the library): beside the nominal peaks derived from the unit counts
     fp64_meas = 2.0 * rates["fp64_fma_per_s"] / 1e12 if rates else None
     fp32_meas = rates["fp32_fma_per_s"] / 1e12 if rates else None
-    # rooflines: the FP32X2 AO stage (k_ao_mo_oz) is bound by FP32/ALU issue
-    # (its contraction runs on the tensor pipe), the determinant stage by the
-    # FP64 pipe
+    # rooflines: both FP32X2 stages are bound by FP32/ALU issue (the AO
+    # stage's contraction runs on the tensor pipe, its determinant stage in
+    # pairs of FP32); the FP64 determinant stage of the mixed_tf32 and FP64
+    # forms (k_det) by the FP64 pipe
     oz_ops = oz_stage_alu_ops(mol) * W
     x2_ms = float(stage_x2[1])
     oz_rate = oz_ops / (x2_ms / 1e3) / 1e12
     x2_equiv = x2_stage_ops(mol) * W / (x2_ms / 1e3) / 1e12
+    dx2_ops = det_x2_stage_ops(mol) * W
+    dx2_ms = float(stage_x2[2])
+    dx2_rate = dx2_ops / (dx2_ms / 1e3) / 1e12
     flops_det = det_stage_flops(mol) * W
-    det_ms = float(stage_x2[2])
+    det_ms = float(stage_mixed[2])
     det_rate = flops_det / (det_ms / 1e3) / 1e12
     roofline = {"kernel": "k_ao_mo_oz (AOs in pairs of FP32, exact digit-sliced contraction on tcgen05; FP32X2 form)",
                 "bound": "alu", "achieved": oz_rate, "peak": FP32_PEAK_TOPS, "unit": "T FP32 ops/s",
@@ -830,7 +880,15 @@ def main():
     simt_flops = fp64_ao["flops"] * W
     simt_equiv = simt_flops + (2.0 * exp_fma * fp64_ao["exp"] * W if exp_fma else 0.0)
     rooflines = {
+        "k_det_x2": {"bound": "alu", "achieved": dx2_rate, "peak": FP32_PEAK_TOPS, "unit": "T FP32 ops/s",
+                     "frac": dx2_rate / FP32_PEAK_TOPS, "kernel_ms": dx2_ms, "ops_per_launch": dx2_ops,
+                     "traffic": (None if DETX2_TRAFFIC_BYTES_PER_WALKER is None
+                                 else DETX2_TRAFFIC_BYTES_PER_WALKER * W),
+                     "peak_measured": fp32_meas, "frac_of_measured": dx2_rate / fp32_meas if fp32_meas else None,
+                     "ops_model": "bench.det_x2_stage_ops: pair-of-FP32 elimination, tables, minors and "
+                                  "expansion (FP32X2 form's determinant stage)"},
         "k_det": {"bound": "alu", "achieved": det_rate, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                  "form": "mixed_tf32 (the same kernel runs the FP64 form's determinant stage)",
                   "frac": det_rate / FP64_PEAK_TFLOPS, "kernel_ms": det_ms, "flops_per_launch": flops_det,
                   "traffic": None if DET_TRAFFIC_BYTES_PER_WALKER is None else DET_TRAFFIC_BYTES_PER_WALKER * W,
                   "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal)",
@@ -846,15 +904,15 @@ def main():
                                            "each exponential as the measured FMA equivalents"},
         "k_ao_mo_tc": {"kernel_ms": float(stage_mixed[1]), "note": "FP32 AO stage + tcgen05 TF32x3 contraction"},
     }
-    # whole step: the FP32X2 step cannot beat its AO stage at the FP32 issue
-    # rate plus its determinant stage at the FP64 rate (the two run in turn)
-    bound_ms = oz_ops / (FP32_PEAK_TOPS * 1e12) * 1e3 + flops_det / (FP64_PEAK_TFLOPS * 1e12) * 1e3
+    # whole step: the FP32X2 step cannot beat its AO stage plus its
+    # determinant stage at the FP32 issue rate (the two run in turn)
+    bound_ms = (oz_ops + dx2_ops) / (FP32_PEAK_TOPS * 1e12) * 1e3
     whole_step = {"ms_per_step": ms_step, "bound_ms": bound_ms, "frac": bound_ms / ms_step,
-                  "note": "AO stage at the FP32 issue rate + determinant stage at the FP64 rate, in sequence"}
+                  "note": "AO stage and determinant stage at the FP32 issue rate, in sequence"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32x2 AO+MO / f64 det", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32x2 (AO, MO, det; f64 in/out)", "data": "synthetic",
         "config": {"workload": (WORKLOAD.replace("262144 walkers", f"{W} walkers")
                                 + (" + many-body Jastrow (K_en, 5 K_een terms)" if args.manybody_jastrow else "")),
                    "walkers_per_gpu": W, "precision": "fp32x2",

@@ -1,6 +1,6 @@
 // Pairs of FP32 numbers ("double-float"): x = hi + lo with |lo| <= ulp(hi)/2,
 // about 48 significant bits, evaluated on the FP32 pipes.  On GB300 the FP64
-// pipe runs at 1/58 of the FP32 rate; the QMC_FP32X2 form computes the atomic
+// pipe runs at about 1/62 of the FP32 rate; the QMC_FP32X2 form computes the atomic
 // orbitals and the AO->MO contraction in this arithmetic so that the MO
 // channels reach near-FP64 accuracy at FP32-pipe cost.
 //

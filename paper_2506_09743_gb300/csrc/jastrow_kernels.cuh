@@ -21,7 +21,7 @@
 // float pairs (hi + lo, integer operations only), pair differences
 // (hi_i - hi_j) + (lo_i - lo_j) keep 2^-24 relative accuracy even for close
 // pairs, pair terms are FP32 and the sums J, V, kinJ are carried as
-// compensated (Kahan) FP32 pairs; on GB300 the FP64 pipe runs at 1/64 of the
+// compensated (Kahan) FP32 pairs; on GB300 the FP64 pipe runs at about 1/62 of the
 // FP32 rate, so this kernel issues no FP64 instruction until the three final
 // sums are widened.
 #pragma once

@@ -8,7 +8,7 @@
 // about 2^-47 per operation) bring the MO channels to within a few 2^-46 of
 // |AO| |C|, and the FP64 determinant stage then matches the FP64 form to
 // well under 2e-4 Ha on every walker short of the nodes.  GB300's FP64 pipe
-// runs at 1/58 of the FP32 rate, so pairs of FP32 cost far less than FP64.
+// runs at about 1/62 of the FP32 rate, so pairs of FP32 cost far less than FP64.
 //
 // One thread per (walker, electron), 128 walkers per block, one block row
 // per electron (the layout of the SIMT kernel of the other forms).  Per shell

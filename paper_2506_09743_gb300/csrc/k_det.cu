@@ -3,7 +3,7 @@
 //
 // Work decomposition: one thread per (walker, spin); the two spins of a
 // walker are adjacent lanes of one warp.  FP64 issue slots are the scarce
-// resource on GB300 (the FP64 pipe runs at 1/58 of the FP32 rate), so each
+// resource on GB300 (the FP64 pipe runs at about 1/62 of the FP32 rate), so each
 // thread keeps its reference inverse in registers and runs long chains of
 // independent FMAs (no shuffles inside the linear algebra, no idle lanes,
 // no duplicated per-walker work):

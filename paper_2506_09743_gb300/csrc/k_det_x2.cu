@@ -5,7 +5,7 @@
 // elimination with partial pivoting, Jacobi trace, excitation tables T_val
 // and Top, the determinant expansion of Eqs. nabla_sigma / delta_sigma with
 // the table formulas of App. F), with the linear algebra in pairs of FP32 on
-// the FP32 pipes instead of FP64: on GB300 the FP64 pipe runs at 1/62 of the
+// the FP32 pipes instead of FP64: on GB300 the FP64 pipe runs at about 1/62 of the
 // FP32 rate, and a pair multiply-accumulate costs about 12 FP32 instructions.
 //
 // Row scaling.  Each electron row r of a spin block is multiplied by an
