@@ -65,6 +65,25 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// FP64 flops per walker of the table-method determinant stage (k_det): per
+// spin with n electrons, nh holes and nv virtual columns 2n^3 (inverse),
+// 2n^2 (Jacobi trace) and nv 2(2n^2 + nh n) (tables); 2 per distinct rank-1
+// and 12 per distinct rank-2 spin excitation; 8 per determinant.  exc holds
+// the distinct excitation records per spin ([2][kMaxExc][5], rank first).
+double det_stage_flops(const WfDev& d, const std::vector<int>& exc) {
+  double f = 8.0 * d.n_det;
+  for (int s = 0; s < 2; ++s) {
+    const double n = s == 0 ? d.n_up : d.n_down;
+    if (n == 0) continue;
+    f += 2 * n * n * n + 2 * n * n + d.nv[s] * 2.0 * (2 * n * n + d.nh[s] * n);
+    for (int i = 1; i < d.n_exc[s]; ++i) {
+      const int rank = exc[(s * kMaxExc + i) * 5];
+      f += rank == 1 ? 2.0 : rank == 2 ? 12.0 : 0.0;
+    }
+  }
+  return f;
+}
+
 size_t ta_size(int prec) { return prec == QMC_FP64 ? 8 : 4; }
 
 size_t workspace_bytes(const qmc_wf* wf, int64_t W) {
@@ -600,10 +619,20 @@ qmc_status build_tables(qmc_wf* wf) {
       det_tab[4 * n + 2 * s] = packed;
       det_tab[4 * n + 2 * s + 1] = e[0];
     }
+  // The FP32X2 form's determinant stage.  k_det_x2 (pairs of FP32, eight
+  // lanes per spin block) has a fixed cost per walker that the FP64 stage
+  // k_det (one thread per spin block) does not; it pays where the tables and
+  // the expansion make the FP64 work large.  Measured det-stage times on
+  // 262,144 walkers of the CO basis with n electrons per spin (k_det /
+  // k_det_x2, ms): one determinant 0.09 / 0.31 (n = 2) ... 0.52 / 0.61 (n = 7);
+  // 100 determinants 0.66 / 0.72 (n = 3, 2,484 FP64 flops per walker),
+  // 0.89 / 0.81 (n = 4, 3,462 flops), 1.72 / 1.14 (n = 7, 6,486 flops).
+  d.det_x2 = (prec == QMC_FP32X2 && det_stage_flops(d, exc) >= 3000.0) ? 1 : 0;
+  if (d.det_x2 && det_x2_smem_bytes(d, true) > 227 * 1024) d.det_x2 = 0;
   if (h.w != 0.0 && !general_supported(d) && !bf_multidet_supported(d))
     return fail(QMC_ERR_UNSUPPORTED,
                 "backflow needs <= 8 electrons, <= 4 per spin and (several determinants) <= 8 orbital columns");
-  if (det_smem_bytes(d, true) > 227 * 1024 || (prec == QMC_FP32X2 && det_x2_smem_bytes(d, true) > 227 * 1024))
+  if (det_smem_bytes(d, true) > 227 * 1024)
     return fail(QMC_ERR_UNSUPPORTED, "determinant stage exceeds shared memory (too many MOs or excitations)");
 
   // ---- tensor-core B operand (MO^T, N = 16 rows, K = k_pad), TF32 hi/lo
@@ -918,7 +947,7 @@ static qmc_status eval_path(qmc_wf* wf, const double* walkers, int64_t W, int64_
   mark(wf, 4, st);
   s = launch_status(wf->det_method == QMC_DET_EXPLICIT
                         ? launch_det_explicit(d, wf->precision, W, v, kinetic, e_loc, log_psi, st)
-                        : x2 ? launch_det_x2(d, W, v, kinetic, e_loc, log_psi, st)
+                        : x2 && d.det_x2 ? launch_det_x2(d, W, v, kinetic, e_loc, log_psi, st)
                              : launch_det(d, wf->precision, W, v, kinetic, e_loc, log_psi, st),
                     "det");
   if (s) return s;

@@ -28,13 +28,16 @@
 // of the spin block (n <= 8 electrons), sixteen lanes per walker, eight
 // walkers per block of 128 threads.  Gauss-Jordan elimination runs in place
 // with implicit pivoting: at step k the unused row p_k with the largest
-// |a[p_k][k]| is broadcast by shuffles and eliminated from every other row;
-// afterwards lane i holds Z[i][k] = (A^^-1)[m_i][p_k], m_i being the step at
-// which row i was the pivot (the in-place result of the row-permuted
-// elimination).  The tables are then formed with one shuffle per operand:
-//     t[m_i]   = sum_k Z[i][k] Phi^_p[p_k]         (lane i)
-//     y[r]     = B^_p[r] - sum_m B^_0[r][m] t[m]   (lane r; t[m] from lane p_m)
-//     Top[m_i] = sum_k Z[i][k] y[p_k]              (lane i)
+// |a[p_k][k]| is broadcast by shuffles and eliminated from every other row
+// (the pivot row divided by its pivot in the same instruction stream, as
+// 0 - (-1/pivot) a_p); afterwards lane i holds Z[i][k] = (A^^-1)[m_i][p_k],
+// m_i being the step at which row i was the pivot (the in-place result of the
+// row-permuted elimination).  The tables are then formed per virtual column
+// p from three all-gathers within the group, each lane writing one pair to a
+// shared-memory slot and reading the group's slots back in 16-byte loads:
+//     t[m_i]   = sum_k Z[i][k] Phi^_p[p_k]         (lane i; slot m_r holds Phi^_p[r])
+//     y[r]     = B^_p[r] - sum_m B^_0[r][m] t[m]   (lane r; slot m_i holds t[m_i])
+//     Top[m_i] = sum_k Z[i][k] y[p_k]              (lane i; slot m_r holds y[r])
 // and stored, as in k_det, per walker in shared memory; the sixteen lanes of
 // a walker then split its determinant list and reduce their sums with
 // shuffles.  det A^ = sgn(p) prod_k pivot_k is kept as a pair with a
@@ -184,24 +187,28 @@ __global__ void __launch_bounds__(kThreadsX2, 6)
       if (ok > key || (ok == key && op < p)) { key = ok; p = op; }
     }
     pk[k] = p;
-    // the pivot row, normalised
+    // the pivot row as it stands; one instruction stream for every lane:
+    // the pivot row becomes 0 - (-inv) a_p = a_p / pv, every other row
+    // a - g a_p with g = a[k] / pv
     const f32x2 pv = shfl_x2(a[k], gbase + p);
     const f32x2 inv = recip_x2(pv);
-    f32x2 prn[NS];
+    f32x2 prw[NS];
 #pragma unroll
-    for (int c = 0; c < NS; ++c) prn[c] = shfl_x2(a[c], gbase + p) * inv;
+    for (int c = 0; c < NS; ++c) prw[c] = shfl_x2(a[c], gbase + p);
     if (act) {
       detm = detm * pv;
       dete += renorm_x2(detm);
-      if (r == p) {
+      const bool piv = r == p;
+      if (piv) {
         used = true;
         mi = k;
+      }
+      if (row) {
+        const f32x2 g = a[k] * inv;
+        const f32x2 gg = piv ? -inv : g;
 #pragma unroll
-        for (int c = 0; c < NS; ++c) a[c] = c == k ? inv : prn[c];
-      } else if (row) {
-        const f32x2 f = a[k];
-#pragma unroll
-        for (int c = 0; c < NS; ++c) a[c] = c == k ? -(f * inv) : fms_x2(a[c], f, prn[c]);
+        for (int c = 0; c < NS; ++c)
+          a[c] = c == k ? (piv ? inv : -g) : fms_x2(piv ? f32x2(0.f) : a[c], gg, prw[c]);
       }
     }
   }
@@ -233,6 +240,26 @@ __global__ void __launch_bounds__(kThreadsX2, 6)
     for (int c = 0; c < NS; ++c) b0r[c] = b0_s[r * kLanes + c];
   }
   const bool hole = row && mi >= hl;
+  // per group three broadcast buffers (Phi_p by pivot step, t by step, y by
+  // pivot step), 10 pairs apart so that a warp's four groups read different
+  // banks
+  __shared__ __align__(16) f32x2 bc_all[3][kThreadsX2 / kLanes][10];
+  f32x2* bcP = bc_all[0][threadIdx.x >> 3];
+  f32x2* bcT = bc_all[1][threadIdx.x >> 3];
+  f32x2* bcY = bc_all[2][threadIdx.x >> 3];
+  // sum_k z[k] buf[k] over the n broadcast slots (two pairs per 16-byte load)
+  auto dot_bc = [&](const f32x2* buf, const f32x2* z) -> f32x2 {
+    f32x2 acc(0.f);
+    const float4* b4 = reinterpret_cast<const float4*>(buf);
+#pragma unroll
+    for (int k2 = 0; k2 < (NS + 1) / 2; ++k2) {
+      const float4 qv = b4[k2];
+      if (2 * k2 < n) mac_x2(acc, z[2 * k2], f32x2(qv.x, qv.y));
+      if (2 * k2 + 1 < NS)
+        if (2 * k2 + 1 < n) mac_x2(acc, z[2 * k2 + 1], f32x2(qv.z, qv.w));
+    }
+    return acc;
+  };
   const int nv_max = max(wf.nv[0], wf.nv[1]);
   double nphi = (row && nv > 0) ? ld(0, n) : 0.0;
   double nbp = (KIN && row && nv > 0) ? ld(1, n) : 0.0;
@@ -244,30 +271,25 @@ __global__ void __launch_bounds__(kThreadsX2, 6)
       nphi = ld(0, n + pv + 1);
       if (KIN) nbp = ld(1, n + pv + 1);
     }
-    // t[m_i] = sum_k Z[i][k] Phi^_p[p_k]
-    f32x2 t(0.f);
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      const f32x2 v = shfl_x2(phi, gbase + pk[k]);
-      if (k < n) mac_x2(t, a[k], v);
-    }
-    t = normalize_x2(t);
+    // t[m_i] = sum_k Z[i][k] Phi^_p[p_k]: lane r puts Phi^_p[r] in slot m_r
+    if (row) bcP[mi] = phi;
+    __syncwarp();
+    f32x2 t = normalize_x2(dot_bc(bcP, a));
     if (pact && hole) tab[tab_off + (mi - hl) * nv + pv] = t;
     if (KIN) {
-      // y[r] = B^_p[r] - sum_m B^_0[r][m] t[m], t[m] held by lane p_m
-      f32x2 y = bp;
+      // y[r] = B^_p[r] - sum_m B^_0[r][m] t[m]: lane i puts t[m_i] in slot
+      // m_i (accumulated unnormalised, normalised once)
+      if (row) bcT[mi] = t;
+      __syncwarp();
+      f32x2 nb0[NS];
 #pragma unroll
-      for (int m = 0; m < NS; ++m) {
-        const f32x2 tm = shfl_x2(t, gbase + pk[m]);
-        if (m < n) y = fms_x2(y, b0r[m], tm);
-      }
-      // Top[m_i] = sum_k Z[i][k] y[p_k]
-      f32x2 acc(0.f);
-#pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        const f32x2 v = shfl_x2(y, gbase + pk[k]);
-        if (k < n) mac_x2(acc, a[k], v);
-      }
+      for (int m = 0; m < NS; ++m) nb0[m] = -b0r[m];
+      f32x2 y = dot_bc(bcT, nb0);
+      y = normalize_x2(bp + y);
+      // Top[m_i] = sum_k Z[i][k] y[p_k]: lane r puts y[r] in slot m_r
+      if (row) bcY[mi] = y;
+      __syncwarp();
+      f32x2 acc = dot_bc(bcY, a);
       if (pact && hole) tab[tab_off + nh * nv + (mi - hl) * nv + pv] = normalize_x2(acc);
     }
   }
@@ -328,11 +350,12 @@ __global__ void __launch_bounds__(kThreadsX2, 6)
   const int esum_o = __shfl_xor_sync(0xffffffffu, esum, 8);
   const f32x2 tr0_o = KIN ? shfl_xor_x2(tr0, 8) : f32x2(0.f);
   if (q == 0 && live) {
-    const double sr = widen(sum_r);
-    const double lp = jscal[w] + log(fabs(widen(detm) * widen(detm_o) * sr)) +
+    // the products and the kinetic quotient in pairs; FP64 for the logarithm
+    // and the final sums only (the FP64 pipe runs at about 1/62 of the FP32 rate)
+    const double lp = jscal[w] + log(fabs(widen((detm * detm_o) * sum_r))) +
                       (double)(dete + dete_o + esum + esum_o) * 0.69314718055994530942;
     if (log_psi) log_psi[w] = lp;
-    if (KIN) e_loc[w] = -0.5 * (jscal[ldm + w] + widen(tr0 + tr0_o) + widen(sum_k) / sr) + jscal[2 * ldm + w];
+    if (KIN) e_loc[w] = -0.5 * (jscal[ldm + w] + widen(tr0 + tr0_o + sum_k * recip_x2(sum_r))) + jscal[2 * ldm + w];
   }
 }
 

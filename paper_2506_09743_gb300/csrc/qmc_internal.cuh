@@ -103,6 +103,7 @@ struct WfDev {
   // nullptr: the kernel bounds every shell instead
   const float4* oz_bound;
   int tc_value;            // 1: the FP32X2 form's Metropolis value path runs k_ao_mo_tc (FP32 AOs)
+  int det_x2;              // 1: the FP32X2 form's determinant stage runs k_det_x2 (pairs of FP32), 0: k_det (FP64)
   const float* exp_tab;    // [64][2] 2^(j/64) as pairs: exp of the FP32X2 form
   const float2* mo_x2n;    // [n_ao][n_mo] MO table (angular factors folded in) as pairs, AO order
   int gen_x2;              // 1: the general (backflow) kernels evaluate the orbitals in pairs of FP32
