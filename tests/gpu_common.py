@@ -13,8 +13,9 @@ Per-walker gates, fixed before measurement:
 * FP64 form: |dE| <= 1e-10 max(1, |E|) for every walker whose backward-error
   bound 128 u s max(1, |E|) (u = 2^-53) is below that, and for at least 99%
   of all walkers; every walker within the bound.
-* FP32X2 form (AOs and contraction in pairs of FP32, FP64 determinants):
-  |dE| <= 2e-4 Ha on every walker inside the cut (``gated_check``).
+* FP32X2 form (AOs, contraction and, where it pays, the determinant stage
+  in pairs of FP32; FP64 determinants otherwise): |dE| <= 2e-4 Ha on every
+  walker inside the cut (``gated_check``).
 * FP32-AO forms (fp32, mixed_tf32): not held to 2e-4 Ha.  FP32 AO values
   put about one CO walker in six beyond it; the check asserts that every
   walker is within the FP32 backward-error bound 128 u s max(1, |E|),

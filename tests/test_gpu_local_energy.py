@@ -441,3 +441,40 @@ def test_fp32x2_near_coalescence(pkg, name):
     E, _ = _run(pkg, mol, r, "fp32x2")
     st = gated_check(E, E_ref, sens)
     print(name, "near-coalescence fp32x2", st)
+
+
+def _co_rows(n_up, n_down, n_det=100):
+    """The CO basis, MOs and Jastrow with n_up / n_down electrons and 100
+    determinants of SD over its 14 orbitals (up to 5 active holes per spin)."""
+    import dataclasses
+
+    co = qi.make_co()
+    all_dets = qi.sd_expansion(n_up, n_down, 14, max(0, min(n_up, n_down) - 5))
+    dets = qi._dets_array(qi._select_dets(all_dets, n_det, np.random.default_rng(qi.SEED_DETS)))
+    return dataclasses.replace(
+        co, name=f"co_rows_{n_up}_{n_down}", n_up=n_up, n_down=n_down, det_exc=dets,
+        det_weight=qi._ci_weights(len(dets), np.random.default_rng(qi.SEED_CI)),
+        electron_home=qi.electron_homes(co.atom_z, n_up, n_down))
+
+
+# Spin blocks of 4 to 8 rows, equal and unequal per spin: the FP64 stage of
+# these expansions costs 3,522 to 7,544 flops per walker, so the FP32X2 form
+# runs its pair-of-FP32 determinant stage (one instantiation per block size;
+# two spin groups of a warp with different row counts), the FP64 form k_det.
+@pytest.mark.parametrize("n_up,n_down", [(4, 4), (5, 4), (6, 6), (7, 6), (8, 8)])
+def test_determinant_stage_block_sizes(pkg, n_up, n_down):
+    mol = _co_rows(n_up, n_down)
+    r = qi.walkers(mol, 300, seed=23)
+    E_ref, lp_ref, sens = oracle_reference(mol, r)
+    E64, lp64 = _run(pkg, mol, r, "fp64", ldw_pad=5)
+    st64 = fp64_check(E64, E_ref, sens)
+    assert np.all(np.abs(lp64 - lp_ref) <= 128 * 2.0 ** -53 * sens * np.maximum(1, np.abs(lp_ref)))
+    E, lp = _run(pkg, mol, r, "fp32x2")
+    st = reduced_check("fp32x2", E, E_ref, sens)
+    # log|Psi|: the FP32X2 Jastrow sums FP32 pair terms |u| <= w0 / b = 0.5
+    # (a few ulp each, 2^-21 allowed), the pair-of-FP32 orbitals and
+    # determinants add about 2^-44 s (2^-40 s allowed)
+    n = mol.n_up + mol.n_down
+    tol_lp = 2.0 ** -21 * (n * (n - 1) // 2) * 0.5 + 2.0 ** -40 * sens
+    assert np.all(np.abs(lp - lp_ref) <= tol_lp), float(np.max(np.abs(lp - lp_ref) / tol_lp))
+    print(f"rows {n_up}/{n_down} fp64 {st64} fp32x2 {st}")
