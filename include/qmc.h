@@ -68,13 +68,17 @@ typedef enum {
  *                  contraction exact on the tcgen05 tensor cores (the pairs
  *                  cut into BF16 digits; SIMT pairs when n_mo > 16,
  *                  n_ao > 96 or n_ao n_mo < 256), electron-nucleus potential in pairs of
- *                  FP32 and electron-electron terms in compensated FP32, FP64
- *                  determinants: MO values within about 2^-43 of |AO||C|, so
- *                  that the local energy matches the FP64 form to 2e-4 Ha on
- *                  every walker away from the nodes (where FP32 AOs leave
- *                  about one CO walker in six beyond it).  The Metropolis
- *                  value path (log|Psi| of the acceptance test) runs the
- *                  MIXED_TF32 stages: FP32-level log|Psi|.
+ *                  FP32 and electron-electron terms in compensated FP32: MO
+ *                  values within about 2^-43 of |AO||C|, so that the local
+ *                  energy matches the FP64 form to 2e-4 Ha on every walker
+ *                  away from the nodes (where FP32 AOs leave about one CO
+ *                  walker in six beyond it).  The determinant stage (table
+ *                  method) runs in pairs of FP32 on rows scaled by powers of
+ *                  two where its FP64 form would cost at least 3,000 flops per
+ *                  walker (CO with 100 determinants: 6,560), in FP64
+ *                  otherwise; the explicit method stays FP64.  The Metropolis
+ *                  value path (log|Psi| of the acceptance test) evaluates the
+ *                  orbitals as MIXED_TF32 does: FP32-level log|Psi|.
  * Jastrow terms are FP64 in QMC_FP64 and use FP32 pair arithmetic with
  * compensated sums in the other forms; the Coulomb potential is FP64 in
  * QMC_FP64; in QMC_FP32X2 its electron-nucleus terms are pairs of FP32 and

@@ -48,7 +48,8 @@ class Wavefunction:
     """A device-resident Slater-Jastrow(-backflow) wavefunction.
 
     ``mol`` is a ``qmc_inputs.Molecule`` (plain arrays).  ``precision`` is one
-    of ``fp64``, ``fp32``, ``mixed_tf32``, ``mixed_bf16``.
+    of ``fp64``, ``fp32``, ``mixed_tf32``, ``fp32x2`` (``mixed_bf16`` is
+    declared but not built: QMC_ERR_UNSUPPORTED).
     """
 
     def __init__(self, mol, precision: str = "fp64", device: int = 0):
