@@ -110,7 +110,7 @@ __device__ __forceinline__ int renorm_x2(f32x2& v) {
 }  // namespace
 
 template <int NS, bool KIN>
-__global__ void __launch_bounds__(kThreadsX2, 6)
+__global__ void __launch_bounds__(kThreadsX2, 7)
     k_det_x2(WfDev wf, int64_t W, const double* __restrict__ mo, int nmp, int64_t ldm,
              const double* __restrict__ jscal, int stride, double* __restrict__ e_loc, double* __restrict__ log_psi) {
   constexpr int NCH = KIN ? 2 : 1;
