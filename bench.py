@@ -49,9 +49,9 @@ DET_TRAFFIC_BYTES_PER_WALKER = (414.384128e6 + 4.216064e6) / 131072
 # 131,072 CO walkers (66.3 MB read, 409.0 MB written per launch); None whenever the kernel changes.
 OZ_TRAFFIC_BYTES_PER_WALKER = (66.262016e6 + 408.966912e6) / 131072
 # DRAM bytes (read + write) per walker of the k_det_x2 launch (FP32X2 determinant stage), from an ncu
-# capture of that kernel on 131,072 CO walkers (414.4 MB read, 1.2 MB written: energies only, no
-# log|Psi|); None whenever the kernel changes.
-DETX2_TRAFFIC_BYTES_PER_WALKER = (414.364160e6 + 1.238272e6) / 131072
+# capture of that kernel on 131,072 CO walkers; None whenever the kernel changes (the last capture,
+# 414.4 MB read and 1.2 MB written, was of the six-blocks-per-SM build).
+DETX2_TRAFFIC_BYTES_PER_WALKER = None
 
 
 def det_stage_flops(mol) -> float:
